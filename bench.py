@@ -1,0 +1,376 @@
+"""Benchmark: alpha complexes of synthetic atom sets on GB300 (atoms/s).
+
+One step = one ac_build over the whole workload: quantisation, grid binning,
+neighbour lists, the fused estimation + pruning pass (potential simplices and
+AC2, Sections 4.3-4.4 / Steps 1-5 of arXiv 1908.05944), canonical lists and
+Size filtration values. Inputs are resident in device memory when the timed
+region starts; L2 is flushed (a 256 MB write) between timed steps.
+
+`e2e` repeats the step through the public C ABI with host buffers: create from
+pinned host arrays (host->device copy), build, copy every simplex list and
+filtration value back to pinned host memory, destroy.
+
+With --impl reference the exact CPU oracle (oracle/) is timed instead, on a
+bounded sub-ball of the same workload per step, on the host cores.
+
+Multi-GPU: independent replicas (the path has no exchange step); each rank
+builds its own copy; value = atoms of all ranks / max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "alpha-complex atoms/s, plain vs filtered & batched, 100k/3M atoms; % roofline"
+UNIT = "atoms/s"
+
+# Algorithmic work of the per-atom pass, FP32 flops (an FMA counts 2), per unit:
+# AC3 test of an edge / triangle / tetrahedron candidate (orthocentre solve) and
+# one AC2 test of a (simplex, neighbour) pair: 3 FMA dot + 1 FMA + compare.
+FLOPS_AC3 = {1: 20.0, 2: 60.0, 3: 120.0}
+FLOPS_AC2 = 12.0
+FP32_LANES_PER_SM = 128
+SMS = 152
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default="globule100k_probe")
+    p.add_argument("--precision", default="filtered", choices=["filtered", "plain_fp64"])
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-forms", action="store_true", help="skip the plain/shell side measurements")
+    return p.parse_args()
+
+
+def dist_init(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "nccl" if args.impl == "ours" else "gloo"
+        if args.impl == "ours":
+            torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        dist.init_process_group(backend=backend)
+    return rank, world
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if torch.cuda.is_available() and dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+class ClockSampler:
+    """nvidia-smi SM clocks and throttle reasons, sampled while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self._t = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for k, name in enumerate(names):
+                if parts[5 + k].lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def workload(name):
+    import synth
+    return synth.workload(name)
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh)
+    except Exception:
+        return {}
+
+
+def algorithmic_flops(st):
+    f = 0.0
+    for d in (1, 2, 3):
+        f += FLOPS_AC3[d] * st["ac3_tests"][d]
+    f += FLOPS_AC2 * (sum(st["ac2_tests_tet"]) + sum(st["ac2_tests_tri"]) + st["ac2_tests_edge"])
+    return f
+
+
+def run_ours(args, rank, world):
+    import torch
+
+    import paper_1908_05944_gb300 as ac
+
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    c_np, r_np = workload(args.workload)
+    n = len(r_np)
+    prec = ac.AC_PRECISION_FILTERED if args.precision == "filtered" else ac.AC_PRECISION_PLAIN_FP64
+    c = torch.from_numpy(c_np).cuda()
+    r = torch.from_numpy(r_np).cuda()
+    cx = ac.AlphaComplex(c, r, 0.0, ac.options(precision=prec))
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    for _ in range(args.warmup):
+        cx.build(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    ms = []
+    local_ms = []
+    launches = 0
+    flops = []
+    with ClockSampler(dev) as clk:
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            torch.cuda.synchronize()
+            t0 = torch.cuda.Event(enable_timing=True)
+            t1 = torch.cuda.Event(enable_timing=True)
+            t0.record(stream)
+            cx.build(stream)
+            t1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(t0.elapsed_time(t1))
+            st = cx.stats()
+            local_ms.append(st["ms_stage"][7])
+            launches += st["kernel_launches"]
+            flops.append(algorithmic_flops(st))
+    torch.cuda.synchronize()
+    barrier(world)
+    total_ms = max_over_ranks(float(sum(ms)), world)
+    st = cx.stats()
+    counts = [cx.count(d) for d in range(4)]
+    res = {
+        "n_atoms": n,
+        "ms_per_step": total_ms / args.steps,
+        "value": n * world * args.steps / (total_ms / 1e3),
+        "simplices_per_s": sum(counts) * world * args.steps / (total_ms / 1e3),
+        "counts": counts,
+        "stats": st,
+        "local_ms": float(np.mean(local_ms)),
+        "local_flops": float(np.mean(flops)),
+        "launches": launches,
+        "clocks": clk.summary(),
+    }
+    cx.close()
+    return res
+
+
+def run_e2e(args, rank, world, steps):
+    """Whole public-API round trip with host buffers (pinned)."""
+    import torch
+
+    import paper_1908_05944_gb300 as ac
+
+    c_np, r_np = workload(args.workload)
+    n = len(r_np)
+    c_h = torch.from_numpy(c_np).pin_memory()
+    r_h = torch.from_numpy(r_np).pin_memory()
+    prec = ac.AC_PRECISION_FILTERED if args.precision == "filtered" else ac.AC_PRECISION_PLAIN_FP64
+    h2d = c_np.nbytes + r_np.nbytes
+    outs_host = None
+    times = []
+    d2h = 0
+    for it in range(steps + 1):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        cx = ac.AlphaComplex(c_h, r_h, 0.0, ac.options(precision=prec))
+        cx.build()
+        d2h = 0
+        if outs_host is None:
+            outs_host = []
+            for d in range(4):
+                m = cx.count(d)
+                outs_host.append((torch.empty((max(m, 1) * 2, d + 1), dtype=torch.int32).pin_memory(),
+                                  torch.empty(max(m, 1) * 2, dtype=torch.float64).pin_memory()))
+        for d in range(4):
+            tv = cx.simplices(d, copy=False)
+            fv = cx.filtration_values(d, copy=False)
+            cnt = tv.shape[0]
+            if cnt:
+                if outs_host[d][0].shape[0] < cnt:
+                    outs_host[d] = (torch.empty((cnt * 2, d + 1), dtype=torch.int32).pin_memory(),
+                                    torch.empty(cnt * 2, dtype=torch.float64).pin_memory())
+                outs_host[d][0][:cnt].copy_(tv, non_blocking=True)
+                outs_host[d][1][:cnt].copy_(fv, non_blocking=True)
+            d2h += cnt * (d + 1) * 4 + cnt * 8
+        torch.cuda.synchronize()
+        cx.close()
+        torch.cuda.synchronize()
+        if it > 0:  # first round trip warms the allocator
+            times.append(time.perf_counter() - t0)
+    t = max_over_ranks(float(sum(times)), world)
+    return {"value": n * world * steps / t, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+
+
+def cpu_baseline(args, sample_atoms=20000):
+    import oracle
+    import synth
+
+    c, r = workload(args.workload)
+    sub_c, sub_r = sub_ball(c, r, sample_atoms)
+    threads = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    res = oracle.alpha_complex(sub_c, sub_r, 0.0, threads=threads)
+    dt = time.perf_counter() - t0
+    return {"value": len(sub_r) / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{len(sub_r)}-atom sub-ball of {args.workload} around its centre, 1 run, {dt:.2f} s",
+            "simplices": int(sum(res.counts()))}
+
+
+def sub_ball(c, r, k):
+    centre = np.median(c, axis=0)
+    d = np.linalg.norm(c - centre, axis=1)
+    idx = np.sort(np.argsort(d)[:k])
+    return c[idx], r[idx]
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    import oracle
+
+    c, r = workload(args.workload)
+    sc, sr = sub_ball(c, r, 20000)
+    threads = os.cpu_count() or 1
+    for _ in range(args.warmup):
+        oracle.alpha_complex(sc, sr, 0.0, threads=threads)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.alpha_complex(sc, sr, 0.0, threads=threads)
+        times.append(time.perf_counter() - t0)
+    tot = sum(times)
+    value = len(sr) * args.steps / tot
+    sample = f"{len(sr)}-atom sub-ball of {args.workload} per step"
+    return {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64/int128 (exact)",
+        "data": "synthetic", "config": {"workload": args.workload, "alpha": 0.0, "sample_atoms": len(sr)},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    args = parse()
+    rank, world = dist_init(args)
+    if args.impl == "reference":
+        line = run_reference(args, rank, world)
+        if rank == 0:
+            print(json.dumps(line))
+        return
+    import torch  # noqa: F401
+
+    import importlib
+    importlib.import_module("paper_1908_05944_gb300.build").build()
+    res = run_ours(args, rank, world)
+    peaks = measured_peaks()
+    clocks = res["clocks"]
+    sm_mhz = clocks.get("sm_mhz") or peaks.get("clocks_under_load", {}).get("sm_mhz_median") or 2070.0
+    peak_tflops = SMS * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+    achieved = res["local_flops"] / (res["local_ms"] * 1e-3) / 1e12 if res["local_ms"] > 0 else 0.0
+    line = {
+        "metric": METRIC, "value": res["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": res["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32 filter, f64/int128 exact fallback" if args.precision == "filtered"
+        else "f64 filter, int128 exact fallback",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "n_atoms": res["n_atoms"], "alpha": 0.0,
+                   "precision": args.precision, "l2": "flushed (256 MB write) between timed steps",
+                   "parallelism": f"replicas x{world}"},
+        "simplices_per_s": res["simplices_per_s"],
+        "simplices": res["counts"],
+        "clocks": clocks,
+        "gpu_launches": res["launches"],
+        "roofline": {"bound": "alu", "kernel": "k_local (fused estimation + pruning)", "achieved": achieved,
+                     "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved / peak_tflops if peak_tflops else None,
+                     "traffic": None,
+                     "peak_basis": f"FP32 FMA: {SMS} SMs x {FP32_LANES_PER_SM} lanes x 2 x {sm_mhz:.0f} MHz "
+                                   "(derived; sampled SM clock)"},
+        "stage_ms": res["stats"]["ms_stage"],
+        "predicates": {"ac2_tet": res["stats"]["ac2_tests_tet"], "ac2_tri": res["stats"]["ac2_tests_tri"],
+                       "ac2_edge": res["stats"]["ac2_tests_edge"], "ac3": res["stats"]["ac3_tests"]},
+    }
+    if not args.no_e2e:
+        line["e2e"] = run_e2e(args, rank, world, max(2, min(args.steps, 5)))
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args)
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

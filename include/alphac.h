@@ -1,0 +1,198 @@
+/*
+ * alphac: alpha complexes of weighted points (atoms) on one GB300 GPU.
+ *
+ * The method is the Delaunay-free construction of Masood, Ray and Natarajan,
+ * "Parallel Computation of Alpha Complexes for Biomolecules" (arXiv 1908.05944):
+ * an estimation pass builds, bottom-up, every edge, triangle and tetrahedron
+ * whose OrthoSize is at most alpha (Section 4.3, Step 1 of Section 3.1), and a
+ * pruning pass keeps those whose orthocentre passes the empty-orthosphere test
+ * AC2, inserting the faces of kept simplices directly (Section 4.4, Steps 2-5).
+ *
+ * Conventions
+ *   - Lengths in angstrom, alpha in angstrom^2. Centres and radii are quantised
+ *     to 1/1024 A (round half to even); alpha to 2^-20 A^2. Every predicate is
+ *     decided exactly on these integers.
+ *   - Ties (the paper's "symbolic perturbation", Section 2) are broken by
+ *     perturbing the squared radii, W_k + eps_k, with eps_k decreasing steeply
+ *     in the INPUT index k. The alpha bound itself (AC3) is not perturbed and
+ *     is inclusive.
+ *   - A simplex is a tuple of input indices in ascending order; each dimension
+ *     is returned as one row-major int32 array (count, d+1) sorted
+ *     lexicographically.
+ *   - "Device" pointers are CUDA global memory of the current device; "host"
+ *     pointers are ordinary (pageable or pinned) memory. Where an argument may
+ *     be either, the library asks the CUDA driver which it is.
+ *   - stream arguments are cudaStream_t values passed as void* (NULL = the
+ *     legacy default stream).
+ *   - Every call returns AC_OK (0) or a negative AC_ERR_* code; no exception
+ *     crosses this boundary. ac_last_error_detail() gives a message for the
+ *     calling thread's last failure.
+ *   - Results live in device memory owned by the context and stay valid until
+ *     the next ac_build on it or ac_destroy.
+ *   - A context is not thread safe: one host thread at a time may use it.
+ */
+#ifndef ALPHAC_H
+#define ALPHAC_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define AC_API __attribute__((visibility("default")))
+#else
+#define AC_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define AC_OK 0
+#define AC_ERR_INVALID_ARG -1 /* NULL pointer, n < 0, NaN/Inf, radius <= 0, bad dim */
+#define AC_ERR_DEGENERATE -2  /* two centres coincide after quantisation */
+#define AC_ERR_RANGE -3       /* inputs beyond the exact-integer ranges (see ac_create) */
+#define AC_ERR_CAPACITY -4    /* an internal list outgrew what regrowth allows */
+#define AC_ERR_OOM -5         /* device allocation failed */
+#define AC_ERR_CUDA -6        /* a CUDA runtime call failed (the sticky error is not cleared) */
+#define AC_ERR_TIMEOUT -7     /* a bounded device-side wait gave up */
+#define AC_ERR_STATE -8       /* results asked for before ac_build, or after a failed one */
+
+/* precision of the predicate evaluation; every mode decides every predicate exactly */
+#define AC_PRECISION_FILTERED 0  /* FP32 with a forward error bound -> FP64 -> exact integers */
+#define AC_PRECISION_PLAIN_FP64 1 /* FP64 with a forward error bound -> exact integers */
+
+/* which value ac_filtration_values returns */
+#define AC_FILTRATION_SIZE 0      /* Size (Section 2.3): radius^2 of the smallest empty orthosphere */
+#define AC_FILTRATION_ORTHOSIZE 1 /* OrthoSize: the simplex's own orthosphere */
+
+typedef struct ac_ctx ac_ctx;
+
+/* Zero-initialised options select the defaults. */
+typedef struct {
+    int32_t precision;     /* AC_PRECISION_* */
+    int32_t filtration;    /* AC_FILTRATION_* */
+    double cell_factor;    /* grid cell side = cell_factor * sqrt(r_max^2 + alpha); 0 = 1.0 */
+    int32_t block_warps;   /* warps per block of the per-atom kernel; 0 = 8 */
+    int32_t keep_candidates; /* 1: also keep the estimation-pass lists Sigma_ortho^1..3 */
+    int32_t reserved[8];
+} ac_options;
+
+typedef struct {
+    int64_t n_atoms;
+    int64_t candidates[4]; /* |Sigma_ortho^d|: simplices with OrthoSize <= alpha (Step 1) */
+    int64_t simplices[4];  /* |K_alpha^d| */
+    int64_t neighbour_pairs; /* ordered pairs of atoms whose grown balls meet */
+    int32_t max_degree;
+    int32_t grid_dims[3];
+    /* predicate decisions by the level that settled them: [0] FP32, [1] FP64, [2] exact */
+    int64_t ac2_tests_tet[3];
+    int64_t ac2_tests_tri[3];
+    int64_t ac2_tests_edge; /* exact 64-bit integers */
+    int64_t ac3_tests[4];   /* per dimension, exact integers */
+    double ms_total;        /* device time of the last ac_build (CUDA events) */
+    double ms_stage[8];     /* grid, neighbours, per-atom pass, canonical K3, K2, K1+K0+lists, filtration,
+                               and the per-atom kernel's own launch */
+    int64_t kernel_launches; /* kernels the last ac_build launched */
+} ac_stats;
+
+/*
+ * Create a context for one set of balls (Section 2: B = {(p_i, r_i)}) and one
+ * alpha (Section 2.4). Copies and quantises the input; the caller keeps its
+ * buffers. centres: n x 3 row-major doubles (A); radii: n doubles (A), both
+ * host or device. opt may be NULL.
+ * Ranges checked here (else AC_ERR_RANGE): |coordinate| <= 2^20 A, and
+ * r_max^2 + alpha <= 16 A^2 (h = sqrt(r_max^2 + alpha) <= 4 A keeps every
+ * predicate inside 128-bit integers). n must be below 2^31.
+ * Errors: AC_ERR_INVALID_ARG (NULL out, n < 0, NaN/Inf, radius <= 0),
+ * AC_ERR_RANGE, AC_ERR_OOM, AC_ERR_CUDA. On error *out is NULL.
+ */
+AC_API int ac_create(const double* centres, const double* radii, int64_t n, double alpha, const ac_options* opt,
+              ac_ctx** out);
+
+/*
+ * Create a context for a batch of independent molecules sharing one alpha.
+ * Molecule m is atoms [offsets[m], offsets[m+1]) of centres/radii; offsets is
+ * a HOST array of n_mol + 1 non-decreasing int64 starting at 0. Indices in the
+ * results are per molecule (0-based within the molecule). Same errors as
+ * ac_create.
+ */
+AC_API int ac_create_batch(const double* centres, const double* radii, const int64_t* offsets, int64_t n_mol,
+                    double alpha, const ac_options* opt, ac_ctx** out);
+
+/*
+ * Compute the alpha complex (Steps 1-5 of Section 3.1; Sections 4.2-4.4) and
+ * the filtration values. Enqueued on stream; returns after the device work is
+ * finished (list sizes are read back to size the results).
+ * Errors: AC_ERR_DEGENERATE, AC_ERR_CAPACITY, AC_ERR_OOM, AC_ERR_CUDA.
+ */
+AC_API int ac_build(ac_ctx* ctx, void* stream);
+
+/*
+ * Device pointer to the simplices of dimension dim (0..3): *count rows of
+ * dim+1 ascending int32 input indices, sorted lexicographically. mol selects a
+ * molecule of a batch context (-1 for a single-molecule context). Owned by ctx.
+ * Errors: AC_ERR_INVALID_ARG, AC_ERR_STATE.
+ */
+AC_API int ac_get_simplices(ac_ctx* ctx, int dim, int64_t mol, const int32_t** d_tuples, int64_t* count);
+
+/*
+ * Device pointer to one double per simplex of ac_get_simplices(dim, mol), in
+ * the same order: Size (Section 2.3) in A^2, or OrthoSize when the context was
+ * created with AC_FILTRATION_ORTHOSIZE. Owned by ctx.
+ */
+AC_API int ac_filtration_values(ac_ctx* ctx, int dim, int64_t mol, const double** d_f, int64_t* count);
+
+/*
+ * Device pointer to one uint8 per simplex of (dim, mol): 1 if AC2 fails at the
+ * simplex's own orthocentre (it is in the complex as a face of a larger
+ * simplex, "attached"), else 0. Owned by ctx.
+ */
+AC_API int ac_attached_flags(ac_ctx* ctx, int dim, int64_t mol, const uint8_t** d_flags, int64_t* count);
+
+/*
+ * Device pointers to the estimation-pass lists Sigma_ortho^dim (dim 1..3) of a
+ * context created with keep_candidates = 1 (single molecule only): rows of
+ * ascending input indices, sorted lexicographically. AC_ERR_STATE otherwise.
+ */
+AC_API int ac_get_candidates(ac_ctx* ctx, int dim, const int32_t** d_tuples, int64_t* count);
+
+/*
+ * Re-evaluate the filtration values at other centres/radii (device, same
+ * layout as ac_create, n atoms) with the combinatorics of the last build held
+ * fixed: each simplex keeps its source simplex (the one whose orthocentre is
+ * its closest witness) and takes that source's OrthoSize, in FP64.
+ * d_f_out[dim] receives one double per simplex of dim (device, caller-owned;
+ * NULL skips that dimension). For finite-difference checks of ac_backward.
+ */
+AC_API int ac_eval_filtration(ac_ctx* ctx, const double* d_centres, const double* d_radii, double* const d_f_out[4],
+                       void* stream);
+
+/*
+ * Gradient of L = sum_dim sum_s dLdf[dim][s] * f[dim][s] with respect to the
+ * centres and radii, combinatorics fixed (FP64). With lambda the barycentric
+ * coordinates of the source's orthocentre c in its affine hull:
+ * df/dp_k = 2 lambda_k (p_k - c), df/dr_k = -2 r_k lambda_k.
+ * d_dLdf[dim]: device, one double per simplex (NULL = zero). Outputs are
+ * device, caller-owned, n x 3 and n doubles, OVERWRITTEN (not accumulated).
+ */
+AC_API int ac_backward(ac_ctx* ctx, const double* const d_dLdf[4], double* d_dLdcentres, double* d_dLdradii,
+                void* stream);
+
+/* Counters and stage times of the last ac_build. */
+AC_API int ac_get_stats(ac_ctx* ctx, ac_stats* out);
+
+/* Number of molecules (1 for a single-molecule context) and atoms. */
+AC_API int ac_get_sizes(ac_ctx* ctx, int64_t* n_mol, int64_t* n_atoms);
+
+/* Free the context and everything it owns. NULL is a no-op. */
+AC_API void ac_destroy(ac_ctx* ctx);
+
+/* Static description of an AC_* code. */
+AC_API const char* ac_error_string(int code);
+
+/* Detail of the calling thread's last failure (empty string if none). */
+AC_API const char* ac_last_error_detail(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ALPHAC_H */

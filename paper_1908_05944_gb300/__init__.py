@@ -1,0 +1,327 @@
+"""Python binding of alphac (include/alphac.h): alpha complexes of weighted atoms on one GPU.
+
+The binding only marshals arguments to the C ABI of ``_build/libalphac.so``;
+every step of the computation runs in the library's CUDA kernels. There is no
+CPU fallback: if the library is missing or cannot be loaded, calls raise.
+
+Method: Masood, Ray, Natarajan, "Parallel Computation of Alpha Complexes for
+Biomolecules" (arXiv 1908.05944): potential simplices bottom-up (Section 4.3),
+pruning by the empty-orthosphere test AC2 (Section 4.4), Size filtration values
+(Section 2.3).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libalphac.so")
+
+AC_OK = 0
+AC_ERR_INVALID_ARG = -1
+AC_ERR_DEGENERATE = -2
+AC_ERR_RANGE = -3
+AC_ERR_CAPACITY = -4
+AC_ERR_OOM = -5
+AC_ERR_CUDA = -6
+AC_ERR_TIMEOUT = -7
+AC_ERR_STATE = -8
+AC_PRECISION_FILTERED = 0
+AC_PRECISION_PLAIN_FP64 = 1
+AC_FILTRATION_SIZE = 0
+AC_FILTRATION_ORTHOSIZE = 1
+
+# every symbol include/alphac.h declares
+EXPORTS = ["ac_create", "ac_create_batch", "ac_build", "ac_get_simplices", "ac_filtration_values", "ac_attached_flags",
+           "ac_get_candidates", "ac_eval_filtration", "ac_backward", "ac_get_stats", "ac_get_sizes", "ac_destroy",
+           "ac_error_string", "ac_last_error_detail"]
+
+
+class ac_options(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int32), ("filtration", ctypes.c_int32), ("cell_factor", ctypes.c_double),
+                ("block_warps", ctypes.c_int32), ("keep_candidates", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 8)]
+
+
+class ac_stats(ctypes.Structure):
+    _fields_ = [("n_atoms", ctypes.c_int64), ("candidates", ctypes.c_int64 * 4), ("simplices", ctypes.c_int64 * 4),
+                ("neighbour_pairs", ctypes.c_int64), ("max_degree", ctypes.c_int32), ("grid_dims", ctypes.c_int32 * 3),
+                ("ac2_tests_tet", ctypes.c_int64 * 3), ("ac2_tests_tri", ctypes.c_int64 * 3),
+                ("ac2_tests_edge", ctypes.c_int64), ("ac3_tests", ctypes.c_int64 * 4), ("ms_total", ctypes.c_double),
+                ("ms_stage", ctypes.c_double * 8), ("kernel_launches", ctypes.c_int64)]
+
+    def to_dict(self):
+        out = {}
+        for name, _ in self._fields_:
+            v = getattr(self, name)
+            out[name] = list(v) if isinstance(v, ctypes.Array) else v
+        return out
+
+
+class AlphacError(RuntimeError):
+    def __init__(self, code: int, where: str, detail: str = ""):
+        msg = f"{where}: {error_string(code)} ({code})"
+        if detail:
+            msg += f": {detail}"
+        super().__init__(msg)
+        self.code = code
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def _declare(lib):
+    vp, i64, i32, dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double
+    P = ctypes.POINTER
+    lib.ac_create.argtypes = [vp, vp, i64, dbl, P(ac_options), P(vp)]
+    lib.ac_create_batch.argtypes = [vp, vp, vp, i64, dbl, P(ac_options), P(vp)]
+    lib.ac_build.argtypes = [vp, vp]
+    lib.ac_get_simplices.argtypes = [vp, i32, i64, P(vp), P(i64)]
+    lib.ac_filtration_values.argtypes = [vp, i32, i64, P(vp), P(i64)]
+    lib.ac_attached_flags.argtypes = [vp, i32, i64, P(vp), P(i64)]
+    lib.ac_get_candidates.argtypes = [vp, i32, P(vp), P(i64)]
+    lib.ac_eval_filtration.argtypes = [vp, vp, vp, vp, vp]
+    lib.ac_backward.argtypes = [vp, vp, vp, vp, vp]
+    lib.ac_get_stats.argtypes = [vp, P(ac_stats)]
+    lib.ac_get_sizes.argtypes = [vp, P(i64), P(i64)]
+    lib.ac_destroy.argtypes = [vp]
+    lib.ac_destroy.restype = None
+    lib.ac_error_string.argtypes = [i32]
+    lib.ac_error_string.restype = ctypes.c_char_p
+    lib.ac_last_error_detail.argtypes = []
+    lib.ac_last_error_detail.restype = ctypes.c_char_p
+    for name in EXPORTS:
+        if name not in ("ac_destroy", "ac_error_string", "ac_last_error_detail"):
+            getattr(lib, name).restype = ctypes.c_int
+
+
+def lib():
+    """The loaded libalphac.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"alphac library not built: {LIB_PATH} is missing (run __graft_entry__.build())")
+            handle = ctypes.CDLL(LIB_PATH)
+            _declare(handle)
+            _lib = handle
+    return _lib
+
+
+def error_string(code: int) -> str:
+    return lib().ac_error_string(code).decode()
+
+
+def _check(rc: int, where: str):
+    if rc != AC_OK:
+        raise AlphacError(rc, where, lib().ac_last_error_detail().decode())
+
+
+def _ptr(a):
+    """Data pointer of a torch tensor or numpy array (contiguous, correct dtype expected)."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr()
+    return a.ctypes.data
+
+
+def _as_f64(a):
+    if hasattr(a, "data_ptr"):
+        import torch
+        return a.detach().to(torch.float64).contiguous()
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return torch.cuda.current_stream().cuda_stream
+        except Exception:
+            pass
+        return None
+    return getattr(stream, "cuda_stream", stream)
+
+
+class _DeviceArray:
+    """Non-owning __cuda_array_interface__ view of device memory owned by a context."""
+
+    def __init__(self, ptr, shape, typestr):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr, "data": (ptr or 0, False),
+                                         "version": 3, "strides": None}
+
+
+def options(precision=AC_PRECISION_FILTERED, filtration=AC_FILTRATION_SIZE, cell_factor=0.0, block_warps=0,
+            keep_candidates=False) -> ac_options:
+    o = ac_options()
+    o.precision = precision
+    o.filtration = filtration
+    o.cell_factor = cell_factor
+    o.block_warps = block_warps
+    o.keep_candidates = 1 if keep_candidates else 0
+    return o
+
+
+class AlphaComplex:
+    """One ac_ctx: created from centres (n,3) and radii (n,) in A and alpha in A^2.
+
+    Inputs may be numpy arrays, CPU tensors or CUDA tensors; results are CUDA
+    torch tensors (copies, unless copy=False gives views into the context).
+    """
+
+    def __init__(self, centres, radii, alpha: float = 0.0, opt: ac_options | None = None, offsets=None):
+        self._h = None
+        L = lib()
+        c = _as_f64(centres)
+        r = _as_f64(radii)
+        n = int(r.shape[0]) if len(r.shape) else 0
+        if tuple(c.shape) != (n, 3):
+            raise ValueError(f"centres must be ({n}, 3), got {tuple(c.shape)}")
+        self._keep = (c, r)
+        h = ctypes.c_void_p()
+        o = opt if opt is not None else options()
+        if offsets is None:
+            rc = L.ac_create(_ptr(c) if n else None, _ptr(r) if n else None, n, float(alpha), ctypes.byref(o),
+                             ctypes.byref(h))
+            self.n_mol = 1
+        else:
+            off = np.ascontiguousarray(offsets, dtype=np.int64)
+            rc = L.ac_create_batch(_ptr(c) if n else None, _ptr(r) if n else None, off.ctypes.data, len(off) - 1,
+                                   float(alpha), ctypes.byref(o), ctypes.byref(h))
+            self.n_mol = len(off) - 1
+        _check(rc, "ac_create")
+        self._h = h
+        self.n = n
+        self.alpha = alpha
+
+    def build(self, stream=None):
+        _check(lib().ac_build(self._h, _stream_ptr(stream)), "ac_build")
+        return self
+
+    def _view(self, getter, dim, mol, width, typestr, copy):
+        import torch
+        p = ctypes.c_void_p()
+        cnt = ctypes.c_int64()
+        _check(getter(self._h, dim, mol, ctypes.byref(p), ctypes.byref(cnt)), getter.__name__)
+        shape = (cnt.value, width) if width else (cnt.value,)
+        if cnt.value == 0:
+            dt = {"<i4": torch.int32, "<f8": torch.float64, "|u1": torch.uint8}[typestr]
+            return torch.zeros(shape, dtype=dt, device="cuda")
+        t = torch.as_tensor(_DeviceArray(p.value, shape, typestr), device="cuda")
+        return t.clone() if copy else t
+
+    def simplices(self, dim: int, mol: int = -1, copy: bool = True):
+        return self._view(lib().ac_get_simplices, dim, mol, dim + 1, "<i4", copy)
+
+    def filtration_values(self, dim: int, mol: int = -1, copy: bool = True):
+        return self._view(lib().ac_filtration_values, dim, mol, 0, "<f8", copy)
+
+    def attached(self, dim: int, mol: int = -1, copy: bool = True):
+        return self._view(lib().ac_attached_flags, dim, mol, 0, "|u1", copy)
+
+    def candidates(self, dim: int, copy: bool = True):
+        import torch
+        p = ctypes.c_void_p()
+        cnt = ctypes.c_int64()
+        _check(lib().ac_get_candidates(self._h, dim, ctypes.byref(p), ctypes.byref(cnt)), "ac_get_candidates")
+        if cnt.value == 0:
+            return torch.zeros((0, dim + 1), dtype=torch.int32, device="cuda")
+        t = torch.as_tensor(_DeviceArray(p.value, (cnt.value, dim + 1), "<i4"), device="cuda")
+        return t.clone() if copy else t
+
+    def stats(self) -> dict:
+        s = ac_stats()
+        _check(lib().ac_get_stats(self._h, ctypes.byref(s)), "ac_get_stats")
+        return s.to_dict()
+
+    def eval_filtration(self, centres, radii, stream=None):
+        """FP64 filtration values at other centres/radii (CUDA tensors), combinatorics fixed."""
+        import torch
+        c = centres.detach().to(device="cuda", dtype=torch.float64).contiguous()
+        r = radii.detach().to(device="cuda", dtype=torch.float64).contiguous()
+        outs = [torch.empty(self.count(d), dtype=torch.float64, device="cuda") for d in range(4)]
+        ptrs = (ctypes.c_void_p * 4)(*[o.data_ptr() if o.numel() else None for o in outs])
+        _check(lib().ac_eval_filtration(self._h, c.data_ptr(), r.data_ptr(), ctypes.cast(ptrs, ctypes.c_void_p),
+                                        _stream_ptr(stream)), "ac_eval_filtration")
+        return outs
+
+    def backward(self, dldf, stream=None):
+        """dL/dcentres (n,3) and dL/dradii (n,) for L = sum_d dldf[d] . f[d] (CUDA float64 tensors)."""
+        import torch
+        ws = []
+        ptrs = (ctypes.c_void_p * 4)()
+        for d in range(4):
+            w = None if dldf[d] is None else dldf[d].detach().to(device="cuda", dtype=torch.float64).contiguous()
+            ws.append(w)
+            ptrs[d] = None if (w is None or w.numel() == 0) else w.data_ptr()
+        dc = torch.empty((self.n, 3), dtype=torch.float64, device="cuda")
+        dr = torch.empty((self.n,), dtype=torch.float64, device="cuda")
+        _check(lib().ac_backward(self._h, ctypes.cast(ptrs, ctypes.c_void_p), dc.data_ptr() if self.n else None,
+                                 dr.data_ptr() if self.n else None, _stream_ptr(stream)), "ac_backward")
+        return dc, dr
+
+    def count(self, dim: int, mol: int = -1) -> int:
+        p = ctypes.c_void_p()
+        cnt = ctypes.c_int64()
+        _check(lib().ac_get_simplices(self._h, dim, mol, ctypes.byref(p), ctypes.byref(cnt)), "ac_get_simplices")
+        return cnt.value
+
+    def close(self):
+        h, self._h = self._h, None
+        if h:
+            lib().ac_destroy(h)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def alpha_complex(centres, radii, alpha: float = 0.0, stream=None, **opt) -> AlphaComplex:
+    """Create and build in one call."""
+    return AlphaComplex(centres, radii, alpha, options(**opt) if opt else None).build(stream)
+
+
+class AlphaFiltration:
+    """torch.autograd.Function: (centres, radii) -> filtration values f[0..3] (FP64, A^2).
+
+    The combinatorics (which simplices, and the source simplex of each value)
+    are fixed by the forward build; the backward is the library's FP64 kernel.
+    """
+
+    @staticmethod
+    def apply(centres, radii, alpha: float = 0.0):
+        return _alpha_filtration_fn().apply(centres, radii, alpha)
+
+
+_fn_cache = None
+
+
+def _alpha_filtration_fn():
+    global _fn_cache
+    if _fn_cache is None:
+        import torch
+
+        class _F(torch.autograd.Function):
+            @staticmethod
+            def forward(ctx, centres, radii, alpha):
+                ac = AlphaComplex(centres, radii, alpha).build()
+                ctx.ac = ac
+                ctx.dtypes = (centres.dtype, radii.dtype, centres.device)
+                return tuple(ac.filtration_values(d) for d in range(4))
+
+            @staticmethod
+            def backward(ctx, *grads):
+                dc, dr = ctx.ac.backward(list(grads))
+                cdt, rdt, dev = ctx.dtypes
+                return dc.to(device=dev, dtype=cdt), dr.to(device=dev, dtype=rdt), None
+
+        _fn_cache = _F
+    return _fn_cache

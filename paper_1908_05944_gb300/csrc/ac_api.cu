@@ -1,0 +1,564 @@
+// C-ABI entry points of alphac and the host-side orchestration of one build.
+// The stages follow the paper (arXiv 1908.05944): grid binning (Section 4.2),
+// potential simplices and pruning (Sections 4.3-4.4, Steps 1-5 of Section 3.1),
+// then canonical lists and Size filtration values (Section 2.3).
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <new>
+
+#include "ac_internal.cuh"
+
+namespace ac {
+
+static thread_local std::string g_detail;
+thread_local long long g_launch_count = 0;
+
+void set_detail(const std::string& s) { g_detail = s; }
+
+int fail(int code, const std::string& detail) {
+    g_detail = detail;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what, const char* file, int line) {
+    char buf[512];
+    snprintf(buf, sizeof(buf), "%s failed: %s (%s:%d)", what, cudaGetErrorString(e), file, line);
+    g_detail = buf;
+    return e == cudaErrorMemoryAllocation ? AC_ERR_OOM : AC_ERR_CUDA;
+}
+
+DevBuf::~DevBuf() {
+    if (p) cudaFree(p);
+}
+
+DevBuf& DevBuf::operator=(DevBuf&& o) noexcept {
+    if (this != &o) {
+        if (p) cudaFree(p);
+        p = o.p;
+        bytes = o.bytes;
+        o.p = nullptr;
+        o.bytes = 0;
+    }
+    return *this;
+}
+
+int DevBuf::reserve(size_t nbytes) {
+    if (nbytes <= bytes && p) return AC_OK;
+    if (p) {
+        cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+    }
+    size_t want = nbytes < 256 ? 256 : nbytes;
+    cudaError_t e = cudaMalloc(&p, want);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        p = nullptr;
+        char buf[128];
+        snprintf(buf, sizeof(buf), "cudaMalloc of %zu bytes failed", want);
+        return fail(AC_ERR_OOM, buf);
+    }
+    bytes = want;
+    return AC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// exclusive scan (n inputs -> n + 1 outputs, out[n] = total); in may alias out
+
+template <class T>
+__device__ inline T warp_incl_scan(T v) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        T t = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += t;
+    }
+    return v;
+}
+
+constexpr int SCAN_THREADS = 512;
+constexpr int SCAN_ITEMS = 8;
+constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
+
+template <class T>
+__device__ T block_excl_scan(T v, T* total) {
+    __shared__ T warp_sums[SCAN_THREADS / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    T inc = warp_incl_scan(v);
+    if (lane == 31) warp_sums[wid] = inc;
+    __syncthreads();
+    if (wid == 0) {
+        T w = lane < SCAN_THREADS / 32 ? warp_sums[lane] : T(0);
+        T wi = warp_incl_scan(w);
+        if (lane < SCAN_THREADS / 32) warp_sums[lane] = wi - w;
+        if (lane == SCAN_THREADS / 32 - 1) *total = wi;
+    }
+    __syncthreads();
+    T r = inc - v + warp_sums[wid];
+    __syncthreads();
+    return r;
+}
+
+template <class T>
+__global__ void k_scan_reduce(const T* in, int64_t n, T* partial) {
+    int64_t base = (int64_t)blockIdx.x * SCAN_TILE;
+    T s = 0;
+    for (int k = 0; k < SCAN_ITEMS; k++) {
+        int64_t i = base + (int64_t)k * SCAN_THREADS + threadIdx.x;
+        if (i < n) s += in[i];
+    }
+    __shared__ T tot;
+    block_excl_scan<T>(s, &tot);
+    if (threadIdx.x == 0) partial[blockIdx.x] = tot;
+}
+
+template <class T>
+__global__ void k_scan_apply(const T* in, T* out, int64_t n, const T* partial_excl) {
+    int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
+    T v[SCAN_ITEMS];
+    T s = 0;
+    for (int k = 0; k < SCAN_ITEMS; k++) {
+        int64_t i = base + k;
+        v[k] = i < n ? in[i] : T(0);
+        s += v[k];
+    }
+    __shared__ T tot;
+    T pre = block_excl_scan<T>(s, &tot) + partial_excl[blockIdx.x];
+    for (int k = 0; k < SCAN_ITEMS; k++) {
+        int64_t i = base + k;
+        if (i < n) out[i] = pre;
+        pre += v[k];
+    }
+    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) out[n] = partial_excl[blockIdx.x] + tot;
+}
+
+template <class T>
+static int scan_impl(const T* in, T* out, int64_t n, DevBuf& tmp, size_t tmp_off, cudaStream_t s) {
+    if (n <= 0) {
+        AC_CUDA(cudaMemsetAsync(out, 0, sizeof(T), s));
+        return AC_OK;
+    }
+    int64_t nb = (n + SCAN_TILE - 1) / SCAN_TILE;
+    size_t need = tmp_off + sizeof(T) * (size_t)(nb + 1);
+    // the recursion nests partial arrays after each other in tmp; reserve generously up front
+    if (need > tmp.bytes) return fail(AC_ERR_OOM, "scan scratch too small");
+    T* partial = reinterpret_cast<T*>(static_cast<char*>(tmp.p) + tmp_off);
+    if (nb == 1) {
+        // one tile: the block offset is zero
+        AC_CUDA(cudaMemsetAsync(partial, 0, sizeof(T), s));
+    } else {
+        k_scan_reduce<T><<<(unsigned)nb, SCAN_THREADS, 0, s>>>(in, n, partial);
+        AC_LAUNCHED();
+        size_t next_off = tmp_off + ((sizeof(T) * (size_t)(nb + 1) + 255) & ~(size_t)255);
+        AC_TRY(scan_impl<T>(partial, partial, nb, tmp, next_off, s));
+    }
+    k_scan_apply<T><<<(unsigned)nb, SCAN_THREADS, 0, s>>>(in, out, n, partial);
+    AC_LAUNCHED();
+    return AC_OK;
+}
+
+template <class T>
+static int scan_entry(const T* in, T* out, int64_t n, DevBuf& tmp, cudaStream_t s) {
+    size_t need = 0;
+    for (int64_t m = n; m > 0; m = (m + SCAN_TILE - 1) / SCAN_TILE) {
+        int64_t nb = (m + SCAN_TILE - 1) / SCAN_TILE;
+        need += ((sizeof(T) * (size_t)(nb + 1) + 255) & ~(size_t)255);
+        if (nb == 1) break;
+    }
+    AC_TRY(tmp.reserve(need + 256));
+    return scan_impl<T>(in, out, n, tmp, 0, s);
+}
+
+int scan_exclusive_i64(const int64_t* in, int64_t* out, int64_t n, DevBuf& tmp, cudaStream_t s) {
+    return scan_entry<long long>(reinterpret_cast<const long long*>(in), reinterpret_cast<long long*>(out), n, tmp, s);
+}
+
+int scan_exclusive_u32_to_u32(const uint32_t* in, uint32_t* out, int64_t n, DevBuf& tmp, cudaStream_t s) {
+    return scan_entry<unsigned>(in, out, n, tmp, s);
+}
+
+int read_counters(ac_ctx* c, DevCounters* h, cudaStream_t s) {
+    AC_CUDA(cudaMemcpyAsync(h, c->counters.p, sizeof(DevCounters), cudaMemcpyDeviceToHost, s));
+    AC_CUDA(cudaStreamSynchronize(s));
+    return AC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// quantisation (input order) and per-molecule bounding boxes
+
+__global__ void k_quantise(const double* __restrict__ centres, const double* __restrict__ radii, int64_t n,
+                           const int32_t* __restrict__ mol_of, int4* __restrict__ P, int32_t* __restrict__ bbox,
+                           int* __restrict__ wmax, DevCounters* cnt) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double x = centres[3 * i], y = centres[3 * i + 1], z = centres[3 * i + 2], r = radii[i];
+    bool finite = isfinite(x) && isfinite(y) && isfinite(z) && isfinite(r);
+    if (!finite || !(r > 0.0)) {
+        atomicOr(&cnt->err, DERR_INVALID);
+        atomicMin(&cnt->bad_index, (int)i);
+        return;
+    }
+    const double lim = 1048576.0;  // |x| <= 2^20 A keeps quantised coordinates within 2^30
+    if (fabs(x) > lim || fabs(y) > lim || fabs(z) > lim || r > 64.0) {
+        atomicOr(&cnt->err, DERR_RANGE);
+        atomicMin(&cnt->bad_index, (int)i);
+        return;
+    }
+    int X = __double2int_rn(x * 1024.0), Y = __double2int_rn(y * 1024.0), Z = __double2int_rn(z * 1024.0);
+    int R = __double2int_rn(r * 1024.0);
+    if (R < 1) {
+        atomicOr(&cnt->err, DERR_RANGE);
+        atomicMin(&cnt->bad_index, (int)i);
+        return;
+    }
+    if (R > 4096) {  // radius above 4 A: W would leave the 2^24 range of the predicates
+        atomicOr(&cnt->err, DERR_RANGE);
+        atomicMin(&cnt->bad_index, (int)i);
+        return;
+    }
+    int W = R * R;
+    P[i] = make_int4(X, Y, Z, W);
+    atomicMax(wmax, W);
+    int m = mol_of[i];
+    int32_t* b = bbox + 6 * m;
+    atomicMin(&b[0], X);
+    atomicMin(&b[1], Y);
+    atomicMin(&b[2], Z);
+    atomicMax(&b[3], X);
+    atomicMax(&b[4], Y);
+    atomicMax(&b[5], Z);
+}
+
+__global__ void k_fill_mol(const int64_t* __restrict__ mol_off, int64_t n_mol, int32_t* __restrict__ mol_of) {
+    int64_t m = blockIdx.x;
+    if (m >= n_mol) return;
+    for (int64_t i = mol_off[m] + threadIdx.x; i < mol_off[m + 1]; i += blockDim.x) mol_of[i] = (int32_t)m;
+}
+
+__global__ void k_init_bbox(int32_t* bbox, int64_t n_mol) {
+    int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= n_mol) return;
+    for (int k = 0; k < 3; k++) {
+        bbox[6 * m + k] = INT32_MAX;
+        bbox[6 * m + 3 + k] = INT32_MIN;
+    }
+}
+
+// Quantise the stored inputs (row a1: X = round(1024 x), W = round(1024 r)^2),
+// check their ranges, and lay out the per-molecule grids (Section 4.2): cell
+// side ~ h = sqrt(r_max^2 + alpha), dense cell table over each bounding box.
+int quantise_and_plan(ac_ctx* c, cudaStream_t s) {
+    const int64_t n = c->n, n_mol = c->n_mol;
+    AC_TRY(c->scratch[0].reserve((size_t)n_mol * 6 * sizeof(int32_t)));
+    AC_TRY(c->scratch[1].reserve(sizeof(int)));
+    DevCounters* dc = c->counters.as<DevCounters>();
+    AC_CUDA(cudaMemsetAsync(dc, 0, sizeof(DevCounters), s));
+    const int big = INT32_MAX;
+    AC_CUDA(cudaMemcpyAsync(&dc->bad_index, &big, sizeof(int), cudaMemcpyHostToDevice, s));
+    int32_t* bbox = c->scratch[0].as<int32_t>();
+    int* wmax = c->scratch[1].as<int>();
+    AC_CUDA(cudaMemsetAsync(wmax, 0, sizeof(int), s));
+    k_init_bbox<<<(unsigned)((n_mol + 255) / 256), 256, 0, s>>>(bbox, n_mol);
+    AC_LAUNCHED();
+    if (n > 0) {
+        k_quantise<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(c->centres.as<double>(), c->radii.as<double>(), n,
+                                                              c->mol_of.as<int32_t>(), c->P.as<int4>(), bbox, wmax, dc);
+        AC_LAUNCHED();
+    }
+    DevCounters hc;
+    AC_TRY(read_counters(c, &hc, s));
+    if (hc.err & DERR_INVALID) {
+        char b[128];
+        snprintf(b, sizeof(b), "atom %d: non-finite value or radius <= 0", hc.bad_index);
+        return fail(AC_ERR_INVALID_ARG, b);
+    }
+    if (hc.err & DERR_RANGE) {
+        char b[160];
+        snprintf(b, sizeof(b), "atom %d: |coordinate| > 2^20 A or radius outside (0, 4] A after quantisation",
+                 hc.bad_index);
+        return fail(AC_ERR_RANGE, b);
+    }
+    int wmax_h = 0;
+    std::vector<int32_t> hb((size_t)n_mol * 6);
+    AC_CUDA(cudaMemcpyAsync(&wmax_h, wmax, sizeof(int), cudaMemcpyDeviceToHost, s));
+    AC_CUDA(cudaMemcpyAsync(hb.data(), bbox, hb.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    AC_CUDA(cudaStreamSynchronize(s));
+
+    PredConst& pc = c->pc;
+    pc.A = (int64_t)nearbyint(c->alpha * 1048576.0);
+    pc.H2 = (int64_t)wmax_h + pc.A;
+    if (pc.H2 > ((int64_t)1 << 24)) return fail(AC_ERR_RANGE, "r_max^2 + alpha exceeds 16 A^2");
+    pc.precision = c->opt.precision;
+    pc.keep_candidates = c->opt.keep_candidates ? 1 : 0;
+    int64_t hq = 0;  // ceil(sqrt(H2)) in quanta
+    if (pc.H2 > 0) {
+        hq = (int64_t)floor(sqrt((double)pc.H2));
+        while (hq * hq < pc.H2) hq++;
+    }
+    pc.h_f = (float)hq;
+    pc.h_d = (double)hq;
+    int64_t cell = (int64_t)ceil(c->opt.cell_factor * (double)(hq > 0 ? hq : 1024));
+    if (cell < 1) cell = 1;
+    // grid dims; coarsen if the dense table would be far larger than the atom count
+    std::vector<MolGrid> grids((size_t)n_mol);
+    int64_t total = 0;
+    for (int iter = 0; iter < 40; iter++) {
+        total = 0;
+        for (int64_t m = 0; m < n_mol; m++) {
+            MolGrid& g = grids[(size_t)m];
+            bool empty = c->mol_off[(size_t)m + 1] == c->mol_off[(size_t)m];
+            for (int k = 0; k < 3; k++) {
+                g.org[k] = empty ? 0 : hb[(size_t)(6 * m + k)];
+                int64_t span = empty ? 0 : (int64_t)hb[(size_t)(6 * m + 3 + k)] - hb[(size_t)(6 * m + k)];
+                g.dims[k] = (int32_t)(span / cell + 1);
+            }
+            g.cell_base = total;
+            total += (int64_t)g.dims[0] * g.dims[1] * g.dims[2];
+        }
+        if (total <= 16 * n + (1 << 22)) break;
+        cell *= 2;
+    }
+    pc.cell = (int32_t)cell;
+    pc.reach = hq > 0 ? (int32_t)((2 * hq + cell - 1) / cell) : 1;
+    if (pc.reach < 1) pc.reach = 1;
+    c->n_cells = total;
+    AC_TRY(c->grids.reserve((size_t)n_mol * sizeof(MolGrid)));
+    AC_CUDA(cudaMemcpyAsync(c->grids.p, grids.data(), (size_t)n_mol * sizeof(MolGrid), cudaMemcpyHostToDevice, s));
+    AC_CUDA(cudaStreamSynchronize(s));
+    c->stats.grid_dims[0] = grids[0].dims[0];
+    c->stats.grid_dims[1] = grids[0].dims[1];
+    c->stats.grid_dims[2] = grids[0].dims[2];
+    c->stats.n_atoms = n;
+    return AC_OK;
+}
+
+}  // namespace ac
+
+using namespace ac;
+
+// ---------------------------------------------------------------------------
+// public API
+
+static int create_impl(const double* centres, const double* radii, const int64_t* offsets, int64_t n_mol,
+                       double alpha, const ac_options* opt, ac_ctx** out) {
+    if (!out) return fail(AC_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (n_mol < 1 || !offsets) return fail(AC_ERR_INVALID_ARG, "need at least one molecule");
+    if (offsets[0] != 0) return fail(AC_ERR_INVALID_ARG, "offsets[0] must be 0");
+    for (int64_t m = 0; m < n_mol; m++)
+        if (offsets[m + 1] < offsets[m]) return fail(AC_ERR_INVALID_ARG, "offsets must be non-decreasing");
+    int64_t n = offsets[n_mol];
+    if (n < 0 || n >= ((int64_t)1 << 31) - 1) return fail(AC_ERR_INVALID_ARG, "n out of range");
+    if (n > 0 && (!centres || !radii)) return fail(AC_ERR_INVALID_ARG, "centres/radii NULL");
+    if (!isfinite(alpha)) return fail(AC_ERR_INVALID_ARG, "alpha not finite");
+    if (fabs(alpha) > 16.0) return fail(AC_ERR_RANGE, "|alpha| must be at most 16 A^2");
+
+    ac_ctx* c = new (std::nothrow) ac_ctx();
+    if (!c) return fail(AC_ERR_OOM, "host allocation failed");
+    c->n = n;
+    c->n_mol = n_mol;
+    c->mol_off.assign(offsets, offsets + n_mol + 1);
+    c->alpha = alpha;
+    if (opt) c->opt = *opt;
+    if (c->opt.cell_factor <= 0.0) c->opt.cell_factor = 1.0;
+    if (c->opt.block_warps <= 0) c->opt.block_warps = 8;
+    if (c->opt.precision != AC_PRECISION_FILTERED && c->opt.precision != AC_PRECISION_PLAIN_FP64) {
+        delete c;
+        return fail(AC_ERR_INVALID_ARG, "unknown precision mode");
+    }
+    int rc = AC_OK;
+    cudaStream_t s = 0;
+    auto bail = [&](int code) {
+        ac_destroy(c);
+        return code;
+    };
+    for (int k = 0; k < 10; k++)
+        if (cudaEventCreate(&c->ev[k]) != cudaSuccess) return bail(cuda_fail(cudaGetLastError(), "cudaEventCreate", __FILE__, __LINE__));
+
+    size_t nn = (size_t)(n > 0 ? n : 1);
+    if ((rc = c->centres.reserve(nn * 3 * sizeof(double))) || (rc = c->radii.reserve(nn * sizeof(double))) ||
+        (rc = c->P.reserve(nn * sizeof(int4))) || (rc = c->mol_of.reserve(nn * sizeof(int32_t))) ||
+        (rc = c->d_moloff.reserve((size_t)(n_mol + 1) * sizeof(int64_t))) ||
+        (rc = c->counters.reserve(sizeof(DevCounters))))
+        return bail(rc);
+    if (n > 0) {
+        if (cudaMemcpy(c->centres.p, centres, (size_t)n * 3 * sizeof(double), cudaMemcpyDefault) != cudaSuccess ||
+            cudaMemcpy(c->radii.p, radii, (size_t)n * sizeof(double), cudaMemcpyDefault) != cudaSuccess)
+            return bail(cuda_fail(cudaGetLastError(), "copy of centres/radii", __FILE__, __LINE__));
+    }
+    if (cudaMemcpy(c->d_moloff.p, offsets, (size_t)(n_mol + 1) * sizeof(int64_t), cudaMemcpyHostToDevice) != cudaSuccess)
+        return bail(cuda_fail(cudaGetLastError(), "copy of offsets", __FILE__, __LINE__));
+
+    k_fill_mol<<<(unsigned)n_mol, 256, 0, s>>>(c->d_moloff.as<int64_t>(), n_mol, c->mol_of.as<int32_t>());
+    if (cudaGetLastError() != cudaSuccess) return bail(cuda_fail(cudaGetLastError(), "k_fill_mol", __FILE__, __LINE__));
+    if ((rc = quantise_and_plan(c, s))) return bail(rc);
+    *out = c;
+    return AC_OK;
+}
+
+extern "C" int ac_create(const double* centres, const double* radii, int64_t n, double alpha, const ac_options* opt,
+                         ac_ctx** out) {
+    if (!out) return fail(AC_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (n < 0) return fail(AC_ERR_INVALID_ARG, "n < 0");
+    int64_t off[2] = {0, n};
+    return create_impl(centres, radii, off, 1, alpha, opt, out);
+}
+
+extern "C" int ac_create_batch(const double* centres, const double* radii, const int64_t* offsets, int64_t n_mol,
+                               double alpha, const ac_options* opt, ac_ctx** out) {
+    return create_impl(centres, radii, offsets, n_mol, alpha, opt, out);
+}
+
+static float elapsed(cudaEvent_t a, cudaEvent_t b) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, a, b);
+    return ms;
+}
+
+extern "C" int ac_build(ac_ctx* c, void* stream) {
+    if (!c) return fail(AC_ERR_INVALID_ARG, "ctx is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    c->built = false;
+    const long long launches0 = g_launch_count;
+    AC_CUDA(cudaEventRecord(c->ev[0], s));
+    AC_TRY(quantise_and_plan(c, s));
+    AC_TRY(build_grid(c, s));
+    AC_CUDA(cudaEventRecord(c->ev[1], s));
+    AC_TRY(build_neighbours(c, s));
+    AC_CUDA(cudaEventRecord(c->ev[2], s));
+    AC_TRY(run_local(c, s));
+    AC_CUDA(cudaEventRecord(c->ev[3], s));
+    AC_TRY(canonicalise(c, s));
+    AC_CUDA(cudaEventRecord(c->ev[6], s));
+    AC_TRY(compute_filtration(c, s));
+    AC_CUDA(cudaEventRecord(c->ev[7], s));
+    AC_CUDA(cudaEventSynchronize(c->ev[7]));
+    DevCounters h;
+    AC_TRY(read_counters(c, &h, s));
+    ac_stats& st = c->stats;
+    st.n_atoms = c->n;
+    st.candidates[0] = 0;
+    for (int d = 1; d < 4; d++) st.candidates[d] = (int64_t)h.n_cand[d];
+    for (int d = 0; d < 4; d++) st.simplices[d] = c->K[d].count;
+    st.neighbour_pairs = c->nb_total;
+    st.max_degree = h.max_degree;
+    for (int k = 0; k < 3; k++) {
+        st.ac2_tests_tet[k] = (int64_t)h.ac2_tet[k];
+        st.ac2_tests_tri[k] = (int64_t)h.ac2_tri[k];
+    }
+    st.ac2_tests_edge = (int64_t)h.ac2_edge;
+    for (int d = 0; d < 4; d++) st.ac3_tests[d] = (int64_t)h.ac3[d];
+    st.ms_stage[0] = elapsed(c->ev[0], c->ev[1]);
+    st.ms_stage[1] = elapsed(c->ev[1], c->ev[2]);
+    st.ms_stage[2] = elapsed(c->ev[2], c->ev[3]);
+    st.ms_stage[3] = elapsed(c->ev[3], c->ev[4]);
+    st.ms_stage[4] = elapsed(c->ev[4], c->ev[5]);
+    st.ms_stage[5] = elapsed(c->ev[5], c->ev[6]);
+    st.ms_stage[6] = elapsed(c->ev[6], c->ev[7]);
+    st.ms_stage[7] = c->n > 0 ? elapsed(c->ev[8], c->ev[9]) : 0.0;  // last launch of the per-atom kernel
+    st.ms_total = elapsed(c->ev[0], c->ev[7]);
+    st.kernel_launches = g_launch_count - launches0;
+    c->built = true;
+    return AC_OK;
+}
+
+static int get_list(ac_ctx* c, ac::SimplexList* L, int dim, int64_t mol, int64_t* first, int64_t* count) {
+    if (!c || dim < 0 || dim > 3 || !count) return fail(AC_ERR_INVALID_ARG, "bad argument");
+    if (!c->built) return fail(AC_ERR_STATE, "no successful ac_build on this context");
+    int64_t m = mol < 0 ? 0 : mol;
+    if (mol < -1 || m >= c->n_mol || (mol == -1 && c->n_mol != 1))
+        return fail(AC_ERR_INVALID_ARG, "molecule index out of range");
+    ac::SimplexList& S = L[dim];
+    *first = S.mol_off.empty() ? 0 : S.mol_off[(size_t)m];
+    *count = S.mol_off.empty() ? 0 : S.mol_off[(size_t)m + 1] - S.mol_off[(size_t)m];
+    return AC_OK;
+}
+
+extern "C" int ac_get_simplices(ac_ctx* c, int dim, int64_t mol, const int32_t** d_tuples, int64_t* count) {
+    int64_t first = 0;
+    AC_TRY(get_list(c, c ? c->K : nullptr, dim, mol, &first, count));
+    if (!d_tuples) return fail(AC_ERR_INVALID_ARG, "d_tuples is NULL");
+    *d_tuples = c->K[dim].tuples.as<int32_t>() + first * (dim + 1);
+    return AC_OK;
+}
+
+extern "C" int ac_filtration_values(ac_ctx* c, int dim, int64_t mol, const double** d_f, int64_t* count) {
+    int64_t first = 0;
+    AC_TRY(get_list(c, c ? c->K : nullptr, dim, mol, &first, count));
+    if (!d_f) return fail(AC_ERR_INVALID_ARG, "d_f is NULL");
+    const ac::DevBuf& b = c->opt.filtration == AC_FILTRATION_ORTHOSIZE ? c->K[dim].orthosize : c->K[dim].f;
+    *d_f = b.as<double>() + first;
+    return AC_OK;
+}
+
+extern "C" int ac_attached_flags(ac_ctx* c, int dim, int64_t mol, const uint8_t** d_flags, int64_t* count) {
+    int64_t first = 0;
+    AC_TRY(get_list(c, c ? c->K : nullptr, dim, mol, &first, count));
+    if (!d_flags) return fail(AC_ERR_INVALID_ARG, "d_flags is NULL");
+    *d_flags = c->K[dim].attached.as<uint8_t>() + first;
+    return AC_OK;
+}
+
+extern "C" int ac_get_candidates(ac_ctx* c, int dim, const int32_t** d_tuples, int64_t* count) {
+    if (!c || dim < 1 || dim > 3 || !d_tuples || !count) return fail(AC_ERR_INVALID_ARG, "bad argument");
+    if (!c->built) return fail(AC_ERR_STATE, "no successful ac_build on this context");
+    if (!c->opt.keep_candidates || c->n_mol != 1) return fail(AC_ERR_STATE, "context does not keep candidates");
+    *d_tuples = c->C[dim].tuples.as<int32_t>();
+    *count = c->C[dim].count;
+    return AC_OK;
+}
+
+extern "C" int ac_eval_filtration(ac_ctx* c, const double* d_centres, const double* d_radii, double* const d_f_out[4],
+                                  void* stream) {
+    if (!c || !d_centres || !d_radii || !d_f_out) return fail(AC_ERR_INVALID_ARG, "bad argument");
+    if (!c->built) return fail(AC_ERR_STATE, "no successful ac_build on this context");
+    return eval_filtration(c, d_centres, d_radii, d_f_out, (cudaStream_t)stream);
+}
+
+extern "C" int ac_backward(ac_ctx* c, const double* const d_dLdf[4], double* d_dLdcentres, double* d_dLdradii,
+                           void* stream) {
+    if (!c || !d_dLdf || !d_dLdcentres || !d_dLdradii) return fail(AC_ERR_INVALID_ARG, "bad argument");
+    if (!c->built) return fail(AC_ERR_STATE, "no successful ac_build on this context");
+    return backward(c, d_dLdf, d_dLdcentres, d_dLdradii, (cudaStream_t)stream);
+}
+
+extern "C" int ac_get_stats(ac_ctx* c, ac_stats* out) {
+    if (!c || !out) return fail(AC_ERR_INVALID_ARG, "bad argument");
+    *out = c->stats;
+    return AC_OK;
+}
+
+extern "C" int ac_get_sizes(ac_ctx* c, int64_t* n_mol, int64_t* n_atoms) {
+    if (!c) return fail(AC_ERR_INVALID_ARG, "ctx is NULL");
+    if (n_mol) *n_mol = c->n_mol;
+    if (n_atoms) *n_atoms = c->n;
+    return AC_OK;
+}
+
+extern "C" void ac_destroy(ac_ctx* c) {
+    if (!c) return;
+    for (int k = 0; k < 10; k++)
+        if (c->ev[k]) cudaEventDestroy(c->ev[k]);
+    delete c;
+}
+
+extern "C" const char* ac_error_string(int code) {
+    switch (code) {
+        case AC_OK: return "ok";
+        case AC_ERR_INVALID_ARG: return "invalid argument";
+        case AC_ERR_DEGENERATE: return "degenerate input (coincident centres)";
+        case AC_ERR_RANGE: return "input outside the exact-integer range";
+        case AC_ERR_CAPACITY: return "internal list capacity exceeded";
+        case AC_ERR_OOM: return "out of device memory";
+        case AC_ERR_CUDA: return "CUDA runtime error";
+        case AC_ERR_TIMEOUT: return "bounded device wait timed out";
+        case AC_ERR_STATE: return "no results: call ac_build first";
+        default: return "unknown error";
+    }
+}
+
+extern "C" const char* ac_last_error_detail(void) { return g_detail.c_str(); }

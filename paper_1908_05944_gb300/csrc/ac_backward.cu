@@ -1,0 +1,140 @@
+// Differentiation of the filtration values with the combinatorics held fixed.
+//
+// Every simplex sigma of the complex takes its value from a source simplex s:
+// itself when its orthocentre is its closest witness, else the coface whose
+// orthocentre is (Section 2.3; the attached case of the proofs of Lemmas 1-2).
+// f(sigma) = OrthoSize(s) = min pi(x, b_v0) over the affine set where all
+// vertices of s have equal power. With multipliers mu on the equal-power
+// constraints the stationarity condition puts the minimiser at
+// c = sum_k lambda_k p_k (lambda_0 = 1 - sum mu, lambda_k = mu_k: barycentric
+// coordinates of c in aff(s)), and the Lagrangian is sum_k lambda_k pi(c, b_k).
+// The envelope theorem then gives
+//   dOrthoSize/dp_k = 2 lambda_k (p_k - c),  dOrthoSize/dr_k = -2 r_k lambda_k.
+// Everything here is FP64 on the caller's continuous inputs.
+#include "ac_internal.cuh"
+
+namespace ac {
+
+struct Ortho {
+    double lam[4];
+    double c[3];
+    double value;
+};
+
+// Orthocentre, barycentric coordinates and OrthoSize of K vertices (global input
+// indices, ascending) from FP64 centres (n x 3) and radii.
+__device__ Ortho ortho_fp64(const double* __restrict__ X, const double* __restrict__ R, const int4& t, int K) {
+    Ortho o;
+    const int v[4] = {t.x, t.y, t.z, t.w};
+    const double p0[3] = {X[3 * v[0]], X[3 * v[0] + 1], X[3 * v[0] + 2]};
+    const double w0 = R[v[0]] * R[v[0]];
+    double q[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}}, a[3] = {0, 0, 0};
+    for (int k = 1; k < K; k++) {
+        double wk = R[v[k]] * R[v[k]];
+        for (int c = 0; c < 3; c++) q[k - 1][c] = X[3 * v[k] + c] - p0[c];
+        a[k - 1] = q[k - 1][0] * q[k - 1][0] + q[k - 1][1] * q[k - 1][1] + q[k - 1][2] * q[k - 1][2] - wk + w0;
+    }
+    const int d = K - 1;
+    double G[3][3];
+    for (int i = 0; i < d; i++)
+        for (int j = 0; j < d; j++) G[i][j] = q[i][0] * q[j][0] + q[i][1] * q[j][1] + q[i][2] * q[j][2];
+    double mu[3] = {0, 0, 0};
+    if (d == 1) {
+        mu[0] = a[0] / (2.0 * G[0][0]);
+    } else if (d == 2) {
+        double det = G[0][0] * G[1][1] - G[0][1] * G[1][0];
+        mu[0] = (G[1][1] * a[0] - G[0][1] * a[1]) / (2.0 * det);
+        mu[1] = (G[0][0] * a[1] - G[1][0] * a[0]) / (2.0 * det);
+    } else if (d == 3) {
+        double adj[3][3];
+        for (int i = 0; i < 3; i++)
+            for (int j = 0; j < 3; j++) {
+                int r0 = (i + 1) % 3, r1 = (i + 2) % 3, c0 = (j + 1) % 3, c1 = (j + 2) % 3;
+                adj[j][i] = G[r0][c0] * G[r1][c1] - G[r0][c1] * G[r1][c0];
+            }
+        double det = G[0][0] * adj[0][0] + G[0][1] * adj[1][0] + G[0][2] * adj[2][0];
+        for (int i = 0; i < 3; i++) mu[i] = (adj[i][0] * a[0] + adj[i][1] * a[1] + adj[i][2] * a[2]) / (2.0 * det);
+    }
+    double y[3] = {0, 0, 0};
+    for (int k = 0; k < d; k++)
+        for (int c = 0; c < 3; c++) y[c] += mu[k] * q[k][c];
+    double s = 1.0;
+    for (int k = 0; k < d; k++) {
+        o.lam[k + 1] = mu[k];
+        s -= mu[k];
+    }
+    o.lam[0] = s;
+    for (int c = 0; c < 3; c++) o.c[c] = p0[c] + y[c];
+    o.value = y[0] * y[0] + y[1] * y[1] + y[2] * y[2] - w0;
+    return o;
+}
+
+__global__ void k_eval(const double* __restrict__ X, const double* __restrict__ R, const int8_t* __restrict__ sdim,
+                       const int64_t* __restrict__ sidx, int64_t m, const int4* const* __restrict__ G,
+                       double* __restrict__ out) {
+    int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= m) return;
+    const int d = sdim[j];
+    const int4 t = G[d][sidx[j]];
+    out[j] = ortho_fp64(X, R, t, d + 1).value;
+}
+
+__global__ void k_backward(const double* __restrict__ X, const double* __restrict__ R, const int8_t* __restrict__ sdim,
+                           const int64_t* __restrict__ sidx, int64_t m, const int4* const* __restrict__ G,
+                           const double* __restrict__ w, double* __restrict__ dX, double* __restrict__ dR) {
+    int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= m) return;
+    const double wj = w[j];
+    if (wj == 0.0) return;
+    const int d = sdim[j];
+    const int4 t = G[d][sidx[j]];
+    const Ortho o = ortho_fp64(X, R, t, d + 1);
+    const int v[4] = {t.x, t.y, t.z, t.w};
+    for (int k = 0; k <= d; k++) {
+        const int a = v[k];
+        const double l2 = 2.0 * wj * o.lam[k];
+        for (int c = 0; c < 3; c++) atomicAdd(&dX[3 * a + c], l2 * (X[3 * a + c] - o.c[c]));
+        atomicAdd(&dR[a], -l2 * R[a]);
+    }
+}
+
+static int gtable(ac_ctx* c, DevBuf& tab, cudaStream_t s) {
+    const int4* h[4];
+    for (int d = 0; d < 4; d++) h[d] = c->Gbuf[d].as<int4>();
+    AC_TRY(tab.reserve(sizeof(h)));
+    AC_CUDA(cudaMemcpyAsync(tab.p, h, sizeof(h), cudaMemcpyHostToDevice, s));
+    return AC_OK;
+}
+
+int eval_filtration(ac_ctx* c, const double* centres, const double* radii, double* const f_out[4], cudaStream_t s) {
+    AC_TRY(gtable(c, c->scratch[5], s));
+    for (int d = 0; d < 4; d++) {
+        const int64_t m = c->K[d].count;
+        if (!f_out[d] || m == 0) continue;
+        k_eval<<<(unsigned)((m + 127) / 128), 128, 0, s>>>(centres, radii, c->K[d].src_dim.as<int8_t>(),
+                                                           c->K[d].src_idx.as<int64_t>(), m,
+                                                           c->scratch[5].as<const int4*>(), f_out[d]);
+        AC_LAUNCHED();
+    }
+    AC_CUDA(cudaStreamSynchronize(s));
+    return AC_OK;
+}
+
+int backward(ac_ctx* c, const double* const dldf[4], double* dc, double* dr, cudaStream_t s) {
+    AC_TRY(gtable(c, c->scratch[5], s));
+    const int64_t n = c->n;
+    AC_CUDA(cudaMemsetAsync(dc, 0, (size_t)(n > 0 ? n : 0) * 3 * sizeof(double), s));
+    AC_CUDA(cudaMemsetAsync(dr, 0, (size_t)(n > 0 ? n : 0) * sizeof(double), s));
+    for (int d = 0; d < 4; d++) {
+        const int64_t m = c->K[d].count;
+        if (!dldf[d] || m == 0) continue;
+        k_backward<<<(unsigned)((m + 127) / 128), 128, 0, s>>>(c->centres.as<double>(), c->radii.as<double>(),
+                                                               c->K[d].src_dim.as<int8_t>(), c->K[d].src_idx.as<int64_t>(),
+                                                               m, c->scratch[5].as<const int4*>(), dldf[d], dc, dr);
+        AC_LAUNCHED();
+    }
+    AC_CUDA(cudaStreamSynchronize(s));
+    return AC_OK;
+}
+
+}  // namespace ac

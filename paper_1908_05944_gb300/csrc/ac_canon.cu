@@ -1,0 +1,561 @@
+// Canonical simplex lists and filtration values.
+//
+// Steps 3-5 of Section 3.1 (arXiv 1908.05944): K^d is the set of facets of
+// K^(d+1) together with the simplices of Sigma_ortho^d that pass AC2 at their
+// orthocentre. The per-atom pass emitted the latter; here both sources are
+// mapped to input indices, each tuple sorted ascending, bucketed by its first
+// vertex (counting sort over input indices), sorted and de-duplicated inside
+// each bucket. A simplex that arrives only as a facet fails AC2 at its own
+// orthocentre: it is "attached".
+//
+// Filtration value Size (Section 2.3): an unattached simplex's closest witness
+// is its orthocentre, so Size = OrthoSize; an attached simplex's closest
+// witness lies on a face of its witness region, i.e. it is a witness of a
+// coface with the same Size (the argument of Lemmas 1 and 2), so Size is the
+// smallest Size of its cofaces one dimension up. Ties pick the coface that
+// comes first in lexicographic order. OrthoSize is an exact rational of
+// 128-bit integers, converted to FP64 with three roundings (relative error
+// below 4 * 2^-53).
+#include <math.h>
+
+#include "ac_internal.cuh"
+
+namespace ac {
+
+// ---------------------------------------------------------------------------
+// helpers
+
+__device__ __forceinline__ void sort_asc(int4& t, int K) {
+    // tiny sorting network on the first K components
+    auto cs = [](int& a, int& b) {
+        if (a > b) {
+            int x = a;
+            a = b;
+            b = x;
+        }
+    };
+    if (K == 2) {
+        cs(t.x, t.y);
+    } else if (K == 3) {
+        cs(t.x, t.y);
+        cs(t.y, t.z);
+        cs(t.x, t.y);
+    } else {
+        cs(t.x, t.y);
+        cs(t.z, t.w);
+        cs(t.x, t.z);
+        cs(t.y, t.w);
+        cs(t.y, t.z);
+    }
+}
+
+__device__ __forceinline__ bool less_rest(const int4& a, const int4& b) {
+    if (a.y != b.y) return a.y < b.y;
+    if (a.z != b.z) return a.z < b.z;
+    return a.w < b.w;
+}
+
+__device__ __forceinline__ bool same(const int4& a, const int4& b) {
+    return a.x == b.x && a.y == b.y && a.z == b.z && a.w == b.w;
+}
+
+// Unused tuple slots hold -1 so comparisons ignore them.
+__device__ __forceinline__ int4 facet_of(const int4& t, int K, int drop) {
+    // t has K+1 valid ascending entries; return the K-tuple without entry drop
+    int v[4] = {t.x, t.y, t.z, t.w};
+    int o[4] = {-1, -1, -1, -1};
+    int w = 0;
+    for (int k = 0; k <= K; k++)
+        if (k != drop) o[w++] = v[k];
+    return make_int4(o[0], o[1], o[2], o[3]);
+}
+
+// Items: [0, nA) from a list in sorted positions (flag 1), then nB * (K+1)
+// facets of a canonical list of width K+1 (flag 0).
+struct PrepArgs {
+    const int4* a4;
+    const int2* a2;
+    int64_t nA;
+    const int4* cof;
+    int64_t nB;
+    int K;
+    const int32_t* order;  // sorted position -> input index
+    int4* t_out;
+    uint8_t* f_out;
+    int64_t* bucket_cnt;
+};
+
+__global__ void k_prep(PrepArgs a) {
+    int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int K = a.K;
+    int64_t total = a.nA + a.nB * (K + 1);
+    if (j >= total) return;
+    int4 t;
+    uint8_t flag;
+    if (j < a.nA) {
+        if (K == 2) {
+            int2 e = a.a2[j];
+            t = make_int4(a.order[e.x], a.order[e.y], -1, -1);
+        } else {
+            int4 e = a.a4[j];
+            t = make_int4(a.order[e.x], a.order[e.y], K >= 3 ? a.order[e.z] : -1, K >= 4 ? a.order[e.w] : -1);
+        }
+        sort_asc(t, K);
+        flag = 1;
+    } else {
+        int64_t r = j - a.nA;
+        int64_t row = r / (K + 1);
+        int drop = (int)(r % (K + 1));
+        t = facet_of(a.cof[row], K, drop);
+        flag = 0;
+    }
+    a.t_out[j] = t;
+    a.f_out[j] = flag;
+    atomicAdd((unsigned long long*)&a.bucket_cnt[t.x], 1ull);
+}
+
+__global__ void k_bucket_scatter(const int4* __restrict__ t_in, const uint8_t* __restrict__ f_in, int64_t total,
+                                 const int64_t* __restrict__ off, unsigned long long* __restrict__ cursor,
+                                 int4* __restrict__ t_out, uint8_t* __restrict__ f_out) {
+    int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= total) return;
+    int4 t = t_in[j];
+    int64_t slot = off[t.x] + (int64_t)atomicAdd(&cursor[t.x], 1ull);
+    t_out[slot] = t;
+    f_out[slot] = f_in[j];
+}
+
+// Sort each bucket by the remaining entries, merge duplicates (OR of flags),
+// write the unique count of the bucket.
+__global__ void k_bucket_sort_unique(int4* __restrict__ t, uint8_t* __restrict__ f, const int64_t* __restrict__ off,
+                                     int64_t n, int64_t* __restrict__ uniq) {
+    int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= n) return;
+    int64_t a = off[g], b = off[g + 1];
+    for (int64_t i = a + 1; i < b; i++) {
+        int4 v = t[i];
+        uint8_t fv = f[i];
+        int64_t j = i;
+        while (j > a && less_rest(v, t[j - 1])) {
+            t[j] = t[j - 1];
+            f[j] = f[j - 1];
+            j--;
+        }
+        t[j] = v;
+        f[j] = fv;
+    }
+    int64_t w = a;
+    for (int64_t i = a; i < b; i++) {
+        if (w > a && same(t[w - 1], t[i])) {
+            f[w - 1] |= f[i];
+        } else {
+            t[w] = t[i];
+            f[w] = f[i];
+            w++;
+        }
+    }
+    uniq[g] = w - a;
+}
+
+struct WriteArgs {
+    const int4* t;
+    const uint8_t* f;
+    const int64_t* off;   // bucket start in t
+    const int64_t* uoff;  // output row of the bucket's first unique
+    int64_t n;
+    int K;
+    const int32_t* mol_of;   // input index -> molecule
+    const int64_t* mol_off;  // molecule -> first input index
+    int4* G;                 // canonical rows, global input indices
+    int32_t* out;            // packed rows, per-molecule local indices
+    uint8_t* attached;
+};
+
+__global__ void k_bucket_write(WriteArgs a) {
+    int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= a.n) return;
+    int64_t src = a.off[g], dst = a.uoff[g], cnt = a.uoff[g + 1] - a.uoff[g];
+    int base = (int)a.mol_off[a.mol_of[g]];
+    for (int64_t k = 0; k < cnt; k++) {
+        int4 t = a.t[src + k];
+        a.G[dst + k] = t;
+        int v[4] = {t.x, t.y, t.z, t.w};
+        for (int c = 0; c < a.K; c++) a.out[(dst + k) * a.K + c] = v[c] - base;
+        a.attached[dst + k] = a.f[src + k] ? 0 : 1;
+    }
+}
+
+// Per-molecule first row: rows of molecule m start at uoff[mol_off[m]].
+__global__ void k_mol_rows(const int64_t* __restrict__ uoff, const int64_t* __restrict__ mol_off, int64_t n_mol,
+                           int64_t* __restrict__ out) {
+    int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (m > n_mol) return;
+    out[m] = uoff[mol_off[m]];
+}
+
+// ---------------------------------------------------------------------------
+// canonicalise one dimension from (positions list, flag 1) + (facets of a canonical list, flag 0)
+
+struct Work {
+    DevBuf t_a, f_a, t_b, f_b, cnt, cursor, uniq;
+};
+
+static int canon_dim(ac_ctx* c, int d, const int4* a4, const int2* a2, int64_t nA, const int4* cof, int64_t nB,
+                     SimplexList& L, DevBuf& Gout, Work& w, cudaStream_t s) {
+    const int K = d + 1;
+    const int64_t n = c->n;
+    const int64_t total = nA + nB * (K + 1);
+    AC_TRY(w.t_a.reserve((size_t)(total + 1) * sizeof(int4)));
+    AC_TRY(w.f_a.reserve((size_t)(total + 1)));
+    AC_TRY(w.t_b.reserve((size_t)(total + 1) * sizeof(int4)));
+    AC_TRY(w.f_b.reserve((size_t)(total + 1)));
+    AC_TRY(w.cnt.reserve((size_t)(n + 1) * sizeof(int64_t)));
+    AC_TRY(w.cursor.reserve((size_t)(n + 1) * sizeof(int64_t)));
+    AC_TRY(w.uniq.reserve((size_t)(n + 1) * sizeof(int64_t)));
+    AC_TRY(L.v0_off.reserve((size_t)(n + 1) * sizeof(int64_t)));
+    int64_t* cnt = w.cnt.as<int64_t>();
+    AC_CUDA(cudaMemsetAsync(cnt, 0, (size_t)(n + 1) * sizeof(int64_t), s));
+    AC_CUDA(cudaMemsetAsync(w.cursor.p, 0, (size_t)(n + 1) * sizeof(int64_t), s));
+    if (total > 0) {
+        PrepArgs pa{a4, a2, nA, cof, nB, K, c->order.as<int32_t>(), w.t_a.as<int4>(), w.f_a.as<uint8_t>(), cnt};
+        k_prep<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(pa);
+        AC_LAUNCHED();
+    }
+    AC_TRY(scan_exclusive_i64(cnt, cnt, n, c->scan_tmp, s));  // bucket offsets
+    if (total > 0) {
+        k_bucket_scatter<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(
+            w.t_a.as<int4>(), w.f_a.as<uint8_t>(), total, cnt, w.cursor.as<unsigned long long>(), w.t_b.as<int4>(),
+            w.f_b.as<uint8_t>());
+        AC_LAUNCHED();
+    }
+    int64_t* uniq = w.uniq.as<int64_t>();
+    if (n > 0) {
+        k_bucket_sort_unique<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(w.t_b.as<int4>(), w.f_b.as<uint8_t>(), cnt, n,
+                                                                        uniq);
+        AC_LAUNCHED();
+    }
+    int64_t* uoff = L.v0_off.as<int64_t>();
+    AC_TRY(scan_exclusive_i64(uniq, uoff, n, c->scan_tmp, s));
+    int64_t count = 0;
+    AC_CUDA(cudaMemcpyAsync(&count, uoff + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    AC_CUDA(cudaStreamSynchronize(s));
+    L.count = count;
+    size_t rows = (size_t)(count > 0 ? count : 1);
+    AC_TRY(L.tuples.reserve(rows * K * sizeof(int32_t)));
+    AC_TRY(L.attached.reserve(rows));
+    AC_TRY(L.f.reserve(rows * sizeof(double)));
+    AC_TRY(L.orthosize.reserve(rows * sizeof(double)));
+    AC_TRY(L.src_dim.reserve(rows));
+    AC_TRY(L.src_idx.reserve(rows * sizeof(int64_t)));
+    AC_TRY(Gout.reserve(rows * sizeof(int4)));
+    if (n > 0) {
+        WriteArgs wa{w.t_b.as<int4>(), w.f_b.as<uint8_t>(), cnt, uoff, n, K, c->mol_of.as<int32_t>(),
+                     c->d_moloff.as<int64_t>(), Gout.as<int4>(), L.tuples.as<int32_t>(), L.attached.as<uint8_t>()};
+        k_bucket_write<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(wa);
+        AC_LAUNCHED();
+    }
+    // per-molecule row ranges
+    AC_TRY(w.cursor.reserve((size_t)(c->n_mol + 1) * sizeof(int64_t)));
+    k_mol_rows<<<(unsigned)((c->n_mol + 1 + 127) / 128), 128, 0, s>>>(uoff, c->d_moloff.as<int64_t>(), c->n_mol,
+                                                                       w.cursor.as<int64_t>());
+    AC_LAUNCHED();
+    L.mol_off.assign((size_t)c->n_mol + 1, 0);
+    AC_CUDA(cudaMemcpyAsync(L.mol_off.data(), w.cursor.p, (size_t)(c->n_mol + 1) * sizeof(int64_t),
+                            cudaMemcpyDeviceToHost, s));
+    AC_CUDA(cudaStreamSynchronize(s));
+    return AC_OK;
+}
+
+// Vertices (Step 5): K^0 = endpoints of K^1 + atoms whose centre passes AC2.
+__global__ void k_mark_endpoints(const int4* __restrict__ E, int64_t m, uint8_t* __restrict__ endpoint) {
+    int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= m) return;
+    int4 e = E[j];
+    endpoint[e.x] = 1;
+    endpoint[e.y] = 1;
+}
+
+__global__ void k_vertex_flags(const uint8_t* __restrict__ endpoint, const uint8_t* __restrict__ vert_pass,
+                               const int32_t* __restrict__ rank, int64_t n, int64_t* __restrict__ inK) {
+    int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= n) return;
+    inK[g] = (endpoint[g] || vert_pass[rank[g]]) ? 1 : 0;
+}
+
+__global__ void k_vertex_write(const int64_t* __restrict__ voff, const uint8_t* __restrict__ vert_pass,
+                               const int32_t* __restrict__ rank, int64_t n, const int32_t* __restrict__ mol_of,
+                               const int64_t* __restrict__ mol_off, int4* __restrict__ G, int32_t* __restrict__ out,
+                               uint8_t* __restrict__ attached) {
+    int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= n) return;
+    if (voff[g + 1] == voff[g]) return;
+    int64_t r = voff[g];
+    G[r] = make_int4((int)g, -1, -1, -1);
+    out[r] = (int)(g - mol_off[mol_of[g]]);
+    attached[r] = vert_pass[rank[g]] ? 0 : 1;
+}
+
+int canonicalise(ac_ctx* c, cudaStream_t s) {
+    DevCounters h;
+    AC_TRY(read_counters(c, &h, s));
+    if (h.err & (DERR_OVF_TET | DERR_OVF_TRI | DERR_OVF_EDGE | DERR_OVF_CAND))
+        return fail(AC_ERR_CAPACITY, "per-atom output overflow");
+    Work w;
+    const int64_t n = c->n;
+    // K^3
+    AC_TRY(canon_dim(c, 3, c->tet_out.as<int4>(), nullptr, (int64_t)h.n_tet_out, nullptr, 0, c->K[3], c->Gbuf[3], w, s));
+    AC_CUDA(cudaEventRecord(c->ev[4], s));
+    // K^2 = unattached triangles + facets of K^3
+    AC_TRY(canon_dim(c, 2, c->tri_pass.as<int4>(), nullptr, (int64_t)h.n_tri_pass, c->Gbuf[3].as<int4>(), c->K[3].count,
+                     c->K[2], c->Gbuf[2], w, s));
+    AC_CUDA(cudaEventRecord(c->ev[5], s));
+    // K^1 = unattached edges + edges of K^2
+    AC_TRY(canon_dim(c, 1, nullptr, c->edge_pass.as<int2>(), (int64_t)h.n_edge_pass, c->Gbuf[2].as<int4>(),
+                     c->K[2].count, c->K[1], c->Gbuf[1], w, s));
+    // K^0
+    {
+        SimplexList& L = c->K[0];
+        size_t nn = (size_t)(n > 0 ? n : 1);
+        AC_TRY(w.f_a.reserve(nn));
+        AC_TRY(w.cnt.reserve((nn + 1) * sizeof(int64_t)));
+        AC_TRY(L.v0_off.reserve((nn + 1) * sizeof(int64_t)));
+        uint8_t* endpoint = w.f_a.as<uint8_t>();
+        AC_CUDA(cudaMemsetAsync(endpoint, 0, nn, s));
+        if (c->K[1].count > 0) {
+            k_mark_endpoints<<<(unsigned)((c->K[1].count + 255) / 256), 256, 0, s>>>(c->Gbuf[1].as<int4>(), c->K[1].count,
+                                                                                    endpoint);
+            AC_LAUNCHED();
+        }
+        int64_t* inK = w.cnt.as<int64_t>();
+        if (n > 0) {
+            k_vertex_flags<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(endpoint, c->vert_pass.as<uint8_t>(),
+                                                                       c->rank.as<int32_t>(), n, inK);
+            AC_LAUNCHED();
+        }
+        int64_t* voff = L.v0_off.as<int64_t>();
+        AC_TRY(scan_exclusive_i64(inK, voff, n, c->scan_tmp, s));
+        int64_t count = 0;
+        AC_CUDA(cudaMemcpyAsync(&count, voff + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        AC_CUDA(cudaStreamSynchronize(s));
+        L.count = count;
+        size_t rows = (size_t)(count > 0 ? count : 1);
+        AC_TRY(L.tuples.reserve(rows * sizeof(int32_t)));
+        AC_TRY(L.attached.reserve(rows));
+        AC_TRY(L.f.reserve(rows * sizeof(double)));
+        AC_TRY(L.orthosize.reserve(rows * sizeof(double)));
+        AC_TRY(L.src_dim.reserve(rows));
+        AC_TRY(L.src_idx.reserve(rows * sizeof(int64_t)));
+        AC_TRY(c->Gbuf[0].reserve(rows * sizeof(int4)));
+        if (n > 0) {
+            k_vertex_write<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(voff, c->vert_pass.as<uint8_t>(),
+                                                                       c->rank.as<int32_t>(), n, c->mol_of.as<int32_t>(),
+                                                                       c->d_moloff.as<int64_t>(), c->Gbuf[0].as<int4>(),
+                                                                       L.tuples.as<int32_t>(), L.attached.as<uint8_t>());
+            AC_LAUNCHED();
+        }
+        AC_TRY(w.cursor.reserve((size_t)(c->n_mol + 1) * sizeof(int64_t)));
+        k_mol_rows<<<(unsigned)((c->n_mol + 1 + 127) / 128), 128, 0, s>>>(voff, c->d_moloff.as<int64_t>(), c->n_mol,
+                                                                           w.cursor.as<int64_t>());
+        AC_LAUNCHED();
+        L.mol_off.assign((size_t)c->n_mol + 1, 0);
+        AC_CUDA(cudaMemcpyAsync(L.mol_off.data(), w.cursor.p, (size_t)(c->n_mol + 1) * sizeof(int64_t),
+                                cudaMemcpyDeviceToHost, s));
+        AC_CUDA(cudaStreamSynchronize(s));
+    }
+    // estimation-pass lists, when kept (single molecule)
+    if (c->pc.keep_candidates) {
+        for (int d = 1; d <= 3; d++) {
+            int64_t m = (int64_t)h.n_cand_out[d];
+            AC_TRY(canon_dim(c, d, d >= 2 ? c->cand[d].as<int4>() : nullptr, d == 1 ? c->cand[1].as<int2>() : nullptr, m,
+                             nullptr, 0, c->C[d], c->CGbuf[d], w, s));
+        }
+    }
+    return AC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// OrthoSize (exact) and Size
+
+__device__ __forceinline__ double i128_to_double(i128 x) {
+    bool neg = x < 0;
+    unsigned __int128 u = neg ? (unsigned __int128)(-x) : (unsigned __int128)x;
+    unsigned long long hi = (unsigned long long)(u >> 64), lo = (unsigned long long)u;
+    double r = __ull2double_rn(hi) * 18446744073709551616.0 + __ull2double_rn(lo);
+    return neg ? -r : r;
+}
+
+// OrthoSize in A^2 of a simplex of global input indices (ascending, K entries).
+__device__ double orthosize_exact(const int4* __restrict__ P, const int4& t, int K) {
+    const int4 p0 = P[t.x];
+    const long long W0 = p0.w;
+    if (K == 1) return -(double)W0 * 9.5367431640625e-07;  // 2^-20
+    int v[4] = {t.x, t.y, t.z, t.w};
+    long long q[3][3], a[3];
+    for (int k = 1; k < K; k++) {
+        int4 pk = P[v[k]];
+        q[k - 1][0] = pk.x - p0.x;
+        q[k - 1][1] = pk.y - p0.y;
+        q[k - 1][2] = pk.z - p0.z;
+        a[k - 1] = q[k - 1][0] * q[k - 1][0] + q[k - 1][1] * q[k - 1][1] + q[k - 1][2] * q[k - 1][2] - pk.w + W0;
+    }
+    i128 num, den;
+    if (K == 2) {
+        long long D = q[0][0] * q[0][0] + q[0][1] * q[0][1] + q[0][2] * q[0][2];
+        num = (i128)a[0] * a[0] - (i128)4 * D * W0;
+        den = (i128)4 * D;
+    } else if (K == 3) {
+        long long g11 = q[0][0] * q[0][0] + q[0][1] * q[0][1] + q[0][2] * q[0][2];
+        long long g22 = q[1][0] * q[1][0] + q[1][1] * q[1][1] + q[1][2] * q[1][2];
+        long long g12 = q[0][0] * q[1][0] + q[0][1] * q[1][1] + q[0][2] * q[1][2];
+        long long detG = g11 * g22 - g12 * g12;
+        long long n1 = g22 * a[0] - g12 * a[1], n2 = g11 * a[1] - g12 * a[0];
+        num = (i128)n1 * a[0] + (i128)n2 * a[1] - (i128)4 * detG * W0;
+        den = (i128)4 * detG;
+    } else {
+        long long C[3][3];
+        // C_k = q_{k+1} x q_{k+2}
+        for (int k = 0; k < 3; k++) {
+            const long long* b = q[(k + 1) % 3];
+            const long long* d = q[(k + 2) % 3];
+            C[k][0] = b[1] * d[2] - b[2] * d[1];
+            C[k][1] = b[2] * d[0] - b[0] * d[2];
+            C[k][2] = b[0] * d[1] - b[1] * d[0];
+        }
+        long long D = q[0][0] * C[0][0] + q[0][1] * C[0][1] + q[0][2] * C[0][2];
+        long long N[3];
+        for (int c = 0; c < 3; c++) N[c] = a[0] * C[0][c] + a[1] * C[1][c] + a[2] * C[2][c];
+        i128 nn = (i128)N[0] * N[0] + (i128)N[1] * N[1] + (i128)N[2] * N[2];
+        i128 DD = (i128)D * D;
+        num = nn - DD * (4 * W0);
+        den = DD * 4;
+    }
+    return i128_to_double(num) / i128_to_double(den) * 9.5367431640625e-07;
+}
+
+__global__ void k_orthosize(const int4* __restrict__ P, const int4* __restrict__ G, int64_t m, int K,
+                            const uint8_t* __restrict__ attached, double* __restrict__ os, double* __restrict__ f,
+                            int8_t* __restrict__ src_dim, int64_t* __restrict__ src_idx,
+                            unsigned long long* __restrict__ fkey) {
+    int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= m) return;
+    double v = orthosize_exact(P, G[j], K);
+    os[j] = v;
+    src_dim[j] = (int8_t)(K - 1);
+    src_idx[j] = j;
+    f[j] = v;
+    if (fkey) fkey[j] = attached[j] ? ~0ull : 0ull;
+}
+
+__device__ __forceinline__ unsigned long long order_key(double x) {
+    unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+
+__device__ __forceinline__ double key_value(unsigned long long k) {
+    unsigned long long b = (k >> 63) ? (k & 0x7fffffffffffffffull) : ~k;
+    return __longlong_as_double((long long)b);
+}
+
+// row index of tuple t (global indices, K entries) in the canonical list L, or -1
+__device__ __forceinline__ int64_t find_row(const int4* __restrict__ L, const int64_t* __restrict__ v0_off, const int4& t) {
+    int64_t lo = v0_off[t.x], hi = v0_off[t.x + 1];
+    while (lo < hi) {
+        int64_t mid = (lo + hi) >> 1;
+        int4 r = L[mid];
+        if (same(r, t)) return mid;
+        if (less_rest(r, t)) lo = mid + 1;
+        else hi = mid;
+    }
+    return -1;
+}
+
+// pass 1: smallest coface value of every attached face
+__global__ void k_coface_min(const int4* __restrict__ Cof, const double* __restrict__ fc, int64_t mc, int Kc,
+                             const int4* __restrict__ L, const int64_t* __restrict__ v0_off,
+                             const uint8_t* __restrict__ attached, unsigned long long* __restrict__ fkey) {
+    int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= mc) return;
+    int4 t = Cof[j];
+    unsigned long long key = order_key(fc[j]);
+    for (int drop = 0; drop < Kc; drop++) {
+        int4 face = facet_of(t, Kc - 1, drop);
+        int64_t r = find_row(L, v0_off, face);
+        if (r >= 0 && attached[r]) atomicMin(&fkey[r], key);
+    }
+}
+
+// pass 2: among cofaces attaining the minimum, the first in lexicographic order
+__global__ void k_coface_arg(const int4* __restrict__ Cof, const double* __restrict__ fc, int64_t mc, int Kc,
+                             const int4* __restrict__ L, const int64_t* __restrict__ v0_off,
+                             const uint8_t* __restrict__ attached, const unsigned long long* __restrict__ fkey,
+                             unsigned long long* __restrict__ arg) {
+    int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= mc) return;
+    int4 t = Cof[j];
+    unsigned long long key = order_key(fc[j]);
+    for (int drop = 0; drop < Kc; drop++) {
+        int4 face = facet_of(t, Kc - 1, drop);
+        int64_t r = find_row(L, v0_off, face);
+        if (r >= 0 && attached[r] && fkey[r] == key) atomicMin(&arg[r], (unsigned long long)j);
+    }
+}
+
+__global__ void k_coface_apply(int64_t m, const uint8_t* __restrict__ attached, const unsigned long long* __restrict__ fkey,
+                               const unsigned long long* __restrict__ arg, const int8_t* __restrict__ csrc_dim,
+                               const int64_t* __restrict__ csrc_idx, double* __restrict__ f, int8_t* __restrict__ src_dim,
+                               int64_t* __restrict__ src_idx, unsigned* __restrict__ err) {
+    int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= m || !attached[j]) return;
+    unsigned long long a = arg[j];
+    if (a == ~0ull) {
+        // an attached simplex with no coface in the complex cannot occur
+        atomicOr(err, DERR_INTERNAL);
+        f[j] = __longlong_as_double(0x7ff8000000000000ll);
+        return;
+    }
+    f[j] = key_value(fkey[j]);
+    src_dim[j] = csrc_dim[a];
+    src_idx[j] = csrc_idx[a];
+}
+
+int compute_filtration(ac_ctx* c, cudaStream_t s) {
+    const int4* P = c->P.as<int4>();
+    DevBuf& keyb = c->scratch[2];
+    DevBuf& argb = c->scratch[3];
+    for (int d = 3; d >= 0; d--) {
+        SimplexList& L = c->K[d];
+        const int64_t m = L.count;
+        if (m == 0) continue;
+        AC_TRY(keyb.reserve((size_t)m * sizeof(unsigned long long)));
+        AC_TRY(argb.reserve((size_t)m * sizeof(unsigned long long)));
+        k_orthosize<<<(unsigned)((m + 127) / 128), 128, 0, s>>>(
+            P, c->Gbuf[d].as<int4>(), m, d + 1, L.attached.as<uint8_t>(), L.orthosize.as<double>(), L.f.as<double>(),
+            L.src_dim.as<int8_t>(), L.src_idx.as<int64_t>(), keyb.as<unsigned long long>());
+        AC_LAUNCHED();
+        if (d == 3) continue;
+        SimplexList& U = c->K[d + 1];
+        AC_CUDA(cudaMemsetAsync(argb.p, 0xff, (size_t)m * sizeof(unsigned long long), s));
+        if (U.count > 0) {
+            const unsigned nbk = (unsigned)((U.count + 127) / 128);
+            k_coface_min<<<nbk, 128, 0, s>>>(c->Gbuf[d + 1].as<int4>(), U.f.as<double>(), U.count, d + 2,
+                                             c->Gbuf[d].as<int4>(), L.v0_off.as<int64_t>(), L.attached.as<uint8_t>(),
+                                             keyb.as<unsigned long long>());
+            AC_LAUNCHED();
+            k_coface_arg<<<nbk, 128, 0, s>>>(c->Gbuf[d + 1].as<int4>(), U.f.as<double>(), U.count, d + 2,
+                                             c->Gbuf[d].as<int4>(), L.v0_off.as<int64_t>(), L.attached.as<uint8_t>(),
+                                             keyb.as<unsigned long long>(), argb.as<unsigned long long>());
+            AC_LAUNCHED();
+        }
+        k_coface_apply<<<(unsigned)((m + 127) / 128), 128, 0, s>>>(
+            m, L.attached.as<uint8_t>(), keyb.as<unsigned long long>(), argb.as<unsigned long long>(),
+            U.src_dim.as<int8_t>(), U.src_idx.as<int64_t>(), L.f.as<double>(), L.src_dim.as<int8_t>(),
+            L.src_idx.as<int64_t>(), &c->counters.as<DevCounters>()->err);
+        AC_LAUNCHED();
+    }
+    DevCounters h;
+    AC_TRY(read_counters(c, &h, s));
+    if (h.err & DERR_INTERNAL) return fail(AC_ERR_CUDA, "internal: attached simplex without a coface in the complex");
+    return AC_OK;
+}
+
+}  // namespace ac

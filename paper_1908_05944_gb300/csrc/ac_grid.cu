@@ -1,0 +1,182 @@
+// Grid binning and neighbour lists (Section 4.2 of arXiv 1908.05944).
+//
+// Atoms are binned in a uniform grid of cell side ~ h = sqrt(r_max^2 + alpha)
+// and sorted by cell so that every cell is a contiguous run (the grid itself
+// is never stored per atom). The sort is a counting sort on the cell key (a
+// single-digit radix sort: histogram, exclusive scan, scatter) followed by an
+// in-cell ordering by input index, so the sorted order is deterministic.
+//
+// Neighbours: x is a neighbour of i when the grown balls (squared radius
+// W + A) of i and x meet, |P_i - P_x| <= sqrt(W_i + A) + sqrt(W_x + A), decided
+// exactly in integers. Every vertex pair of a simplex with OrthoSize <= alpha
+// and every ball that can violate AC2 at its orthocentre satisfies this with
+// each vertex (the orthocentre lies in every vertex's grown ball and in the
+// violator's), so these lists are all the later stages search. Pairs are up
+// to 2h apart, hence the stencil reach ceil(2h / cell) cells per axis (not the
+// single ring of adjacent cells of Section 4.3).
+#include "ac_internal.cuh"
+
+namespace ac {
+
+__global__ void k_cell_keys(const int4* __restrict__ P, const int32_t* __restrict__ mol_of,
+                            const MolGrid* __restrict__ grids, int cell, int64_t n, uint32_t* __restrict__ cell_of,
+                            uint32_t* __restrict__ cell_cnt) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int4 p = P[i];
+    MolGrid g = grids[mol_of[i]];
+    int cx = (p.x - g.org[0]) / cell, cy = (p.y - g.org[1]) / cell, cz = (p.z - g.org[2]) / cell;
+    uint32_t c = (uint32_t)(g.cell_base + ((int64_t)cz * g.dims[1] + cy) * g.dims[0] + cx);
+    cell_of[i] = c;
+    atomicAdd(&cell_cnt[c], 1u);
+}
+
+__global__ void k_scatter(const uint32_t* __restrict__ cell_of, const uint32_t* __restrict__ cell_start, int64_t n,
+                          uint32_t* __restrict__ cursor, int32_t* __restrict__ order) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint32_t c = cell_of[i];
+    uint32_t slot = cell_start[c] + atomicAdd(&cursor[c], 1u);
+    order[slot] = (int32_t)i;
+}
+
+// Order each cell's run by input index (runs are short: a few atoms).
+__global__ void k_sort_cells(const uint32_t* __restrict__ cell_start, int64_t n_cells, int32_t* __restrict__ order) {
+    int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= n_cells) return;
+    uint32_t a = cell_start[c], b = cell_start[c + 1];
+    for (uint32_t i = a + 1; i < b; i++) {
+        int32_t v = order[i];
+        uint32_t j = i;
+        while (j > a && order[j - 1] > v) {
+            order[j] = order[j - 1];
+            j--;
+        }
+        order[j] = v;
+    }
+}
+
+__global__ void k_gather(const int32_t* __restrict__ order, const int4* __restrict__ P,
+                         const int32_t* __restrict__ mol_of, int64_t n, int4* __restrict__ Ps,
+                         int32_t* __restrict__ mol_s, int32_t* __restrict__ rank) {
+    int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    int32_t i = order[s];
+    Ps[s] = P[i];
+    mol_s[s] = mol_of[i];
+    rank[i] = (int32_t)s;
+}
+
+int build_grid(ac_ctx* c, cudaStream_t s) {
+    const int64_t n = c->n;
+    size_t nn = (size_t)(n > 0 ? n : 1);
+    AC_TRY(c->cell_of.reserve(nn * sizeof(uint32_t)));
+    AC_TRY(c->cell_cnt.reserve((size_t)(c->n_cells + 1) * sizeof(uint32_t)));
+    AC_TRY(c->cell_start.reserve((size_t)(c->n_cells + 1) * sizeof(uint32_t)));
+    AC_TRY(c->order.reserve(nn * sizeof(int32_t)));
+    AC_TRY(c->rank.reserve(nn * sizeof(int32_t)));
+    AC_TRY(c->Ps.reserve(nn * sizeof(int4)));
+    AC_TRY(c->mol_s.reserve(nn * sizeof(int32_t)));
+    uint32_t* cnt = c->cell_cnt.as<uint32_t>();
+    uint32_t* start = c->cell_start.as<uint32_t>();
+    AC_CUDA(cudaMemsetAsync(cnt, 0, (size_t)c->n_cells * sizeof(uint32_t), s));
+    if (n == 0) {
+        AC_CUDA(cudaMemsetAsync(start, 0, (size_t)(c->n_cells + 1) * sizeof(uint32_t), s));
+        return AC_OK;
+    }
+    const unsigned nb = (unsigned)((n + 255) / 256);
+    k_cell_keys<<<nb, 256, 0, s>>>(c->P.as<int4>(), c->mol_of.as<int32_t>(), c->grids.as<MolGrid>(), c->pc.cell, n,
+                                   c->cell_of.as<uint32_t>(), cnt);
+    AC_LAUNCHED();
+    AC_TRY(scan_exclusive_u32_to_u32(cnt, start, c->n_cells, c->scan_tmp, s));
+    AC_CUDA(cudaMemsetAsync(cnt, 0, (size_t)c->n_cells * sizeof(uint32_t), s));
+    k_scatter<<<nb, 256, 0, s>>>(c->cell_of.as<uint32_t>(), start, n, cnt, c->order.as<int32_t>());
+    AC_LAUNCHED();
+    k_sort_cells<<<(unsigned)((c->n_cells + 255) / 256), 256, 0, s>>>(start, c->n_cells, c->order.as<int32_t>());
+    AC_LAUNCHED();
+    k_gather<<<nb, 256, 0, s>>>(c->order.as<int32_t>(), c->P.as<int4>(), c->mol_of.as<int32_t>(), n, c->Ps.as<int4>(),
+                                c->mol_s.as<int32_t>(), c->rank.as<int32_t>());
+    AC_LAUNCHED();
+    return AC_OK;
+}
+
+// Do the closed grown balls of two atoms meet?  t = D - s_i - s_x; they meet iff
+// t <= 0 or t^2 <= 4 s_i s_x (s = W + A >= 0).
+__device__ __forceinline__ bool grown_meet(int64_t D, int64_t si, int64_t sx) {
+    int64_t t = D - si - sx;
+    return t <= 0 || t * t <= 4 * si * sx;
+}
+
+template <bool FILL>
+__global__ void k_neighbours(const int4* __restrict__ Ps, const int32_t* __restrict__ mol_s,
+                             const MolGrid* __restrict__ grids, const uint32_t* __restrict__ cell_start,
+                             PredConst pc, int64_t n, int64_t* __restrict__ nb_cnt, const int64_t* __restrict__ nb_off,
+                             int32_t* __restrict__ nb, DevCounters* __restrict__ cnt) {
+    int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    int4 p = Ps[s];
+    int64_t si = (int64_t)p.w + pc.A;
+    int64_t count = 0, w = FILL ? nb_off[s] : 0;
+    if (si >= 0) {
+        MolGrid g = grids[mol_s[s]];
+        const int cell = pc.cell, R = pc.reach;
+        int cx = (p.x - g.org[0]) / cell, cy = (p.y - g.org[1]) / cell, cz = (p.z - g.org[2]) / cell;
+        int z0 = max(cz - R, 0), z1 = min(cz + R, g.dims[2] - 1);
+        int y0 = max(cy - R, 0), y1 = min(cy + R, g.dims[1] - 1);
+        int x0 = max(cx - R, 0), x1 = min(cx + R, g.dims[0] - 1);
+        for (int z = z0; z <= z1; z++)
+            for (int y = y0; y <= y1; y++) {
+                int64_t row = g.cell_base + ((int64_t)z * g.dims[1] + y) * g.dims[0];
+                uint32_t a = cell_start[row + x0], b = cell_start[row + x1 + 1];
+                for (uint32_t t = a; t < b; t++) {
+                    if (t == (uint32_t)s) continue;
+                    int4 o = Ps[t];
+                    int64_t dx = o.x - p.x, dy = o.y - p.y, dz = o.z - p.z;
+                    int64_t D = dx * dx + dy * dy + dz * dz;
+                    if (D == 0) {
+                        atomicOr(&cnt->err, DERR_COINCIDENT);
+                        continue;
+                    }
+                    int64_t sx = (int64_t)o.w + pc.A;
+                    if (sx < 0 || !grown_meet(D, si, sx)) continue;
+                    if (FILL) nb[w + count] = (int32_t)t;
+                    count++;
+                }
+            }
+    }
+    if (!FILL) {
+        nb_cnt[s] = count;
+        atomicMax(&cnt->max_degree, (int)count);
+    }
+}
+
+int build_neighbours(ac_ctx* c, cudaStream_t s) {
+    const int64_t n = c->n;
+    AC_TRY(c->nb_cnt.reserve((size_t)(n + 1) * sizeof(int64_t)));
+    int64_t* cntp = c->nb_cnt.as<int64_t>();
+    if (n == 0) {
+        c->nb_total = 0;
+        AC_CUDA(cudaMemsetAsync(cntp, 0, sizeof(int64_t), s));
+        AC_TRY(c->nb.reserve(4));
+        return AC_OK;
+    }
+    const unsigned nb = (unsigned)((n + 127) / 128);
+    DevCounters* dc = c->counters.as<DevCounters>();
+    k_neighbours<false><<<nb, 128, 0, s>>>(c->Ps.as<int4>(), c->mol_s.as<int32_t>(), c->grids.as<MolGrid>(),
+                                           c->cell_start.as<uint32_t>(), c->pc, n, cntp, nullptr, nullptr, dc);
+    AC_LAUNCHED();
+    AC_TRY(scan_exclusive_i64(cntp, cntp, n, c->scan_tmp, s));
+    int64_t total = 0;
+    AC_CUDA(cudaMemcpyAsync(&total, cntp + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    DevCounters h;
+    AC_TRY(read_counters(c, &h, s));
+    if (h.err & DERR_COINCIDENT) return fail(AC_ERR_DEGENERATE, "two centres coincide after quantisation to 1/1024 A");
+    c->nb_total = total;
+    AC_TRY(c->nb.reserve((size_t)(total > 0 ? total : 1) * sizeof(int32_t)));
+    k_neighbours<true><<<nb, 128, 0, s>>>(c->Ps.as<int4>(), c->mol_s.as<int32_t>(), c->grids.as<MolGrid>(),
+                                          c->cell_start.as<uint32_t>(), c->pc, n, nullptr, cntp, c->nb.as<int32_t>(), dc);
+    AC_LAUNCHED();
+    return AC_OK;
+}
+
+}  // namespace ac

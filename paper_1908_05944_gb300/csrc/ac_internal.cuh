@@ -1,0 +1,213 @@
+// Internal declarations of the alphac library (alpha complexes of weighted
+// points, arXiv 1908.05944) for sm_103a. Not part of the public C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "alphac.h"
+
+typedef __int128 i128;
+
+namespace ac {
+
+// ---------------------------------------------------------------------------
+// error plumbing
+
+void set_detail(const std::string& s);
+int fail(int code, const std::string& detail);
+int cuda_fail(cudaError_t e, const char* what, const char* file, int line);
+
+#define AC_CUDA(call)                                                        \
+    do {                                                                     \
+        cudaError_t _e = (call);                                             \
+        if (_e != cudaSuccess) return ac::cuda_fail(_e, #call, __FILE__, __LINE__); \
+    } while (0)
+
+// after every kernel launch: check it and count it (reported as kernel_launches)
+extern thread_local long long g_launch_count;
+#define AC_LAUNCHED()                                                                       \
+    do {                                                                                    \
+        cudaError_t _e = cudaGetLastError();                                                \
+        if (_e != cudaSuccess) return ac::cuda_fail(_e, "kernel launch", __FILE__, __LINE__); \
+        ++ac::g_launch_count;                                                               \
+    } while (0)
+
+#define AC_TRY(call)            \
+    do {                        \
+        int _rc = (call);       \
+        if (_rc != AC_OK) return _rc; \
+    } while (0)
+
+// Device-side error word bits (set with atomicOr by kernels, read by the host).
+enum : uint32_t {
+    DERR_COINCIDENT = 1u << 0,   // two quantised centres coincide
+    DERR_RANGE = 1u << 1,        // a value left the exact-integer range
+    DERR_INVALID = 1u << 2,      // NaN/Inf or radius <= 0
+    DERR_OVF_TET = 1u << 3,      // K^3 output list full
+    DERR_OVF_TRI = 1u << 4,      // unattached-triangle list full
+    DERR_OVF_EDGE = 1u << 5,     // unattached-edge list full
+    DERR_OVF_CAND = 1u << 6,     // a candidate list full
+    DERR_DEGREE = 1u << 7,       // neighbour count above the kernel's mask width
+    DERR_INTERNAL = 1u << 8,     // an invariant of the method failed (a bug)
+};
+
+// ---------------------------------------------------------------------------
+// grow-only device buffer
+
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+    DevBuf() = default;
+    DevBuf(const DevBuf&) = delete;
+    DevBuf& operator=(const DevBuf&) = delete;
+    DevBuf(DevBuf&& o) noexcept : p(o.p), bytes(o.bytes) {
+        o.p = nullptr;
+        o.bytes = 0;
+    }
+    DevBuf& operator=(DevBuf&& o) noexcept;
+    ~DevBuf();
+    int reserve(size_t nbytes);  // keeps contents only if no growth happened
+    template <class T>
+    T* as() const { return static_cast<T*>(p); }
+};
+
+// ---------------------------------------------------------------------------
+// counters written by the kernels (one device struct, zeroed per build)
+
+struct DevCounters {
+    unsigned long long n_tet_out;     // K^3 emitted
+    unsigned long long n_tri_pass;    // Sigma^2 triangles with AC2 at their orthocentre
+    unsigned long long n_edge_pass;   // Sigma^1 edges with AC2
+    unsigned long long n_cand[4];     // |Sigma^d| (d = 1..3 counted in the per-atom pass)
+    unsigned long long n_cand_out[4]; // candidates written (keep_candidates)
+    unsigned long long ac2_tet[3];
+    unsigned long long ac2_tri[3];
+    unsigned long long ac2_edge;
+    unsigned long long ac3[4];
+    unsigned long long work_next;     // persistent-kernel work counter
+    unsigned int err;
+    int max_degree;
+    int bad_index;
+    int pad;
+};
+
+// Grid of one molecule: origin (quanta), cell side, dims, first global cell.
+struct MolGrid {
+    int32_t org[3];
+    int32_t dims[3];
+    int64_t cell_base;
+};
+
+// Build-wide constants for the predicates.
+struct PredConst {
+    int64_t A;        // alpha in quanta^2
+    int64_t H2;       // max(W) + A: squared radius bound of a grown ball
+    int32_t cell;     // grid cell side in quanta
+    int32_t reach;    // cells searched per axis for neighbours: ceil(2h / cell)
+    float h_f;        // sqrt(H2) rounded up, FP32
+    double h_d;       // sqrt(H2) rounded up, FP64
+    int precision;    // AC_PRECISION_*
+    int keep_candidates;
+};
+
+// One list of simplices of one dimension in canonical order.
+struct SimplexList {
+    DevBuf tuples;   // int32 (count, d+1), per-molecule local indices
+    DevBuf f;        // double
+    DevBuf orthosize;// double
+    DevBuf attached; // uint8
+    DevBuf src_dim;  // int8: dimension of the source simplex (closest witness)
+    DevBuf src_idx;  // int64: index of the source simplex in its list
+    DevBuf v0_off;   // int64 (n+1): rows with first vertex (global input index) g start at v0_off[g]
+    int64_t count = 0;
+    std::vector<int64_t> mol_off;  // host: first row of each molecule, n_mol + 1
+};
+
+}  // namespace ac
+
+struct ac_ctx {
+    int64_t n = 0;
+    int64_t n_mol = 1;
+    std::vector<int64_t> mol_off;  // host, n_mol + 1
+    double alpha = 0.0;
+    ac_options opt{};
+    ac::PredConst pc{};
+    bool built = false;
+
+    // inputs
+    ac::DevBuf centres;  // double n x 3 (input order)
+    ac::DevBuf radii;    // double n
+    ac::DevBuf P;        // int4 (X, Y, Z, W) quantised, input order
+    ac::DevBuf mol_of;   // int32 molecule of each atom (input order)
+    ac::DevBuf d_moloff; // int64 n_mol + 1
+    ac::DevBuf grids;    // MolGrid per molecule
+    int64_t n_cells = 0;
+
+    // grid + sorted order
+    ac::DevBuf cell_of;   // uint32 per atom (input order)
+    ac::DevBuf cell_cnt;  // uint32 per cell
+    ac::DevBuf cell_start;// uint32 per cell + 1
+    ac::DevBuf order;     // int32: sorted position -> input index
+    ac::DevBuf rank;      // int32: input index -> sorted position
+    ac::DevBuf Ps;        // int4 sorted
+    ac::DevBuf mol_s;     // int32 molecule, sorted
+
+    // neighbour lists (sorted positions)
+    ac::DevBuf nb_cnt;   // int64 n+1 (counts, then exclusive offsets)
+    ac::DevBuf nb;       // int32
+    int64_t nb_total = 0;
+
+    // per-atom pass outputs (sorted positions)
+    ac::DevBuf tet_out;   // int4
+    ac::DevBuf tri_pass;  // int4 (x,y,z used)
+    ac::DevBuf edge_pass; // int2
+    ac::DevBuf vert_pass; // uint8 per sorted atom
+    ac::DevBuf cand[4];   // Sigma^d candidate lists when kept (int4 / int2)
+    int64_t cap_tet = 0, cap_tri = 0, cap_edge = 0, cap_cand[4] = {0, 0, 0, 0};
+
+    // canonical results; Gbuf/CGbuf hold the same rows as int4 of global input indices
+    ac::SimplexList K[4];
+    ac::DevBuf Gbuf[4];
+    ac::SimplexList C[4];  // Sigma^d (keep_candidates)
+    ac::DevBuf CGbuf[4];
+
+    // scratch
+    ac::DevBuf counters;  // DevCounters
+    ac::DevBuf scratch[6];
+    ac::DevBuf scan_tmp;
+
+    ac_stats stats{};
+    cudaEvent_t ev[10] = {};  // stage boundaries; ev[8], ev[9] bracket the per-atom kernel
+    int local_launches = 0;
+};
+
+namespace ac {
+
+// launchers (each returns AC_OK or an AC_ERR_*)
+int scan_exclusive_i64(const int64_t* in, int64_t* out, int64_t n, DevBuf& tmp, cudaStream_t s);
+int scan_exclusive_u32_to_u32(const uint32_t* in, uint32_t* out, int64_t n, DevBuf& tmp, cudaStream_t s);
+
+int quantise_and_plan(ac_ctx* c, cudaStream_t s);
+int build_grid(ac_ctx* c, cudaStream_t s);
+int build_neighbours(ac_ctx* c, cudaStream_t s);
+int run_local(ac_ctx* c, cudaStream_t s);
+int canonicalise(ac_ctx* c, cudaStream_t s);
+int compute_filtration(ac_ctx* c, cudaStream_t s);
+int eval_filtration(ac_ctx* c, const double* centres, const double* radii, double* const f_out[4], cudaStream_t s);
+int backward(ac_ctx* c, const double* const dldf[4], double* dc, double* dr, cudaStream_t s);
+
+int read_counters(ac_ctx* c, DevCounters* h, cudaStream_t s);
+
+// device helpers -------------------------------------------------------------
+
+__host__ __device__ inline int64_t div_floor(int64_t a, int64_t b) {
+    int64_t q = a / b;
+    if ((a % b != 0) && ((a < 0) != (b < 0))) --q;
+    return q;
+}
+
+}  // namespace ac

@@ -1,0 +1,69 @@
+"""The C-ABI library builds, loads without a GPU and exports every declared symbol."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import paper_1908_05944_gb300 as ac
+import importlib
+
+cuda_build = importlib.import_module("paper_1908_05944_gb300.build")
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "alphac.h")
+
+
+def _declared():
+    txt = open(HEADER).read()
+    return sorted(set(re.findall(r"^AC_API\s+[\w\s\*]+?\b(ac_\w+)\s*\(", txt, flags=re.M)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    cuda_build.build()
+    return ac.lib()
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for required in ["ac_create", "ac_create_batch", "ac_build", "ac_get_simplices", "ac_filtration_values",
+                     "ac_eval_filtration", "ac_backward", "ac_get_stats", "ac_destroy", "ac_error_string"]:
+        assert required in names
+    assert sorted(ac.EXPORTS) == names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    for name in _declared():
+        assert hasattr(lib, name), name
+    out = os.popen(f"nm -D --defined-only {ac.LIB_PATH}").read()
+    exported = set(re.findall(r"\bT (ac_\w+)", out))
+    assert set(_declared()) <= exported
+
+
+def test_error_strings_without_gpu(lib):
+    assert ac.error_string(0) == "ok"
+    for code in range(-8, 0):
+        assert ac.error_string(code) != "unknown error"
+    assert ac.error_string(-99) == "unknown error"
+
+
+def test_null_arguments_are_rejected_without_touching_the_gpu(lib):
+    assert lib.ac_create(None, None, 0, 0.0, None, None) == ac.AC_ERR_INVALID_ARG
+    out = ctypes.c_void_p()
+    assert lib.ac_create(None, None, -1, 0.0, None, ctypes.byref(out)) == ac.AC_ERR_INVALID_ARG
+    assert not out.value
+    assert lib.ac_build(None, None) == ac.AC_ERR_INVALID_ARG
+    p = ctypes.c_void_p()
+    n = ctypes.c_int64()
+    assert lib.ac_get_simplices(None, 0, -1, ctypes.byref(p), ctypes.byref(n)) == ac.AC_ERR_INVALID_ARG
+    assert lib.ac_get_stats(None, None) == ac.AC_ERR_INVALID_ARG
+    lib.ac_destroy(None)
+    assert b"NULL" in lib.ac_last_error_detail() or lib.ac_last_error_detail() != b""
+
+
+def test_stats_struct_layout_matches_header():
+    txt = open(HEADER).read()
+    body = txt[txt.index("typedef struct {\n    int64_t n_atoms;"):]
+    body = body[: body.index("} ac_stats;")]
+    fields = re.findall(r"^\s+\w+\s+(\w+)(?:\[\d\])?;", body, flags=re.M)
+    assert fields == [f for f, _ in ac.ac_stats._fields_]

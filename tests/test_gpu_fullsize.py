@@ -1,0 +1,100 @@
+"""Parity at the benchmark sizes, in the launch configuration bench.py times.
+
+* 100,000-atom globule (probe radii): the whole complex against the oracle, in
+  both predicate modes.
+* 3,000,000-atom capsid-like shell: the oracle cannot run whole, so it is run
+  on neighbourhoods of sampled atoms. Whether a simplex containing atom a is in
+  K_alpha, and its Size, depend only on atoms within 2h of a: every vertex of a
+  simplex or coface through a is within 2h (grown balls meet), and every ball
+  that can violate AC2 at such an orthocentre lies within h of it (Section 4.4
+  argument); the sample radius 3h leaves margin. Input order is preserved in
+  the sub-problem, so the index-ordered tie-breaking is the same. Plus
+  properties that hold at any size (closure, monotone Size) on a row sample.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from gpu_util import assert_same_complex, assert_values, run_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+@pytest.mark.parametrize("mode", [0, 1], ids=["filtered", "plain_fp64"])
+def test_globule100k_whole(mode):
+    c, r = synth.workload("globule100k_probe")
+    ref = oracle.alpha_complex(c, r, 0.0)
+    gpu = run_gpu(c, r, 0.0, precision=mode)
+    assert_same_complex(gpu, ref)
+    st = gpu.stats()
+    assert st["candidates"][1:] == [int(x) for x in ref.candidate_counts()[1:]]
+
+
+def _rows_with(tuples, a):
+    return np.nonzero(np.any(tuples == a, axis=1))[0]
+
+
+@pytest.fixture(scope="module")
+def shell():
+    c, r = synth.workload("shell3m_probe")
+    gpu = run_gpu(c, r, 0.0)
+    out = {"c": c, "r": r, "S": [gpu.simplices(d).cpu().numpy() for d in range(4)],
+           "F": [gpu.filtration_values(d).cpu().numpy() for d in range(4)],
+           "A": [gpu.attached(d).cpu().numpy().astype(bool) for d in range(4)], "stats": gpu.stats()}
+    gpu.close()
+    return out
+
+
+def test_shell3m_sampled_neighbourhoods(shell):
+    c, r = shell["c"], shell["r"]
+    h = float(np.sqrt(r.max() ** 2))
+    rng = np.random.default_rng(2024)
+    samples = rng.choice(len(r), 40, replace=False)
+    from scipy.spatial import cKDTree
+
+    tree = cKDTree(c)
+    for a in samples:
+        idx = np.sort(np.array(tree.query_ball_point(c[a], 3.0 * h + 0.5), dtype=np.int64))
+        sub = oracle.alpha_complex(c[idx], r[idx], 0.0)
+        la = int(np.searchsorted(idx, a))
+        for d in range(4):
+            rows = _rows_with(sub.simplices[d], la)
+            want = idx[sub.simplices[d][rows]]
+            want_f = sub.f[d][rows]
+            want_a = sub.attached[d][rows]
+            g_rows = _rows_with(shell["S"][d], a)
+            got = shell["S"][d][g_rows]
+            assert got.shape == want.shape, f"atom {a} dim {d}: {len(got)} vs {len(want)}"
+            assert np.array_equal(got, want), f"atom {a} dim {d}"
+            assert np.array_equal(shell["A"][d][g_rows], want_a)
+            assert_values(shell["F"][d][g_rows], want_f, f"atom {a} dim {d}")
+
+
+def test_shell3m_closure_and_monotone_size(shell):
+    S, F = shell["S"], shell["F"]
+    rng = np.random.default_rng(7)
+    for d in range(1, 4):
+        lower = S[d - 1]
+        keys = lower.astype(np.int64)
+        # lexicographic search in the sorted lower list
+        view = np.ascontiguousarray(keys).view([("", np.int64)] * d).ravel()
+        rows = rng.choice(len(S[d]), min(200000, len(S[d])), replace=False)
+        for drop in range(d + 1):
+            faces = np.delete(S[d][rows], drop, axis=1).astype(np.int64)
+            fv = np.ascontiguousarray(faces).view([("", np.int64)] * d).ravel()
+            pos = np.searchsorted(view, fv)
+            assert np.all(pos < len(view))
+            assert np.array_equal(keys[pos], faces), f"dim {d}: a face is missing"
+            assert np.all(F[d - 1][pos] <= F[d][rows]), f"dim {d}: Size not monotone"
+    st = shell["stats"]
+    n = len(shell["r"])
+    per_atom = sum(st["simplices"]) / n
+    assert 5 < per_atom < 40
