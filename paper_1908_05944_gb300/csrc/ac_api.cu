@@ -192,44 +192,69 @@ int read_counters(ac_ctx* c, DevCounters* h, cudaStream_t s) {
 __global__ void k_quantise(const double* __restrict__ centres, const double* __restrict__ radii, int64_t n,
                            const int32_t* __restrict__ mol_of, int4* __restrict__ P, int32_t* __restrict__ bbox,
                            int* __restrict__ wmax, DevCounters* cnt) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    double x = centres[3 * i], y = centres[3 * i + 1], z = centres[3 * i + 2], r = radii[i];
-    bool finite = isfinite(x) && isfinite(y) && isfinite(z) && isfinite(r);
-    if (!finite || !(r > 0.0)) {
-        atomicOr(&cnt->err, DERR_INVALID);
-        atomicMin(&cnt->bad_index, (int)i);
-        return;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    bool ok = false;
+    int X = 0, Y = 0, Z = 0, W = 0, m = -1;
+    if (i < n) {
+        double x = centres[3 * i], y = centres[3 * i + 1], z = centres[3 * i + 2], r = radii[i];
+        bool finite = isfinite(x) && isfinite(y) && isfinite(z) && isfinite(r);
+        const double lim = 1048576.0;  // |x| <= 2^20 A keeps quantised coordinates within 2^30
+        uint32_t bad = 0;
+        if (!finite || !(r > 0.0)) {
+            bad = DERR_INVALID;
+        } else if (fabs(x) > lim || fabs(y) > lim || fabs(z) > lim || r > 64.0) {
+            bad = DERR_RANGE;
+        } else {
+            X = __double2int_rn(x * 1024.0);
+            Y = __double2int_rn(y * 1024.0);
+            Z = __double2int_rn(z * 1024.0);
+            const int R = __double2int_rn(r * 1024.0);
+            // radius quantised to 0, or above 4 A (W would leave the 2^24 range of the predicates)
+            if (R < 1 || R > 4096) bad = DERR_RANGE;
+            else W = R * R;
+        }
+        if (bad) {
+            atomicOr(&cnt->err, bad);
+            atomicMin(&cnt->bad_index, (int)i);
+        } else {
+            P[i] = make_int4(X, Y, Z, W);
+            ok = true;
+            m = mol_of[i];
+        }
     }
-    const double lim = 1048576.0;  // |x| <= 2^20 A keeps quantised coordinates within 2^30
-    if (fabs(x) > lim || fabs(y) > lim || fabs(z) > lim || r > 64.0) {
-        atomicOr(&cnt->err, DERR_RANGE);
-        atomicMin(&cnt->bad_index, (int)i);
-        return;
+    // one atomic per warp and bound when the warp's atoms share a molecule (the usual case)
+    const int m0 = __shfl_sync(full, m, 0);
+    const bool uniform = __all_sync(full, !ok || m == m0) && __any_sync(full, ok);
+    if (uniform) {
+        const int big = 0x7fffffff, small = (int)0x80000000;
+        const int mnx = __reduce_min_sync(full, ok ? X : big), mny = __reduce_min_sync(full, ok ? Y : big),
+                  mnz = __reduce_min_sync(full, ok ? Z : big);
+        const int mxx = __reduce_max_sync(full, ok ? X : small), mxy = __reduce_max_sync(full, ok ? Y : small),
+                  mxz = __reduce_max_sync(full, ok ? Z : small);
+        const int mw = __reduce_max_sync(full, ok ? W : 0);
+        const int mm = __reduce_max_sync(full, m);
+        if (lane == 0) {
+            int32_t* b = bbox + 6 * mm;
+            atomicMin(&b[0], mnx);
+            atomicMin(&b[1], mny);
+            atomicMin(&b[2], mnz);
+            atomicMax(&b[3], mxx);
+            atomicMax(&b[4], mxy);
+            atomicMax(&b[5], mxz);
+            atomicMax(wmax, mw);
+        }
+    } else if (ok) {
+        int32_t* b = bbox + 6 * m;
+        atomicMin(&b[0], X);
+        atomicMin(&b[1], Y);
+        atomicMin(&b[2], Z);
+        atomicMax(&b[3], X);
+        atomicMax(&b[4], Y);
+        atomicMax(&b[5], Z);
+        atomicMax(wmax, W);
     }
-    int X = __double2int_rn(x * 1024.0), Y = __double2int_rn(y * 1024.0), Z = __double2int_rn(z * 1024.0);
-    int R = __double2int_rn(r * 1024.0);
-    if (R < 1) {
-        atomicOr(&cnt->err, DERR_RANGE);
-        atomicMin(&cnt->bad_index, (int)i);
-        return;
-    }
-    if (R > 4096) {  // radius above 4 A: W would leave the 2^24 range of the predicates
-        atomicOr(&cnt->err, DERR_RANGE);
-        atomicMin(&cnt->bad_index, (int)i);
-        return;
-    }
-    int W = R * R;
-    P[i] = make_int4(X, Y, Z, W);
-    atomicMax(wmax, W);
-    int m = mol_of[i];
-    int32_t* b = bbox + 6 * m;
-    atomicMin(&b[0], X);
-    atomicMin(&b[1], Y);
-    atomicMin(&b[2], Z);
-    atomicMax(&b[3], X);
-    atomicMax(&b[4], Y);
-    atomicMax(&b[5], Z);
 }
 
 __global__ void k_fill_mol(const int64_t* __restrict__ mol_off, int64_t n_mol, int32_t* __restrict__ mol_of) {

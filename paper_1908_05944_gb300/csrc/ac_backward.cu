@@ -10,7 +10,8 @@
 // coordinates of c in aff(s)), and the Lagrangian is sum_k lambda_k pi(c, b_k).
 // The envelope theorem then gives
 //   dOrthoSize/dp_k = 2 lambda_k (p_k - c),  dOrthoSize/dr_k = -2 r_k lambda_k.
-// Everything here is FP64 on the caller's continuous inputs.
+// The gradient is FP64 on the caller's continuous inputs; re-evaluated values
+// (for finite-difference checks) use double-double arithmetic.
 #include "ac_internal.cuh"
 
 namespace ac {
@@ -69,6 +70,104 @@ __device__ Ortho ortho_fp64(const double* __restrict__ X, const double* __restri
     return o;
 }
 
+// Double-double arithmetic (an unevaluated sum hi + lo of two doubles) from the
+// error-free transformations TwoSum (Knuth) and TwoProduct via FMA: about 106
+// bits, so re-evaluated values of ill-conditioned (flat) simplices stay accurate
+// to a few FP64 ulps and central differences with a 1e-6 A step are meaningful.
+struct dd {
+    double hi, lo;
+};
+
+__device__ __forceinline__ dd dd_from(double a) { return {a, 0.0}; }
+
+__device__ __forceinline__ dd two_sum(double a, double b) {
+    double s = a + b;
+    double bb = s - a;
+    double e = (a - (s - bb)) + (b - bb);
+    return {s, e};
+}
+
+__device__ __forceinline__ dd dd_add(dd a, dd b) {
+    dd s = two_sum(a.hi, b.hi);
+    dd t = two_sum(a.lo, b.lo);
+    s.lo += t.hi;
+    s = two_sum(s.hi, s.lo);
+    s.lo += t.lo;
+    return two_sum(s.hi, s.lo);
+}
+
+__device__ __forceinline__ dd dd_neg(dd a) { return {-a.hi, -a.lo}; }
+
+__device__ __forceinline__ dd dd_sub(dd a, dd b) { return dd_add(a, dd_neg(b)); }
+
+__device__ __forceinline__ dd dd_mul(dd a, dd b) {
+    double p = a.hi * b.hi;
+    double e = fma(a.hi, b.hi, -p);
+    e += a.hi * b.lo + a.lo * b.hi;
+    return two_sum(p, e);
+}
+
+__device__ __forceinline__ dd dd_div(dd a, dd b) {
+    double q1 = a.hi / b.hi;
+    dd r = dd_sub(a, dd_mul(b, dd_from(q1)));
+    double q2 = r.hi / b.hi;
+    r = dd_sub(r, dd_mul(b, dd_from(q2)));
+    double q3 = r.hi / b.hi;
+    dd q = two_sum(q1, q2);
+    return dd_add(q, dd_from(q3));
+}
+
+// OrthoSize of K vertices from FP64 centres/radii, evaluated in double-double.
+__device__ double orthosize_dd(const double* __restrict__ X, const double* __restrict__ R, const int4& t, int K) {
+    const int v[4] = {t.x, t.y, t.z, t.w};
+    const dd r0 = dd_from(R[v[0]]);
+    const dd w0 = dd_mul(r0, r0);
+    if (K == 1) return -w0.hi;
+    dd q[3][3], a[3];
+    for (int k = 1; k < K; k++) {
+        const dd rk = dd_from(R[v[k]]);
+        dd sq = dd_from(0.0);
+        for (int c = 0; c < 3; c++) {
+            q[k - 1][c] = two_sum(X[3 * v[k] + c], -X[3 * v[0] + c]);
+            sq = dd_add(sq, dd_mul(q[k - 1][c], q[k - 1][c]));
+        }
+        a[k - 1] = dd_add(dd_sub(sq, dd_mul(rk, rk)), w0);
+    }
+    auto dot = [](const dd* x, const dd* y) {
+        return dd_add(dd_add(dd_mul(x[0], y[0]), dd_mul(x[1], y[1])), dd_mul(x[2], y[2]));
+    };
+    dd num, den;
+    if (K == 2) {
+        dd D = dot(q[0], q[0]);
+        num = dd_mul(a[0], a[0]);
+        den = dd_mul(dd_from(4.0), D);
+    } else if (K == 3) {
+        dd g11 = dot(q[0], q[0]), g22 = dot(q[1], q[1]), g12 = dot(q[0], q[1]);
+        dd det = dd_sub(dd_mul(g11, g22), dd_mul(g12, g12));
+        dd n1 = dd_sub(dd_mul(g22, a[0]), dd_mul(g12, a[1]));
+        dd n2 = dd_sub(dd_mul(g11, a[1]), dd_mul(g12, a[0]));
+        num = dd_add(dd_mul(n1, a[0]), dd_mul(n2, a[1]));
+        den = dd_mul(dd_from(4.0), det);
+    } else {
+        dd C[3][3];
+        for (int k = 0; k < 3; k++) {
+            const dd* b = q[(k + 1) % 3];
+            const dd* e = q[(k + 2) % 3];
+            C[k][0] = dd_sub(dd_mul(b[1], e[2]), dd_mul(b[2], e[1]));
+            C[k][1] = dd_sub(dd_mul(b[2], e[0]), dd_mul(b[0], e[2]));
+            C[k][2] = dd_sub(dd_mul(b[0], e[1]), dd_mul(b[1], e[0]));
+        }
+        dd D = dot(q[0], C[0]);
+        dd N[3];
+        for (int c = 0; c < 3; c++)
+            N[c] = dd_add(dd_add(dd_mul(a[0], C[0][c]), dd_mul(a[1], C[1][c])), dd_mul(a[2], C[2][c]));
+        num = dot(N, N);
+        den = dd_mul(dd_from(4.0), dd_mul(D, D));
+    }
+    dd f = dd_sub(dd_div(num, den), w0);
+    return f.hi + f.lo;
+}
+
 __global__ void k_eval(const double* __restrict__ X, const double* __restrict__ R, const int8_t* __restrict__ sdim,
                        const int64_t* __restrict__ sidx, int64_t m, const int4* const* __restrict__ G,
                        double* __restrict__ out) {
@@ -76,7 +175,7 @@ __global__ void k_eval(const double* __restrict__ X, const double* __restrict__ 
     if (j >= m) return;
     const int d = sdim[j];
     const int4 t = G[d][sidx[j]];
-    out[j] = ortho_fp64(X, R, t, d + 1).value;
+    out[j] = orthosize_dd(X, R, t, d + 1);
 }
 
 __global__ void k_backward(const double* __restrict__ X, const double* __restrict__ R, const int8_t* __restrict__ sdim,

@@ -125,12 +125,85 @@ __global__ void k_bucket_scatter(const int4* __restrict__ t_in, const uint8_t* _
     f_out[slot] = f_in[j];
 }
 
-// Sort each bucket by the remaining entries, merge duplicates (OR of flags),
-// write the unique count of the bucket.
-__global__ void k_bucket_sort_unique(int4* __restrict__ t, uint8_t* __restrict__ f, const int64_t* __restrict__ off,
-                                     int64_t n, int64_t* __restrict__ uniq) {
+// Warp-per-bucket version for buckets of up to WARP_SORT_MAX items: every lane
+// ranks its items against the whole bucket held in shared memory (stable rank:
+// smaller keys plus equal keys that come earlier), places them, then the first
+// of each run of equal tuples takes the OR of the run's flags. Larger buckets
+// are left to k_bucket_sort_unique (flag big).
+constexpr int WARP_SORT_MAX = 256;
+constexpr int SORT_WARPS = 4;  // 4 x 256 x 34 B = 34.8 KB static shared memory (< 48 KB)
+
+__global__ void __launch_bounds__(SORT_WARPS * 32) k_bucket_sort_warp(int4* __restrict__ t, uint8_t* __restrict__ f,
+                                                                       const int64_t* __restrict__ off, int64_t n,
+                                                                       int64_t* __restrict__ uniq,
+                                                                       uint8_t* __restrict__ big) {
+    __shared__ int4 sk[SORT_WARPS][WARP_SORT_MAX];
+    __shared__ int4 so[SORT_WARPS][WARP_SORT_MAX];
+    __shared__ uint8_t sf[SORT_WARPS][WARP_SORT_MAX];
+    __shared__ uint8_t sfo[SORT_WARPS][WARP_SORT_MAX];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t warps = (int64_t)gridDim.x * SORT_WARPS;
+    for (int64_t g = (int64_t)blockIdx.x * SORT_WARPS + w; g < n; g += warps) {
+        const int64_t a = off[g], b = off[g + 1];
+        const int k = (int)(b - a);
+        if (k > WARP_SORT_MAX) {
+            if (lane == 0) big[g] = 1;
+            continue;
+        }
+        if (lane == 0) big[g] = 0;
+        if (k <= 1) {
+            if (lane == 0) uniq[g] = k;
+            continue;
+        }
+        for (int i = lane; i < k; i += 32) {
+            sk[w][i] = t[a + i];
+            sf[w][i] = f[a + i];
+        }
+        __syncwarp();
+        for (int i = lane; i < k; i += 32) {
+            const int4 v = sk[w][i];
+            int r = 0;
+            for (int j = 0; j < k; j++) {
+                const int4 u = sk[w][j];
+                r += (less_rest(u, v) || (same(u, v) && j < i)) ? 1 : 0;
+            }
+            so[w][r] = v;
+            sfo[w][r] = sf[w][i];
+        }
+        __syncwarp();
+        // first of each run of equal tuples, with the OR of the run's flags
+        int base = 0;
+        for (int i0 = 0; i0 < k; i0 += 32) {
+            const int i = i0 + lane;
+            bool first = false;
+            uint8_t fl = 0;
+            int4 v = make_int4(0, 0, 0, 0);
+            if (i < k) {
+                v = so[w][i];
+                first = i == 0 || !same(so[w][i - 1], v);
+                if (first) {
+                    fl = sfo[w][i];
+                    for (int j = i + 1; j < k && same(so[w][j], v); j++) fl |= sfo[w][j];
+                }
+            }
+            const unsigned bal = __ballot_sync(0xffffffffu, first);
+            if (first) {
+                const int pos = base + __popc(bal & ((1u << lane) - 1u));
+                t[a + pos] = v;
+                f[a + pos] = fl;
+            }
+            base += __popc(bal);
+        }
+        if (lane == 0) uniq[g] = base;
+        __syncwarp();
+    }
+}
+
+// The remaining (large) buckets, one thread each.
+__global__ void k_bucket_sort_big(int4* __restrict__ t, uint8_t* __restrict__ f, const int64_t* __restrict__ off,
+                                  int64_t n, int64_t* __restrict__ uniq, const uint8_t* __restrict__ big) {
     int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= n) return;
+    if (g >= n || !big[g]) return;
     int64_t a = off[g], b = off[g + 1];
     for (int64_t i = a + 1; i < b; i++) {
         int4 v = t[i];
@@ -197,7 +270,7 @@ __global__ void k_mol_rows(const int64_t* __restrict__ uoff, const int64_t* __re
 // canonicalise one dimension from (positions list, flag 1) + (facets of a canonical list, flag 0)
 
 struct Work {
-    DevBuf t_a, f_a, t_b, f_b, cnt, cursor, uniq;
+    DevBuf t_a, f_a, t_b, f_b, cnt, cursor, uniq, big;
 };
 
 static int canon_dim(ac_ctx* c, int d, const int4* a4, const int2* a2, int64_t nA, const int4* cof, int64_t nB,
@@ -230,8 +303,17 @@ static int canon_dim(ac_ctx* c, int d, const int4* a4, const int2* a2, int64_t n
     }
     int64_t* uniq = w.uniq.as<int64_t>();
     if (n > 0) {
-        k_bucket_sort_unique<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(w.t_b.as<int4>(), w.f_b.as<uint8_t>(), cnt, n,
-                                                                        uniq);
+        AC_TRY(w.big.reserve((size_t)n));
+        int dev = 0, sms = 0;
+        AC_CUDA(cudaGetDevice(&dev));
+        AC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        int64_t blocks = (n + SORT_WARPS - 1) / SORT_WARPS;
+        if (blocks > (int64_t)sms * 16) blocks = (int64_t)sms * 16;
+        k_bucket_sort_warp<<<(unsigned)blocks, SORT_WARPS * 32, 0, s>>>(w.t_b.as<int4>(), w.f_b.as<uint8_t>(), cnt, n,
+                                                                         uniq, w.big.as<uint8_t>());
+        AC_LAUNCHED();
+        k_bucket_sort_big<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(w.t_b.as<int4>(), w.f_b.as<uint8_t>(), cnt, n,
+                                                                     uniq, w.big.as<uint8_t>());
         AC_LAUNCHED();
     }
     int64_t* uoff = L.v0_off.as<int64_t>();
