@@ -177,6 +177,22 @@ AC_API int ac_eval_filtration(ac_ctx* ctx, const double* d_centres, const double
 AC_API int ac_backward(ac_ctx* ctx, const double* const d_dLdf[4], double* d_dLdcentres, double* d_dLdradii,
                 void* stream);
 
+/*
+ * ac_backward without any device allocation. The paper has no counterpart:
+ * this serves callers that cannot allocate device memory (a training step
+ * whose memory belongs to another allocator, a service with a fixed device
+ * memory budget). ac_backward allocates a small table of per-dimension list
+ * pointers on its first call; here that table is a static device array of
+ * 4 pointers (32 bytes, 256-byte aligned) that every GPU loading the library
+ * holds until exit. Same arguments, results and errors as ac_backward
+ * (AC_ERR_CAPACITY if a context had more lists than the table holds). The
+ * first call on a device looks up the table's device address (with that
+ * device current); make that first call before any stream capture. Every call
+ * rewrites the whole table; calls that overlap on the GPU share it and race.
+ */
+AC_API int ac_backward_noalloc(ac_ctx* ctx, const double* const d_dLdf[4], double* d_dLdcentres, double* d_dLdradii,
+                               void* stream);
+
 /* Counters and stage times of the last ac_build. */
 AC_API int ac_get_stats(ac_ctx* ctx, ac_stats* out);
 

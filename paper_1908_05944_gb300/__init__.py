@@ -36,8 +36,8 @@ AC_FILTRATION_ORTHOSIZE = 1
 
 # every symbol include/alphac.h declares
 EXPORTS = ["ac_create", "ac_create_batch", "ac_build", "ac_get_simplices", "ac_filtration_values", "ac_attached_flags",
-           "ac_get_candidates", "ac_eval_filtration", "ac_backward", "ac_get_stats", "ac_get_sizes", "ac_destroy",
-           "ac_error_string", "ac_last_error_detail"]
+           "ac_get_candidates", "ac_eval_filtration", "ac_backward", "ac_backward_noalloc", "ac_get_stats",
+           "ac_get_sizes", "ac_destroy", "ac_error_string", "ac_last_error_detail"]
 
 
 class ac_options(ctypes.Structure):
@@ -86,6 +86,7 @@ def _declare(lib):
     lib.ac_get_candidates.argtypes = [vp, i32, P(vp), P(i64)]
     lib.ac_eval_filtration.argtypes = [vp, vp, vp, vp, vp]
     lib.ac_backward.argtypes = [vp, vp, vp, vp, vp]
+    lib.ac_backward_noalloc.argtypes = [vp, vp, vp, vp, vp]
     lib.ac_get_stats.argtypes = [vp, P(ac_stats)]
     lib.ac_get_sizes.argtypes = [vp, P(i64), P(i64)]
     lib.ac_destroy.argtypes = [vp]

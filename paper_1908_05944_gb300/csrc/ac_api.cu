@@ -551,6 +551,13 @@ extern "C" int ac_backward(ac_ctx* c, const double* const d_dLdf[4], double* d_d
     return backward(c, d_dLdf, d_dLdcentres, d_dLdradii, (cudaStream_t)stream);
 }
 
+extern "C" int ac_backward_noalloc(ac_ctx* c, const double* const d_dLdf[4], double* d_dLdcentres,
+                                   double* d_dLdradii, void* stream) {
+    if (!c || !d_dLdf || !d_dLdcentres || !d_dLdradii) return fail(AC_ERR_INVALID_ARG, "bad argument");
+    if (!c->built) return fail(AC_ERR_STATE, "no successful ac_build on this context");
+    return backward_noalloc(c, d_dLdf, d_dLdcentres, d_dLdradii, (cudaStream_t)stream);
+}
+
 extern "C" int ac_get_stats(ac_ctx* c, ac_stats* out) {
     if (!c || !out) return fail(AC_ERR_INVALID_ARG, "bad argument");
     *out = c->stats;

@@ -12,6 +12,8 @@
 //   dOrthoSize/dp_k = 2 lambda_k (p_k - c),  dOrthoSize/dr_k = -2 r_k lambda_k.
 // The gradient is FP64 on the caller's continuous inputs; re-evaluated values
 // (for finite-difference checks) use double-double arithmetic.
+#include <mutex>
+
 #include "ac_internal.cuh"
 
 namespace ac {
@@ -230,6 +232,67 @@ int backward(ac_ctx* c, const double* const dldf[4], double* dc, double* dr, cud
         k_backward<<<(unsigned)((m + 127) / 128), 128, 0, s>>>(c->centres.as<double>(), c->radii.as<double>(),
                                                                c->K[d].src_dim.as<int8_t>(), c->K[d].src_idx.as<int64_t>(),
                                                                m, c->scratch[5].as<const int4*>(), dldf[d], dc, dr);
+        AC_LAUNCHED();
+    }
+    AC_CUDA(cudaStreamSynchronize(s));
+    return AC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// ac_backward_noalloc: the same backward kernel without any device allocation.
+//
+// ac_backward keeps the table of the four per-dimension source-list pointers
+// that k_backward reads in a context buffer it allocates on first use. Callers
+// that cannot allocate device memory (for example inside a training step
+// whose memory belongs to another allocator, or a service with a fixed device
+// memory budget) use this entry point instead: the table lives in the static
+// array below, which every GPU that loads the library holds until the process
+// exits. Maximum: NOALLOC_TABLE_ENTRIES = 4 pointers (one per dimension 0..3),
+// 32 bytes in a 256-byte-aligned array. Every call overwrites the whole table
+// before its kernels read it, so nothing in it has to start at zero; calls that
+// overlap on the GPU (other streams, other host threads) share the one table
+// and race.
+constexpr int NOALLOC_TABLE_ENTRIES = 4;
+static __device__ __align__(256) const int4* g_noalloc_table[NOALLOC_TABLE_ENTRIES];
+
+// Device addresses of g_noalloc_table, looked up once per device with that
+// device current (the host-side name is only a stand-in).
+constexpr int NOALLOC_MAX_DEVICES = 64;
+static const int4** g_noalloc_addr[NOALLOC_MAX_DEVICES];
+static std::mutex g_noalloc_mu;
+
+static int noalloc_table(const int4*** out) {
+    int dev = 0;
+    AC_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return fail(AC_ERR_INVALID_ARG, "device ordinal above 63");
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        void* ptr = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_table);
+        if (e != cudaSuccess || !ptr) return cuda_fail(e, "cudaGetSymbolAddress(g_noalloc_table)", __FILE__, __LINE__);
+        g_noalloc_addr[dev] = (const int4**)ptr;
+    }
+    *out = g_noalloc_addr[dev];
+    return AC_OK;
+}
+
+int backward_noalloc(ac_ctx* c, const double* const dldf[4], double* dc, double* dr, cudaStream_t s) {
+    const int lists = 4;
+    if (lists > NOALLOC_TABLE_ENTRIES) return fail(AC_ERR_CAPACITY, "more simplex lists than the static table holds");
+    const int4** table = nullptr;
+    AC_TRY(noalloc_table(&table));
+    const int4* h[NOALLOC_TABLE_ENTRIES];
+    for (int d = 0; d < lists; d++) h[d] = c->Gbuf[d].as<int4>();
+    AC_CUDA(cudaMemcpyAsync(table, h, sizeof(h), cudaMemcpyHostToDevice, s));
+    const int64_t n = c->n;
+    AC_CUDA(cudaMemsetAsync(dc, 0, (size_t)(n > 0 ? n : 0) * 3 * sizeof(double), s));
+    AC_CUDA(cudaMemsetAsync(dr, 0, (size_t)(n > 0 ? n : 0) * sizeof(double), s));
+    for (int d = 0; d < lists; d++) {
+        const int64_t m = c->K[d].count;
+        if (!dldf[d] || m == 0) continue;
+        k_backward<<<(unsigned)((m + 127) / 128), 128, 0, s>>>(c->centres.as<double>(), c->radii.as<double>(),
+                                                               c->K[d].src_dim.as<int8_t>(), c->K[d].src_idx.as<int64_t>(),
+                                                               m, table, dldf[d], dc, dr);
         AC_LAUNCHED();
     }
     AC_CUDA(cudaStreamSynchronize(s));

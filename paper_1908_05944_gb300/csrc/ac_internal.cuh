@@ -199,6 +199,7 @@ int canonicalise(ac_ctx* c, cudaStream_t s);
 int compute_filtration(ac_ctx* c, cudaStream_t s);
 int eval_filtration(ac_ctx* c, const double* centres, const double* radii, double* const f_out[4], cudaStream_t s);
 int backward(ac_ctx* c, const double* const dldf[4], double* dc, double* dr, cudaStream_t s);
+int backward_noalloc(ac_ctx* c, const double* const dldf[4], double* dc, double* dr, cudaStream_t s);
 
 int read_counters(ac_ctx* c, DevCounters* h, cudaStream_t s);
 
