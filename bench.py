@@ -224,6 +224,80 @@ def run_ours(args, rank, world):
     return res
 
 
+def time_builds(cx, steps, warmup, stream, flush):
+    """Device time (ms) of each of `steps` builds after `warmup` untimed ones, L2 flushed in between."""
+    import torch
+
+    for _ in range(warmup):
+        cx.build(stream)
+    ms = []
+    for _ in range(steps):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        cx.build(stream)
+        t1.record(stream)
+        torch.cuda.synchronize()
+        ms.append(t0.elapsed_time(t1))
+    return ms
+
+
+def run_forms(args):
+    """Side measurements: plain FP64 vs filtered, the 3M shell, batched vs per-molecule launches."""
+    import torch
+
+    import paper_1908_05944_gb300 as ac
+    import synth
+
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    out = {}
+    steps, warm = 3, 2
+    for wl, prec in (("globule100k_probe", "plain_fp64"), ("shell3m_probe", "filtered"), ("shell3m_probe", "plain_fp64")):
+        c_np, r_np = workload(wl)
+        p = ac.AC_PRECISION_FILTERED if prec == "filtered" else ac.AC_PRECISION_PLAIN_FP64
+        cx = ac.AlphaComplex(torch.from_numpy(c_np).cuda(), torch.from_numpy(r_np).cuda(), 0.0, ac.options(precision=p))
+        ms = time_builds(cx, steps, warm, stream, flush)
+        st = cx.stats()
+        n = len(r_np)
+        out[f"{wl}/{prec}"] = {"atoms_per_s": n * steps / (sum(ms) / 1e3), "ms_per_step": sum(ms) / steps,
+                               "simplices": st["simplices"], "local_kernel_ms": st["ms_stage"][7]}
+        cx.close()
+        del cx
+    # batch: one context over all molecules vs one context per molecule
+    sizes = synth.batch_sizes(4, 1024)
+    mols = [synth.globule(1000 + m, int(n), probe=True) for m, n in enumerate(sizes)]
+    offsets = np.concatenate([[0], np.cumsum([len(r) for _, r in mols])])
+    c_all = torch.from_numpy(np.concatenate([m[0] for m in mols])).cuda()
+    r_all = torch.from_numpy(np.concatenate([m[1] for m in mols])).cuda()
+    n_all = int(offsets[-1])
+    bx = ac.AlphaComplex(c_all, r_all, 0.0, offsets=offsets)
+    ms = time_builds(bx, steps, warm, stream, flush)
+    batched = n_all * steps / (sum(ms) / 1e3)
+    bx.close()
+    del bx
+    singles = [ac.AlphaComplex(c_all[offsets[m]:offsets[m + 1]], r_all[offsets[m]:offsets[m + 1]], 0.0)
+               for m in range(len(mols))]
+    for cx in singles:
+        cx.build(stream)
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for cx in singles:
+        cx.build(stream)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    per_mol = n_all / (t0.elapsed_time(t1) / 1e3)
+    for cx in singles:
+        cx.close()
+    out["batch1024_probe"] = {"n_atoms": n_all, "batched_atoms_per_s": batched, "batched_ms": sum(ms) / steps,
+                              "per_molecule_atoms_per_s": per_mol}
+    return out
+
+
 def run_e2e(args, rank, world, steps):
     """Whole public-API round trip with host buffers (pinned)."""
     import torch
@@ -363,6 +437,8 @@ def main():
     }
     if not args.no_e2e:
         line["e2e"] = run_e2e(args, rank, world, max(2, min(args.steps, 5)))
+    if rank == 0 and world == 1 and not args.no_forms:
+        line["forms"] = run_forms(args)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args)
     if rank == 0:

@@ -87,7 +87,8 @@ typedef struct {
     int64_t ac2_tests_tet[3];
     int64_t ac2_tests_tri[3];
     int64_t ac2_tests_edge; /* exact 64-bit integers */
-    int64_t ac3_tests[4];   /* per dimension, exact integers */
+    int64_t ac3_tests[4];   /* AC3 tests per dimension (edges: exact 64-bit integers) */
+    int64_t ac3_exact;      /* triangle/tetrahedron AC3 tests the filter left to exact integers */
     double ms_total;        /* device time of the last ac_build (CUDA events) */
     double ms_stage[8];     /* grid, neighbours, per-atom pass, canonical K3, K2, K1+K0+lists, filtration,
                                and the per-atom kernel's own launch */
@@ -192,6 +193,16 @@ AC_API int ac_backward(ac_ctx* ctx, const double* const d_dLdf[4], double* d_dLd
  */
 AC_API int ac_backward_noalloc(ac_ctx* ctx, const double* const d_dLdf[4], double* d_dLdcentres, double* d_dLdradii,
                                void* stream);
+
+/*
+ * Choose the grid cell side (cell_factor in units of sqrt(r_max^2 + alpha))
+ * and the warps per block of the per-atom kernel by timing builds of this
+ * context over a small grid of both (about two dozen builds); the fastest is
+ * kept in the context, a final ac_build leaves valid results, and the choice
+ * is copied to *chosen (may be NULL). Results do not depend on the choice.
+ * Same errors as ac_build.
+ */
+AC_API int ac_autotune(ac_ctx* ctx, void* stream, ac_options* chosen);
 
 /* Counters and stage times of the last ac_build. */
 AC_API int ac_get_stats(ac_ctx* ctx, ac_stats* out);

@@ -36,7 +36,7 @@ AC_FILTRATION_ORTHOSIZE = 1
 
 # every symbol include/alphac.h declares
 EXPORTS = ["ac_create", "ac_create_batch", "ac_build", "ac_get_simplices", "ac_filtration_values", "ac_attached_flags",
-           "ac_get_candidates", "ac_eval_filtration", "ac_backward", "ac_backward_noalloc", "ac_get_stats",
+           "ac_get_candidates", "ac_eval_filtration", "ac_backward", "ac_backward_noalloc", "ac_autotune", "ac_get_stats",
            "ac_get_sizes", "ac_destroy", "ac_error_string", "ac_last_error_detail"]
 
 
@@ -50,7 +50,8 @@ class ac_stats(ctypes.Structure):
     _fields_ = [("n_atoms", ctypes.c_int64), ("candidates", ctypes.c_int64 * 4), ("simplices", ctypes.c_int64 * 4),
                 ("neighbour_pairs", ctypes.c_int64), ("max_degree", ctypes.c_int32), ("grid_dims", ctypes.c_int32 * 3),
                 ("ac2_tests_tet", ctypes.c_int64 * 3), ("ac2_tests_tri", ctypes.c_int64 * 3),
-                ("ac2_tests_edge", ctypes.c_int64), ("ac3_tests", ctypes.c_int64 * 4), ("ms_total", ctypes.c_double),
+                ("ac2_tests_edge", ctypes.c_int64), ("ac3_tests", ctypes.c_int64 * 4), ("ac3_exact", ctypes.c_int64),
+                ("ms_total", ctypes.c_double),
                 ("ms_stage", ctypes.c_double * 8), ("kernel_launches", ctypes.c_int64)]
 
     def to_dict(self):
@@ -87,6 +88,7 @@ def _declare(lib):
     lib.ac_eval_filtration.argtypes = [vp, vp, vp, vp, vp]
     lib.ac_backward.argtypes = [vp, vp, vp, vp, vp]
     lib.ac_backward_noalloc.argtypes = [vp, vp, vp, vp, vp]
+    lib.ac_autotune.argtypes = [vp, vp, P(ac_options)]
     lib.ac_get_stats.argtypes = [vp, P(ac_stats)]
     lib.ac_get_sizes.argtypes = [vp, P(i64), P(i64)]
     lib.ac_destroy.argtypes = [vp]
@@ -235,6 +237,12 @@ class AlphaComplex:
             return torch.zeros((0, dim + 1), dtype=torch.int32, device="cuda")
         t = torch.as_tensor(_DeviceArray(p.value, (cnt.value, dim + 1), "<i4"), device="cuda")
         return t.clone() if copy else t
+
+    def autotune(self, stream=None) -> dict:
+        """Time builds over cell size and block shape, keep the fastest (results unchanged)."""
+        o = ac_options()
+        _check(lib().ac_autotune(self._h, _stream_ptr(stream), ctypes.byref(o)), "ac_autotune")
+        return {"cell_factor": o.cell_factor, "block_warps": o.block_warps}
 
     def stats(self) -> dict:
         s = ac_stats()

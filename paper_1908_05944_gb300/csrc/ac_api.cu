@@ -477,6 +477,7 @@ extern "C" int ac_build(ac_ctx* c, void* stream) {
     }
     st.ac2_tests_edge = (int64_t)h.ac2_edge;
     for (int d = 0; d < 4; d++) st.ac3_tests[d] = (int64_t)h.ac3[d];
+    st.ac3_exact = (int64_t)h.ac3_exact;
     st.ms_stage[0] = elapsed(c->ev[0], c->ev[1]);
     st.ms_stage[1] = elapsed(c->ev[1], c->ev[2]);
     st.ms_stage[2] = elapsed(c->ev[2], c->ev[3]);
@@ -556,6 +557,35 @@ extern "C" int ac_backward_noalloc(ac_ctx* c, const double* const d_dLdf[4], dou
     if (!c || !d_dLdf || !d_dLdcentres || !d_dLdradii) return fail(AC_ERR_INVALID_ARG, "bad argument");
     if (!c->built) return fail(AC_ERR_STATE, "no successful ac_build on this context");
     return backward_noalloc(c, d_dLdf, d_dLdcentres, d_dLdradii, (cudaStream_t)stream);
+}
+
+extern "C" int ac_autotune(ac_ctx* c, void* stream, ac_options* chosen) {
+    if (!c) return fail(AC_ERR_INVALID_ARG, "ctx is NULL");
+    // grid cell side (in units of h) and warps per block of the per-atom kernel
+    const double factors[4] = {1.0, 1.25, 1.5, 2.0};
+    const int warps[3] = {4, 6, 8};
+    const ac_options base = c->opt;
+    ac_options best = base;
+    double best_ms = INFINITY;
+    for (double f : factors)
+        for (int w : warps) {
+            c->opt = base;
+            c->opt.cell_factor = f;
+            c->opt.block_warps = w;
+            double ms = 0.0;
+            for (int rep = 0; rep < 2; rep++) {  // the first build of a shape also sizes its buffers
+                AC_TRY(ac_build(c, stream));
+                ms = c->stats.ms_total;
+            }
+            if (ms < best_ms) {
+                best_ms = ms;
+                best = c->opt;
+            }
+        }
+    c->opt = best;
+    AC_TRY(ac_build(c, stream));
+    if (chosen) *chosen = best;
+    return AC_OK;
 }
 
 extern "C" int ac_get_stats(ac_ctx* c, ac_stats* out) {

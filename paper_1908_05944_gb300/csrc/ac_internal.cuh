@@ -53,6 +53,7 @@ enum : uint32_t {
     DERR_OVF_CAND = 1u << 6,     // a candidate list full
     DERR_DEGREE = 1u << 7,       // neighbour count above the kernel's mask width
     DERR_INTERNAL = 1u << 8,     // an invariant of the method failed (a bug)
+    DERR_OVF_PEND = 1u << 9,     // pending (escalated) list full
 };
 
 // ---------------------------------------------------------------------------
@@ -88,7 +89,11 @@ struct DevCounters {
     unsigned long long ac2_tri[3];
     unsigned long long ac2_edge;
     unsigned long long ac3[4];
-    unsigned long long work_next;     // persistent-kernel work counter
+    unsigned long long ac3_exact;     // AC3 decisions left to exact integers
+    unsigned long long n_pending;     // simplices escalated to the resolve kernel
+    unsigned long long work_next;     // persistent-kernel work counter (all atoms)
+    unsigned long long work_next2;    // work counter over the wide-row list
+    unsigned long long n_wide;        // atoms deferred to the wide-row launch
     unsigned int err;
     int max_degree;
     int bad_index;
@@ -167,7 +172,9 @@ struct ac_ctx {
     ac::DevBuf edge_pass; // int2
     ac::DevBuf vert_pass; // uint8 per sorted atom
     ac::DevBuf cand[4];   // Sigma^d candidate lists when kept (int4 / int2)
-    int64_t cap_tet = 0, cap_tri = 0, cap_edge = 0, cap_cand[4] = {0, 0, 0, 0};
+    ac::DevBuf pending;   // int4 escalated simplices (see ac_local.cu)
+    ac::DevBuf wide;      // int32 atoms with more neighbours than the narrow kernel holds
+    int64_t cap_tet = 0, cap_tri = 0, cap_edge = 0, cap_cand[4] = {0, 0, 0, 0}, cap_pending = 0;
 
     // canonical results; Gbuf/CGbuf hold the same rows as int4 of global input indices
     ac::SimplexList K[4];

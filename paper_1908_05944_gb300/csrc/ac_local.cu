@@ -1,67 +1,86 @@
 // The per-atom pass: potential simplices (Section 4.3, Step 1 of Section 3.1)
-// and their AC2 tests (Section 4.4, Steps 2-5), fused in one kernel.
+// and their AC2 tests (Section 4.4, Steps 2-5), fused in one kernel, plus the
+// kernel that settles the cases its floating-point bounds left open.
 //
 // Ownership. A simplex is owned by its vertex with the lowest sorted position
 // i. One warp handles one owner at a time and works entirely inside L(i), the
 // list of i's neighbours (atoms whose grown balls meet i's, ac_grid.cu), held
-// in shared memory as exact integer offsets q_x = P_x - P_i together with
-// a_x = |q_x|^2 - W_x + W_i. Bitmasks over positions in L(i) (WORDS 32-bit
-// words, so |L(i)| <= 32 * WORDS) carry every relation:
+// in shared memory as offsets q_x = P_x - P_i (exact integers, exact in FP32
+// because |q| <= 2h <= 2^13) and a_x = |q_x|^2 - W_x + W_i. Bitmasks over
+// positions in L(i) (WORDS 32-bit words, |L(i)| <= 32 * WORDS) carry:
 //   up       positions x > i with edge (i,x) in Sigma_ortho^1 (edge AC3 exact)
 //   M[p]     positions adjacent to p (grown balls meet), for p in up
 //   T[p]     positions k > p with triangle (i,p,k) in Sigma_ortho^2
 // Potential triangles are pairs (p,k), k in M[p] & up, k > p; potential
 // tetrahedra are (p,k,l) with l in T[p] & T[k]. Monotonicity of OrthoSize
-// (Section 4.3) makes this complete: every face of a simplex in Sigma_ortho is
-// in Sigma_ortho. AC3 is then decided exactly for each candidate.
+// (Section 4.3) makes this complete. Candidates are enumerated by random
+// access: per-row counts, a prefix sum, and candidate j -> row by binary
+// search -> vertex as the rank-th set bit, 32 candidates per warp step.
 //
-// AC2 at the orthocentre c of sigma. Every ball x that violates it (ties
-// included) has pi(c, b_x) <= OrthoSize(sigma) <= alpha, so its grown ball
-// contains c, as does every vertex's; x is therefore adjacent to all vertices:
-// the candidates are M[p] & M[k] & M[l] (all of L(i) for the vertex i itself),
-// not a stencil of cells around c. For each candidate,
-//   Delta_x = pi(c, b_x) - pi(c, b_i) = a_x - 2 q_x . y,  y = c - P_i,
-// and AC2 fails iff some Delta_x < 0 (ties: symbolic perturbation below).
+// AC2 at the orthocentre c = P_i + y of sigma. Every ball x that violates it
+// (ties included) has pi(c, b_x) <= OrthoSize(sigma) <= alpha, so its grown
+// ball contains c, as does every vertex's: x is adjacent to all vertices, so
+// the candidates are M[p] & M[k] & M[l] (all of L(i) for the vertex i).
+//   Delta_x = pi(c, b_x) - pi(c, b_i) = a_x - 2 q_x . y;  AC2 fails iff some
+//   Delta_x < 0 (Delta_x = 0 is settled by the symbolic perturbation below).
 //
-// Predicate cascade (precision AC_PRECISION_FILTERED). y is formed from exact
-// integer minors (tetrahedron: y = N / (2D), N = a1 (q2 x q3) + a2 (q3 x q1) +
-// a3 (q1 x q2), D = det(q1, q2, q3); triangle: y = mu1 q1 + mu2 q2 with
-// mu = adj(G) a / (2 det G), G the Gram matrix), rounded once to FP32, and
-// Delta is evaluated in FP32 with a static forward error bound:
-//   |fl(Delta) - Delta| <= u|fl(Delta)|(1+u) + u|a_x| + 2 gamma_3 |q_x||y~|
-//                          + 2 |q_x| |y~ - y|
-// with u = 2^-24, gamma_3 = 3u/(1-3u), |q_x| <= 2h (x is a neighbour of i),
-// |y| <= h (OrthoSize <= alpha gives |y|^2 <= W_i + A <= h^2) and
-// |a_x| <= 4h^2 + max W. For a tetrahedron |y~_c - y_c| <= 4.0001u |y_c|
-// (three roundings of N, D and one of the reciprocal, one of the product);
-// for a triangle the bound is accumulated per triangle from |mu~| |q|.
-// Undecided cases are recomputed in FP64 with the same bound at u = 2^-53,
-// then decided exactly in 128-bit integers. AC_PRECISION_PLAIN_FP64 starts at
-// the FP64 level. Edges and vertices are decided in exact 64-bit integers.
+// Bounded floating point. k_local evaluates y and every Delta_x in one
+// precision R (FP32 for AC_PRECISION_FILTERED, FP64 for
+// AC_PRECISION_PLAIN_FP64) with a rigorous bound e_y on |y~_c - y_c| for every
+// component (u = unit roundoff of R, gamma_3 = 3u/(1-3u), H = 2h >= |q| for
+// every q in L(i), A_m = 4h^2 + max W >= |a|; bounds use upward rounding):
+//   tetrahedron: C_k = q_{k+1} x q_{k+2} by FMA, |C~ - C| <= e_C = 2u(1+u)H^2;
+//     D = q_1.C_1, |D~ - D| <= e_D = gamma_3 (H^3 + sqrt3 H e_C) + sqrt3 H e_C;
+//     N = sum a_k C_k, |N~_c - N_c| <= e_N = 6.001 u H^2 sum|a~_k|;
+//     y = N / (2D), rho = e_D/|D~| <= 1/8, Y = max_c |y~_c|:
+//     e_y = (e_N/(2|D~|) + Y (rho + 2.01u)) (1+2.01u) / (1 - rho(1+2.01u) - 2.01u).
+//   triangle: Gram entries by FMA, |g~ - g| <= gamma_3 H^2; det = g11 g22 - g12^2,
+//     |det~ - det| <= e_det = 15.01 u H^4; n = adj(G) a, |n~ - n| <= 6.01 u H^2
+//     (|a~_1| + |a~_2|); mu = n / (2 det) bounded as y above (e_mu); y = mu_1 q_1
+//     + mu_2 q_2, e_y = 2.0001 u (|mu~_1| + |mu~_2|) H + 2 H e_mu.
+//   edge: D = |q|^2 (|D~ - D| <= gamma_3 H^2), mu = a / (2D), y = mu q.
+// AC3 (|y|^2 <= W_i + A, since |y|^2 - W_i is OrthoSize): S~ = fl(|y~|^2),
+// |S~ - |y|^2| <= gamma_3 S~ (1 + gamma_3) + e_y (2|y~|_1 + 3 e_y); W_i + A <=
+// 2^24 is exact. AC2: |fl(Delta) - Delta| <= u|fl(Delta)|(1+u) + u A_m +
+// 2 gamma_3 H |y~| + 2 sqrt3 H e_y, and |y| <= h once AC3 holds, so a test is
+// decided when |fl(Delta)| > (K0 + K1 e_y)(1 + 1.01u), K0 = u A_m +
+// 2 gamma_3 H h, K1 = 2 sqrt3 H (1 + gamma_3).
+// A simplex whose AC3, or whose AC2 with no decided violator, stays open is
+// appended to a pending list (an undecided triangle still counts as potential
+// for the enumeration of tetrahedra: a superset is harmless there). k_resolve
+// settles each pending simplex with one thread: exact AC3, then every AC2 test
+// in FP64 from the exact integer minors (relative error <= 4.0001 u_64 per
+// component of y) and, where that is undecided too, in exact 128-bit integers.
+// Keeping the exact arithmetic out of k_local keeps its register budget small.
+// Edge AC3 and the vertex test are exact 64-bit integers in every mode.
 //
-// Ties (Section 2, symbolic perturbation): squared radii W_k + eps_k with
-// eps_k falling steeply in the INPUT index k. Delta_x is affine in the
-// weights; its coefficient on W_x is -|D| < 0, on W_v (v a vertex of sigma)
-// it is |D| lambda_v(x), lambda the affine coordinates of x (projected onto
-// aff(sigma)) in the vertices of sigma. When Delta_x = 0 the coefficient of the
-// smallest input index with a non-zero coefficient gives the sign.
+// Ties (Section 2, symbolic perturbation): squared radii W_k + eps_k with eps_k
+// falling steeply in the INPUT index k. Delta_x is affine in the weights; its
+// coefficient on W_x is -|D| < 0, on W_v (v a vertex of sigma) it is
+// |D| lambda_v(x), lambda the affine coordinates of the projection of x on
+// aff(sigma). When Delta_x = 0 the coefficient of the smallest input index with
+// a non-zero coefficient gives the sign:
 //   tetrahedron: D lambda_k = det(Q with row k replaced by q_x) = q_x . C_k
 //   triangle:    detG lambda = adj(G) (q_1.q_x, q_2.q_x)
 //   edge:        D lambda_1 = q.q_x
-// and lambda_i = 1 - sum of the others. Exact 64-bit integers.
+// and lambda_i = 1 - sum of the others (exact 64-bit integers).
+#include <math.h>
+
 #include "ac_internal.cuh"
 
 namespace ac {
 
 constexpr unsigned FULL = 0xffffffffu;
 constexpr int STAGE = 64;
+constexpr int PAIR_CHUNK = 128;
 
 template <int WORDS>
 struct WarpSmem {
     static constexpr int M = 32 * WORDS;
-    int4 q[M];      // (qx, qy, qz, a_x) exact
-    float4 qf[M];   // the same in FP32 (a_x rounded)
+    float4 qf[M];   // (qx, qy, qz, a_x): coordinates exact, a_x rounded once
+    int ai[M];      // a_x exact
     int s[M];       // W_x + A
+    float rs[M];    // sqrt(W_x + A) rounded up
     int gid[M];     // input index
     int idx[M];     // sorted position
     unsigned Mrow[M][WORDS];
@@ -70,9 +89,25 @@ struct WarpSmem {
     unsigned char uplist[M];
     int n_up;
     int n_tet, n_tri, n_edge;
+    int rowpre[M + 1];                // prefix sums of candidate counts per row of up
+    int pairpre[PAIR_CHUNK + 1];      // prefix sums of tetrahedron candidates per Sigma^2 pair
+    unsigned short pairs[PAIR_CHUNK]; // Sigma^2 pairs (p | k << 8) of the current chunk
     int4 st_tet[STAGE];
     int4 st_tri[STAGE];
     int2 st_edge[STAGE];
+};
+
+// Constants of the bounds for one precision (derivation in the header comment).
+template <class R>
+struct Bounds {
+    R H, K0, K1, eC, eD_tet, cN, eG, eDet, cn;
+    R k2;   // 2.01 u
+    R ky;   // 2.0001 u
+    R ke;   // 1.0001 u
+    R u;
+    R g3s;    // gamma_3 (1 + gamma_3)
+    R up1;    // >= 1 + 1.01 u
+    R two_up; // >= 2 (1 + 2u): 1/|X~| <= |rcp(2 X~)| two_up
 };
 
 struct LocalArgs {
@@ -81,12 +116,17 @@ struct LocalArgs {
     const int64_t* nb_off;
     const int32_t* nb;
     int64_t n;
+    // Work of one launch: atoms 0..n-1 (work == nullptr), or work[0..*n_work-1].
+    // Atoms with more neighbours than the launch's rows hold go to defer[] when
+    // it is set, else they raise DERR_DEGREE.
+    const int32_t* work;
+    const unsigned long long* n_work;
+    int32_t* defer;
     PredConst pc;
-    // FP32/FP64 triangle thresholds: E = (k0 + k1 * e) where e bounds |y~ - y|
-    float tri_k0_32, tri_k1_32;
-    double tri_k0_64, tri_k1_64;
-    float tet_eps32;
-    double tet_eps64;
+    Bounds<float> b32;
+    Bounds<double> b64;
+    // FP64 thresholds of the resolve kernel (y from exact minors)
+    double tet_eps64, tri_k0_64, tri_k1_64;
     int4* tet_out;
     int64_t cap_tet;
     int4* tri_out;
@@ -94,6 +134,8 @@ struct LocalArgs {
     int2* edge_out;
     int64_t cap_edge;
     uint8_t* vert_pass;
+    int4* pending;
+    int64_t cap_pending;
     int4* cand3;
     int4* cand2;
     int2* cand1;
@@ -101,11 +143,56 @@ struct LocalArgs {
     DevCounters* cnt;
 };
 
-struct LaneCounts {
-    unsigned tet[3], tri[3], edge;
-    unsigned ac3[4];
-    unsigned cand[4];
+// ---------------------------------------------------------------------------
+// directed-rounding arithmetic in one precision
+
+template <class R>
+struct Ar;
+
+template <>
+struct Ar<float> {
+    static __device__ __forceinline__ float fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+    static __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
+    static __device__ __forceinline__ float mul_up(float a, float b) { return __fmul_ru(a, b); }
+    static __device__ __forceinline__ float mul_dn(float a, float b) { return __fmul_rd(a, b); }
+    static __device__ __forceinline__ float fma_up(float a, float b, float c) { return __fmaf_ru(a, b, c); }
+    static __device__ __forceinline__ float add_up(float a, float b) { return __fadd_ru(a, b); }
+    static __device__ __forceinline__ float sub_dn(float a, float b) { return __fsub_rd(a, b); }
+    static __device__ __forceinline__ float rcp(float a) { return __frcp_rn(a); }
+    static __device__ __forceinline__ float abs(float a) { return fabsf(a); }
+    static __device__ __forceinline__ float max(float a, float b) { return fmaxf(a, b); }
 };
+
+template <>
+struct Ar<double> {
+    static __device__ __forceinline__ double fma(double a, double b, double c) { return __fma_rn(a, b, c); }
+    static __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
+    static __device__ __forceinline__ double mul_up(double a, double b) { return __dmul_ru(a, b); }
+    static __device__ __forceinline__ double mul_dn(double a, double b) { return __dmul_rd(a, b); }
+    static __device__ __forceinline__ double fma_up(double a, double b, double c) { return __fma_ru(a, b, c); }
+    static __device__ __forceinline__ double add_up(double a, double b) { return __dadd_ru(a, b); }
+    static __device__ __forceinline__ double sub_dn(double a, double b) { return __dsub_rd(a, b); }
+    static __device__ __forceinline__ double rcp(double a) { return __drcp_rn(a); }
+    static __device__ __forceinline__ double abs(double a) { return fabs(a); }
+    static __device__ __forceinline__ double max(double a, double b) { return fmax(a, b); }
+};
+
+template <class R>
+struct P4 {
+    R x, y, z, w;  // offset from P_i and a_x
+};
+
+// Position e of L(i) in precision R: FP32 uses the rounded a_x; FP64 takes the
+// exact coordinates from FP32 and a_x exactly from the integer copy.
+template <class R, int WORDS>
+__device__ __forceinline__ P4<R> point(const WarpSmem<WORDS>& S, int e) {
+    const float4 v = S.qf[e];
+    if (sizeof(R) == 4) return {(R)v.x, (R)v.y, (R)v.z, (R)v.w};
+    return {(R)v.x, (R)v.y, (R)v.z, (R)S.ai[e]};
+}
+
+// ---------------------------------------------------------------------------
+// warp helpers
 
 __device__ __forceinline__ unsigned lanemask_lt() {
     unsigned m;
@@ -127,47 +214,6 @@ __device__ __forceinline__ int nth_set_bit(unsigned m, int r) {
         }
     }
     return pos;
-}
-
-// Warp-cooperative expansion: each lane holds (tag, mask); f(valid, tag, bit) is
-// called by every lane, 32 (tag, bit) pairs per round, until all set bits of
-// all lanes' masks have been visited.
-template <int WORDS, class F>
-__device__ __forceinline__ void warp_expand(const int lane, const unsigned (&mask)[WORDS], const int tag, F&& f) {
-    int cnt = 0;
-#pragma unroll
-    for (int w = 0; w < WORDS; w++) cnt += __popc(mask[w]);
-    int incl = cnt;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        int t = __shfl_up_sync(FULL, incl, o);
-        if (lane >= o) incl += t;
-    }
-    const int total = __shfl_sync(FULL, incl, 31);
-    const int excl = incl - cnt;
-    for (int base = 0; base < total; base += 32) {
-        const int j = base + lane;
-        int o = 0;
-#pragma unroll
-        for (int step = 16; step >= 1; step >>= 1) {
-            int cand = o + step;
-            int e = __shfl_sync(FULL, excl, cand & 31);
-            if (cand < 32 && e <= j) o = cand;
-        }
-        int r = j - __shfl_sync(FULL, excl, o);
-        int otag = __shfl_sync(FULL, tag, o);
-        int bit = -1;
-#pragma unroll
-        for (int w = 0; w < WORDS; w++) {
-            unsigned mw = __shfl_sync(FULL, mask[w], o);
-            int pc = __popc(mw);
-            if (bit < 0 && j < total) {
-                if (r < pc) bit = 32 * w + nth_set_bit(mw, r);
-                else r -= pc;
-            }
-        }
-        f(j < total, otag, bit);
-    }
 }
 
 template <class T>
@@ -202,9 +248,10 @@ __device__ __forceinline__ void stage_push(const int lane, bool want, const T& i
     __syncwarp();
 }
 
+// warp-aggregated append of the lanes with want set
 template <class T>
 __device__ __forceinline__ void append_direct(bool want, const T& item, T* out, unsigned long long* counter, int64_t cap,
-                                              unsigned* err) {
+                                              unsigned* err, unsigned bit) {
     unsigned b = __ballot_sync(FULL, want);
     if (b == 0) return;
     const int lane = threadIdx.x & 31;
@@ -215,41 +262,220 @@ __device__ __forceinline__ void append_direct(bool want, const T& item, T* out, 
     if (want) {
         unsigned long long slot = base + __popc(b & lanemask_lt());
         if ((int64_t)slot < cap) out[slot] = item;
-        else atomicOr(err, DERR_OVF_CAND);
+        else atomicOr(err, bit);
     }
 }
 
-// smallest input index among the candidates with a non-zero coefficient
-// decides the sign of a Delta that is exactly zero. Returns true if Delta_eps < 0.
-__device__ __forceinline__ bool sos_violates(int nv, const int* g, const long long* coef, int gx) {
-    int best = gx;
-    int sign = -1;  // the test ball's own coefficient is negative
-    for (int k = 0; k < nv; k++)
-        if (coef[k] != 0 && g[k] < best) {
-            best = g[k];
-            sign = coef[k] > 0 ? 1 : -1;
-        }
-    return sign < 0;
+// largest r in [0, n) with pre[r] <= j (pre non-decreasing, pre[0] = 0 <= j)
+__device__ __forceinline__ int row_of(const int* pre, int n, int j) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (pre[mid] <= j) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
 }
 
-__device__ __forceinline__ i128 mul64x64(long long a, long long b) { return (i128)a * (i128)b; }
+// warp-wide exclusive prefix sum of per-lane counts c; the total goes to *tot
+__device__ __forceinline__ int warp_excl(int lane, int c, int* tot) {
+    int incl = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(FULL, incl, o);
+        if (lane >= o) incl += t;
+    }
+    *tot = __shfl_sync(FULL, incl, 31);
+    return incl - c;
+}
+
+// bits of word w of a row that lie above position p
+__device__ __forceinline__ unsigned above_mask(int w, int p) {
+    if (32 * w + 31 <= p) return 0u;
+    if (32 * w > p) return FULL;
+    return ~((2u << (p & 31)) - 1u);
+}
+
+// position of the rank-th set bit of the multi-word mask f(w), w < nw
+template <class F>
+__device__ __forceinline__ int nth_in_words(int nw, int rank, F&& f) {
+    for (int w = 0; w < nw; w++) {
+        const unsigned mw = f(w);
+        const int pc = __popc(mw);
+        if (rank < pc) return 32 * w + nth_set_bit(mw, rank);
+        rank -= pc;
+    }
+    return 0;
+}
+
+// ---------------------------------------------------------------------------
+// orthocentres with error bounds (see the header comment)
+
+template <class R>
+struct Ortho {
+    R y0, y1, y2;
+    R ey;     // bound on |y~_c - y_c|, every c
+    int ac3;  // +1 holds, -1 fails, 0 undecided
+};
+
+// AC3 from y~ and its bound: |y|^2 <= T (T exact)
+template <class R>
+__device__ __forceinline__ int ac3_from(const Ortho<R>& o, R T, const Bounds<R>& B) {
+    using A = Ar<R>;
+    const R S = A::fma(o.y2, o.y2, A::fma(o.y1, o.y1, A::mul(o.y0, o.y0)));
+    const R l1 = A::add_up(A::add_up(A::abs(o.y0), A::abs(o.y1)), A::abs(o.y2));
+    const R eS = A::fma_up(o.ey, A::fma_up(R(3), o.ey, A::mul_up(R(2), l1)), A::mul_up(B.g3s, S));
+    if (A::sub_dn(S, eS) > T) return -1;
+    if (A::add_up(S, eS) < T) return 1;
+    return 0;
+}
+
+// Bound of a quotient y = N / (2X) computed as fl(N~ r~), r~ = rcp(2 X~):
+// e = (eN/(2|X~|) + Y (rho + k)) (1 + k) / (1 - rho (1 + k) - k), k = 2.01u,
+// with rho = e_X/|X~| <= 1/8. No division: 1/|X~| <= inv = 2|r~|(1 + 2u) and
+// 1/(1 - x) <= 1 + 2x for x <= 1/2.
+template <class R>
+__device__ __forceinline__ R quotient_bound(R eN, R inv, R Y, R rho, const Bounds<R>& B) {
+    using A = Ar<R>;
+    const R k = B.k2;
+    const R num = A::mul_up(A::fma_up(Y, A::add_up(rho, k), A::mul_up(eN, R(0.5) * inv)), R(1) + k);
+    const R x = A::fma_up(rho, R(1) + k, k);
+    return A::mul_up(num, A::fma_up(R(2), x, R(1)));
+}
+
+template <class R>
+__device__ __forceinline__ R cross_c(R bs, R et, R bt, R es) {
+    return Ar<R>::fma(bs, et, -Ar<R>::mul(bt, es));
+}
+
+template <class R>
+__device__ __forceinline__ Ortho<R> ortho_tet(const P4<R>& q1, const P4<R>& q2, const P4<R>& q3, R T,
+                                              const Bounds<R>& B) {
+    using A = Ar<R>;
+    Ortho<R> o;
+    // C1 = q2 x q3, C2 = q3 x q1, C3 = q1 x q2
+    const R c1x = cross_c(q2.y, q3.z, q2.z, q3.y), c1y = cross_c(q2.z, q3.x, q2.x, q3.z),
+            c1z = cross_c(q2.x, q3.y, q2.y, q3.x);
+    const R c2x = cross_c(q3.y, q1.z, q3.z, q1.y), c2y = cross_c(q3.z, q1.x, q3.x, q1.z),
+            c2z = cross_c(q3.x, q1.y, q3.y, q1.x);
+    const R c3x = cross_c(q1.y, q2.z, q1.z, q2.y), c3y = cross_c(q1.z, q2.x, q1.x, q2.z),
+            c3z = cross_c(q1.x, q2.y, q1.y, q2.x);
+    const R D = A::fma(q1.z, c1z, A::fma(q1.y, c1y, A::mul(q1.x, c1x)));
+    const R r = A::rcp(R(2) * D);
+    const R inv = A::mul_up(A::abs(r), B.two_up);  // >= 1/|D~|
+    const R rho = A::mul_up(B.eD_tet, inv);         // D~ = 0 gives inf: undecided
+    if (!(rho <= R(0.125))) {
+        o.ac3 = 0;
+        o.ey = R(INFINITY);
+        o.y0 = o.y1 = o.y2 = R(0);
+        return o;
+    }
+    const R Nx = A::fma(q3.w, c3x, A::fma(q2.w, c2x, A::mul(q1.w, c1x)));
+    const R Ny = A::fma(q3.w, c3y, A::fma(q2.w, c2y, A::mul(q1.w, c1y)));
+    const R Nz = A::fma(q3.w, c3z, A::fma(q2.w, c2z, A::mul(q1.w, c1z)));
+    o.y0 = A::mul(Nx, r);
+    o.y1 = A::mul(Ny, r);
+    o.y2 = A::mul(Nz, r);
+    const R eN = A::mul_up(B.cN, A::add_up(A::add_up(A::abs(q1.w), A::abs(q2.w)), A::abs(q3.w)));
+    const R Y = A::max(A::abs(o.y0), A::max(A::abs(o.y1), A::abs(o.y2)));
+    o.ey = quotient_bound(eN, inv, Y, rho, B);
+    o.ac3 = ac3_from(o, T, B);
+    return o;
+}
+
+template <class R>
+__device__ __forceinline__ Ortho<R> ortho_tri(const P4<R>& q1, const P4<R>& q2, R T, const Bounds<R>& B) {
+    using A = Ar<R>;
+    Ortho<R> o;
+    const R g11 = A::fma(q1.z, q1.z, A::fma(q1.y, q1.y, A::mul(q1.x, q1.x)));
+    const R g22 = A::fma(q2.z, q2.z, A::fma(q2.y, q2.y, A::mul(q2.x, q2.x)));
+    const R g12 = A::fma(q1.z, q2.z, A::fma(q1.y, q2.y, A::mul(q1.x, q2.x)));
+    const R det = A::fma(g11, g22, -A::mul(g12, g12));
+    const R r = A::rcp(R(2) * det);
+    const R inv = A::mul_up(A::abs(r), B.two_up);  // >= 1/|det~|
+    const R rho = A::mul_up(B.eDet, inv);
+    if (!(rho <= R(0.125))) {
+        o.ac3 = 0;
+        o.ey = R(INFINITY);
+        o.y0 = o.y1 = o.y2 = R(0);
+        return o;
+    }
+    const R n1 = A::fma(g22, q1.w, -A::mul(g12, q2.w));
+    const R n2 = A::fma(g11, q2.w, -A::mul(g12, q1.w));
+    const R m1 = A::mul(n1, r), m2 = A::mul(n2, r);
+    const R en = A::mul_up(B.cn, A::add_up(A::abs(q1.w), A::abs(q2.w)));
+    const R emu = quotient_bound(en, inv, A::max(A::abs(m1), A::abs(m2)), rho, B);
+    o.y0 = A::fma(m1, q1.x, A::mul(m2, q2.x));
+    o.y1 = A::fma(m1, q1.y, A::mul(m2, q2.y));
+    o.y2 = A::fma(m1, q1.z, A::mul(m2, q2.z));
+    o.ey = A::mul_up(B.H, A::fma_up(R(2), emu, A::mul_up(B.ky, A::add_up(A::abs(m1), A::abs(m2)))));
+    o.ac3 = ac3_from(o, T, B);
+    return o;
+}
+
+template <class R>
+__device__ __forceinline__ Ortho<R> ortho_edge(const P4<R>& q1, const Bounds<R>& B) {
+    using A = Ar<R>;
+    Ortho<R> o;
+    const R D = A::fma(q1.z, q1.z, A::fma(q1.y, q1.y, A::mul(q1.x, q1.x)));
+    const R r = A::rcp(R(2) * D);
+    const R inv = A::mul_up(r, B.two_up);  // >= 1/D~
+    const R rho = A::mul_up(B.eG, inv);    // eG = gamma_3 H^2 bounds |D~ - D|
+    const R m = A::mul(q1.w, r);
+    const R emu = quotient_bound(A::mul_up(B.u, A::abs(q1.w)), inv, A::abs(m), rho, B);
+    o.y0 = A::mul(m, q1.x);
+    o.y1 = A::mul(m, q1.y);
+    o.y2 = A::mul(m, q1.z);
+    o.ey = A::mul_up(B.H, A::fma_up(B.ke, A::abs(m), emu));
+    o.ac3 = 1;  // edge AC3 is decided exactly in phase A
+    return o;
+}
+
+// AC2 scan of one simplex; the candidates of word w are M[p] & M[k] & M[l]
+// (nv = 3), M[p] & M[k] (nv = 2) or M[p] (nv = 1). Returns -1 if a candidate
+// violates AC2, +1 if every test clears, 0 if none violates but some test is
+// undecided at this precision.
+template <class R, int WORDS>
+__device__ __forceinline__ int ac2_scan(const WarpSmem<WORDS>& S, int nw, const Ortho<R>& o, const Bounds<R>& B, int nv,
+                                        int p, int k, int l, unsigned& n_ok) {
+    using A = Ar<R>;
+    const R E = A::mul_up(A::fma_up(B.K1, o.ey, B.K0), B.up1);  // inf when o.ey is
+    bool open = false;
+#pragma unroll 1
+    for (int w = 0; w < nw; w++) {
+        unsigned b = S.Mrow[p][w];
+        if (nv >= 2) b &= S.Mrow[k][w];
+        if (nv == 3) b &= S.Mrow[l][w];
+        while (b) {
+            const int x = 32 * w + __ffs(b) - 1;
+            b &= b - 1;
+            const P4<R> v = point<R>(S, x);
+            const R t = A::fma(v.z, o.y2, A::fma(v.y, o.y1, A::mul(v.x, o.y0)));
+            const R d = A::fma(R(-2), t, v.w);
+            if (d < -E) return -1;
+            if (d > E) n_ok++;
+            else open = true;
+        }
+    }
+    return open ? 0 : 1;
+}
 
 // ---------------------------------------------------------------------------
 
-template <int WORDS>
+template <int WORDS, class R>
 __global__ void __launch_bounds__(256) k_local(LocalArgs A) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     using SM = WarpSmem<WORDS>;
     constexpr int MAXM = SM::M;
+    constexpr bool is32 = sizeof(R) == 4;
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     SM& S = reinterpret_cast<SM*>(smem_raw)[wib];
     DevCounters* cnt = A.cnt;
-    const PredConst& pc = A.pc;
-    const int64_t Aq = pc.A;
-    const bool filtered = pc.precision == AC_PRECISION_FILTERED;
-    LaneCounts lc;
-    memset(&lc, 0, sizeof(lc));
+    const long long Aq = A.pc.A;
+    const bool keep = A.pc.keep_candidates != 0;
+    const Bounds<R>& B = *reinterpret_cast<const Bounds<R>*>(is32 ? (const void*)&A.b32 : (const void*)&A.b64);
+    unsigned n_tet = 0, n_tri = 0, n_edge = 0, n_ac3e = 0, n_ac3t = 0, n_ac3k = 0, n_s1 = 0, n_s2 = 0, n_s3 = 0;
     if (lane == 0) {
         S.n_tet = 0;
         S.n_tri = 0;
@@ -257,12 +483,14 @@ __global__ void __launch_bounds__(256) k_local(LocalArgs A) {
     }
     __syncwarp();
 
+    const long long n_items = A.work ? (long long)*A.n_work : A.n;
+    unsigned long long* next = A.work ? &cnt->work_next2 : &cnt->work_next;
     for (;;) {
         long long i_ll = 0;
-        if (lane == 0) i_ll = (long long)atomicAdd(&cnt->work_next, 1ull);
+        if (lane == 0) i_ll = (long long)atomicAdd(next, 1ull);
         i_ll = __shfl_sync(FULL, i_ll, 0);
-        if (i_ll >= A.n) break;
-        const int i = (int)i_ll;
+        if (i_ll >= n_items) break;
+        const int i = A.work ? A.work[i_ll] : (int)i_ll;
         const int4 Pi = A.Ps[i];
         const int Wi = Pi.w;
         const long long si = (long long)Wi + Aq;
@@ -274,81 +502,94 @@ __global__ void __launch_bounds__(256) k_local(LocalArgs A) {
             continue;
         }
         if (m > MAXM) {
-            if (lane == 0) atomicOr(&cnt->err, DERR_DEGREE);
+            if (lane == 0) {
+                if (A.defer) A.defer[atomicAdd(&cnt->n_wide, 1ull)] = i;  // at most n entries
+                else atomicOr(&cnt->err, DERR_DEGREE);
+            }
             continue;
         }
+        const int nw = (m + 31) >> 5;
+        const R T = (R)si;  // W_i + A <= 2^24: exact
 
-        // ---- phase A: load L(i); upper edges with exact edge AC3 ------------
+        // ---- phase A: load L(i); vertex AC2 (Step 5); upper edges with exact edge AC3
         unsigned vert_bad = 0;
-#pragma unroll
-        for (int w = 0; w < WORDS; w++) {
+#pragma unroll 1
+        for (int w = 0; w < nw; w++) {
             const int e = 32 * w + lane;
             bool upper = false;
             if (e < m) {
                 const int x = A.nb[off + e];
                 const int4 o = A.Ps[x];
                 const int qx = o.x - Pi.x, qy = o.y - Pi.y, qz = o.z - Pi.z;
-                const int D = qx * qx + qy * qy + qz * qz;  // <= 3 * 2^26
+                const int D = qx * qx + qy * qy + qz * qz;  // <= 2^26
                 const int ax = D - o.w + Wi;
-                S.q[e] = make_int4(qx, qy, qz, ax);
                 S.qf[e] = make_float4((float)qx, (float)qy, (float)qz, (float)ax);
+                S.ai[e] = ax;
                 S.s[e] = (int)((long long)o.w + Aq);
+                S.rs[e] = __fsqrt_ru((float)((long long)o.w + Aq));  // W + A <= 2^24: exact in FP32
                 const int gx = A.order[x];
                 S.gid[e] = gx;
                 S.idx[e] = x;
-                // vertex AC2 at p_i (Step 5): Delta_x = a_x; tie -> smaller input index wins
+                // Delta_x = a_x at p_i; a tie goes against the larger input index
                 if (ax < 0 || (ax == 0 && gx < gi)) vert_bad = 1;
                 if (x > i) {
                     // edge AC3: (D + W_i - W_x)^2 <= 4 D (W_i + A)
                     const long long a = (long long)D + Wi - o.w;
                     upper = a * a <= 4ll * D * si;
-                    lc.ac3[1]++;
+                    n_ac3e++;
                 }
             }
             const unsigned b = __ballot_sync(FULL, upper);
             if (lane == 0) S.up[w] = b;
         }
+        if (lane == 0)
+            for (int w = nw; w < WORDS; w++) S.up[w] = 0u;
         vert_bad = __any_sync(FULL, vert_bad);
         if (lane == 0) A.vert_pass[i] = vert_bad ? 0 : 1;
         __syncwarp();
-        // list of upper positions
         {
             int base = 0;
-#pragma unroll
-            for (int w = 0; w < WORDS; w++) {
+#pragma unroll 1
+            for (int w = 0; w < nw; w++) {
                 const unsigned b = S.up[w];
                 if ((b >> lane) & 1u) S.uplist[base + __popc(b & lanemask_lt())] = (unsigned char)(32 * w + lane);
                 base += __popc(b);
             }
-            if (lane == 0) S.n_up = base;
-            lc.cand[1] += lane == 0 ? base : 0;
+            if (lane == 0) {
+                S.n_up = base;
+                n_s1 += base;
+            }
         }
         __syncwarp();
         const int n_up = S.n_up;
-        if (pc.keep_candidates) {
+        if (keep) {
             for (int r0 = 0; r0 < n_up; r0 += 32) {
                 const bool ok = r0 + lane < n_up;
                 const int p = ok ? S.uplist[r0 + lane] : 0;
-                append_direct(ok, make_int2(i, ok ? S.idx[p] : 0), A.cand1, &cnt->n_cand_out[1], A.cap_cand[1], &cnt->err);
+                append_direct(ok, make_int2(i, ok ? S.idx[p] : 0), A.cand1, &cnt->n_cand_out[1], A.cap_cand[1], &cnt->err,
+                              DERR_OVF_CAND);
             }
         }
 
-        // ---- phase B: adjacency rows M[p] for p in up -----------------------
+        // ---- phase B: adjacency rows M[p] for p in up ------------------------
+        // The rows only filter candidates, so they may hold more than the exact
+        // relation: |q_e - q_p|^2 rounded down <= (sqrt s_p + sqrt s_e)^2 rounded up
+        // keeps every pair whose grown balls meet (and a few more at the margin).
+#pragma unroll 1
         for (int r = 0; r < n_up; r++) {
             const int p = S.uplist[r];
-            const int4 qp = S.q[p];
-            const long long sp = S.s[p];
-#pragma unroll
-            for (int w = 0; w < WORDS; w++) {
+            const float4 qp = S.qf[p];
+            const float rp = S.rs[p];
+#pragma unroll 1
+            for (int w = 0; w < nw; w++) {
                 const int e = 32 * w + lane;
                 bool adj = false;
                 if (e < m && e != p) {
-                    const int4 qe = S.q[e];
-                    const int dx = qe.x - qp.x, dy = qe.y - qp.y, dz = qe.z - qp.z;  // |.| <= 2^14
-                    const long long D = (long long)dx * dx + (long long)dy * dy + (long long)dz * dz;
-                    const long long se = S.s[e];
-                    const long long t = D - sp - se;
-                    adj = t <= 0 || t * t <= 4 * sp * se;
+                    const float4 qe = S.qf[e];
+                    const float dx = qe.x - qp.x, dy = qe.y - qp.y, dz = qe.z - qp.z;  // exact: |.| <= 2^14
+                    const float d2 = __fmaf_rd(dz, dz, __fmaf_rd(dy, dy, __fmul_rd(dx, dx)));
+                    const float rr = __fadd_ru(rp, S.rs[e]);
+                    adj = d2 <= __fmul_ru(rr, rr);
                 }
                 const unsigned b = __ballot_sync(FULL, adj);
                 if (lane == 0) {
@@ -356,274 +597,171 @@ __global__ void __launch_bounds__(256) k_local(LocalArgs A) {
                     S.Trow[p][w] = 0u;
                 }
             }
+            if (lane == 0)
+                for (int w = nw; w < WORDS; w++) {
+                    S.Mrow[p][w] = 0u;
+                    S.Trow[p][w] = 0u;
+                }
         }
         __syncwarp();
 
-        // ---- phase C: triangles (i,p,k): AC3 exact, then AC2 -----------------
-        for (int r0 = 0; r0 < n_up; r0 += 32) {
-            const bool rowok = r0 + lane < n_up;
-            const int p = rowok ? S.uplist[r0 + lane] : 0;
-            unsigned mask[WORDS];
-#pragma unroll
-            for (int w = 0; w < WORDS; w++) {
-                unsigned above;
-                if (32 * w + 31 <= p) above = 0u;
-                else if (32 * w > p) above = FULL;
-                else above = ~((2u << (p & 31)) - 1u);
-                mask[w] = rowok ? (S.Mrow[p][w] & S.up[w] & above) : 0u;
+        // ---- phase C: triangles (i,p,k): AC3, then AC2 at the orthocentre -----
+        // candidates of row r (p = uplist[r]): k in M[p] & up, k > p
+        {
+            int run = 0;
+            for (int r0 = 0; r0 < n_up; r0 += 32) {
+                int c = 0;
+                if (r0 + lane < n_up) {
+                    const int p = S.uplist[r0 + lane];
+                    for (int w = 0; w < nw; w++) c += __popc(S.Mrow[p][w] & S.up[w] & above_mask(w, p));
+                }
+                int tot;
+                const int ex = warp_excl(lane, c, &tot);
+                if (r0 + lane < n_up) S.rowpre[r0 + lane] = run + ex;
+                run += tot;
             }
-            warp_expand<WORDS>(lane, mask, p, [&](bool valid, int pp, int kk) {
-                bool in_sigma = false, pass = false;
+            if (lane == 0) S.rowpre[n_up] = run;
+        }
+        __syncwarp();
+        {
+            const int total = S.rowpre[n_up];
+#pragma unroll 1
+            for (int base = 0; base < total; base += 32) {
+                const int j = base + lane;
+                const bool valid = j < total;
+                bool pass = false, pend = false, keep_it = false;
+                int pend_ac3 = 0;
+                int pp = 0, kk = 0;
                 if (valid) {
-                    const int4 q1 = S.q[pp], q2 = S.q[kk];
-                    const long long g11 = (long long)q1.x * q1.x + (long long)q1.y * q1.y + (long long)q1.z * q1.z;
-                    const long long g22 = (long long)q2.x * q2.x + (long long)q2.y * q2.y + (long long)q2.z * q2.z;
-                    const long long g12 = (long long)q1.x * q2.x + (long long)q1.y * q2.y + (long long)q1.z * q2.z;
-                    const long long detG = g11 * g22 - g12 * g12;
-                    lc.ac3[2]++;
-                    if (detG > 0) {
-                        const long long a1 = q1.w, a2 = q2.w;
-                        const long long n1 = g22 * a1 - g12 * a2, n2 = g11 * a2 - g12 * a1;
-                        const i128 na = mul64x64(n1, a1) + mul64x64(n2, a2);
-                        in_sigma = na <= (i128)(4 * detG) * (i128)si;
-                    }
-                    if (in_sigma) {
-                        lc.cand[2]++;
+                    const int r = row_of(S.rowpre, n_up, j);
+                    pp = S.uplist[r];
+                    kk = nth_in_words(nw, j - S.rowpre[r],
+                                      [&](int w) { return S.Mrow[pp][w] & S.up[w] & above_mask(w, pp); });
+                    n_ac3t++;
+                    const Ortho<R> o = ortho_tri<R>(point<R>(S, pp), point<R>(S, kk), T, B);
+                    if (o.ac3 >= 0) {
+                        // potential, or not yet excluded: tetrahedra may build on it
                         atomicOr(&S.Trow[pp][kk >> 5], 1u << (kk & 31));
-                        // AC2 at the triangle's orthocentre
-                        const long long a1 = q1.w, a2 = q2.w;
-                        const long long n1 = g22 * a1 - g12 * a2, n2 = g11 * a2 - g12 * a1;
-                        float y32[3] = {0.f, 0.f, 0.f}, E32 = 0.f;
-                        double y64[3] = {0.0, 0.0, 0.0}, E64 = 0.0;
-                        bool have64 = false;
-                        if (filtered) {
-                            const float rd = __frcp_rn(2.0f * __ll2float_rn(detG));
-                            const float m1 = __fmul_rn(__ll2float_rn(n1), rd), m2 = __fmul_rn(__ll2float_rn(n2), rd);
-                            const float q1f[3] = {(float)q1.x, (float)q1.y, (float)q1.z};
-                            const float q2f[3] = {(float)q2.x, (float)q2.y, (float)q2.z};
-                            float e = 0.f;
-#pragma unroll
-                            for (int c = 0; c < 3; c++) {
-                                y32[c] = __fmaf_rn(m1, q1f[c], __fmul_rn(m2, q2f[c]));
-                                e = __fmaf_ru(fabsf(m1), fabsf(q1f[c]), __fmaf_ru(fabsf(m2), fabsf(q2f[c]), e));
-                            }
-                            e = __fmul_ru(e, 6.05f * 5.9604645e-8f);
-                            E32 = __fmaf_ru(A.tri_k1_32, e, A.tri_k0_32);
+                        if (o.ac3 > 0) {
+                            n_s2++;
+                            keep_it = true;
+                            const int r2 = ac2_scan<R>(S, nw, o, B, 2, pp, kk, 0, n_tri);
+                            pass = r2 > 0;
+                            pend = r2 == 0;
+                        } else {
+                            pend = true;
+                            pend_ac3 = 1;
                         }
-                        auto make64 = [&]() {
-                            const double rd = 1.0 / (2.0 * (double)detG);
-                            const double m1 = (double)n1 * rd, m2 = (double)n2 * rd;
-                            const double q1d[3] = {(double)q1.x, (double)q1.y, (double)q1.z};
-                            const double q2d[3] = {(double)q2.x, (double)q2.y, (double)q2.z};
-                            double e = 0.0;
-                            for (int c = 0; c < 3; c++) {
-                                y64[c] = fma(m1, q1d[c], m2 * q2d[c]);
-                                e += fabs(m1) * fabs(q1d[c]) + fabs(m2) * fabs(q2d[c]);
-                            }
-                            e *= 6.05 * 1.1102230246251565e-16 * (1.0 + 1e-10);
-                            E64 = (A.tri_k0_64 + A.tri_k1_64 * e) * (1.0 + 1e-10);
-                            have64 = true;
-                        };
-                        if (!filtered) make64();
-                        unsigned V[WORDS];
-#pragma unroll
-                        for (int w = 0; w < WORDS; w++) V[w] = S.Mrow[pp][w] & S.Mrow[kk][w];
-                        bool violated = false;
-#pragma unroll
-                        for (int w = 0; w < WORDS; w++) {
-                            unsigned b = V[w];
-                            while (b && !violated) {
-                                const int x = 32 * w + __ffs(b) - 1;
-                                b &= b - 1;
-                                int decided = 0;  // +1 no violation, -1 violation
-                                if (filtered) {
-                                    const float4 xf = S.qf[x];
-                                    const float t = __fmaf_rn(xf.z, y32[2], __fmaf_rn(xf.y, y32[1], __fmul_rn(xf.x, y32[0])));
-                                    const float d = __fmaf_rn(-2.0f, t, xf.w);
-                                    if (d > E32) decided = 1;
-                                    else if (d < -E32) decided = -1;
-                                    if (decided) lc.tri[0]++;
-                                }
-                                if (!decided) {
-                                    if (!have64) make64();
-                                    const int4 xq = S.q[x];
-                                    const double t = fma((double)xq.z, y64[2], fma((double)xq.y, y64[1], (double)xq.x * y64[0]));
-                                    const double d = fma(-2.0, t, (double)xq.w);
-                                    if (d > E64) decided = 1;
-                                    else if (d < -E64) decided = -1;
-                                    if (decided) lc.tri[1]++;
-                                }
-                                if (!decided) {
-                                    lc.tri[2]++;
-                                    const int4 xq = S.q[x];
-                                    const long long gx1 = (long long)q1.x * xq.x + (long long)q1.y * xq.y + (long long)q1.z * xq.z;
-                                    const long long gx2 = (long long)q2.x * xq.x + (long long)q2.y * xq.y + (long long)q2.z * xq.z;
-                                    const i128 v = mul64x64(xq.w, detG) - (mul64x64(n1, gx1) + mul64x64(n2, gx2));
-                                    if (v < 0) decided = -1;
-                                    else if (v > 0) decided = 1;
-                                    else {
-                                        const long long c1 = g22 * gx1 - g12 * gx2, c2 = g11 * gx2 - g12 * gx1;
-                                        const long long coef[3] = {detG - c1 - c2, c1, c2};
-                                        const int g[3] = {gi, S.gid[pp], S.gid[kk]};
-                                        decided = sos_violates(3, g, coef, S.gid[x]) ? -1 : 1;
-                                    }
-                                }
-                                violated = decided < 0;
-                            }
-                        }
-                        pass = !violated;
                     }
                 }
-                if (pc.keep_candidates)
-                    append_direct(in_sigma, make_int4(i, valid ? S.idx[pp] : 0, valid ? S.idx[kk] : 0, 0), A.cand2,
-                                  &cnt->n_cand_out[2], A.cap_cand[2], &cnt->err);
-                stage_push(lane, pass, make_int4(i, valid ? S.idx[pp] : 0, valid ? S.idx[kk] : 0, 0), S.st_tri, &S.n_tri,
-                           A.tri_out, &cnt->n_tri_pass, A.cap_tri, &cnt->err, DERR_OVF_TRI);
-            });
+                const int4 item = make_int4(i, valid ? S.idx[pp] : 0, valid ? S.idx[kk] : 0, 0);
+                if (keep)
+                    append_direct(keep_it, item, A.cand2, &cnt->n_cand_out[2], A.cap_cand[2], &cnt->err, DERR_OVF_CAND);
+                append_direct(pend, make_int4(pend_ac3 ? ~i : i, item.y, item.z, -1), A.pending, &cnt->n_pending,
+                              A.cap_pending, &cnt->err, DERR_OVF_PEND);
+                stage_push(lane, pass, item, S.st_tri, &S.n_tri, A.tri_out, &cnt->n_tri_pass, A.cap_tri, &cnt->err,
+                           DERR_OVF_TRI);
+            }
         }
         __syncwarp();
 
-        // ---- phase D: tetrahedra (i,p,k,l): AC3 exact, then AC2 --------------
-        for (int r0 = 0; r0 < n_up; r0 += 32) {
-            const bool rowok = r0 + lane < n_up;
-            const int p = rowok ? S.uplist[r0 + lane] : 0;
-            unsigned mask[WORDS];
-#pragma unroll
-            for (int w = 0; w < WORDS; w++) mask[w] = rowok ? S.Trow[p][w] : 0u;
-            warp_expand<WORDS>(lane, mask, p, [&](bool valid1, int pp, int kk) {
-                unsigned m2[WORDS];
-#pragma unroll
-                for (int w = 0; w < WORDS; w++) m2[w] = valid1 ? (S.Trow[pp][w] & S.Trow[kk][w]) : 0u;
-                const int tag = valid1 ? (pp | (kk << 8)) : 0;
-                warp_expand<WORDS>(lane, m2, tag, [&](bool valid, int pk, int ll) {
-                    bool in_sigma = false, pass = false;
-                    const int p3 = pk & 255, k3 = pk >> 8;
-                    if (valid) {
-                        const int4 q1 = S.q[p3], q2 = S.q[k3], q3 = S.q[ll];
-                        // cross products (exact in 32 bits: |q| <= 2^13 per axis)
-                        const int C1x = q2.y * q3.z - q2.z * q3.y, C1y = q2.z * q3.x - q2.x * q3.z,
-                                  C1z = q2.x * q3.y - q2.y * q3.x;
-                        const int C2x = q3.y * q1.z - q3.z * q1.y, C2y = q3.z * q1.x - q3.x * q1.z,
-                                  C2z = q3.x * q1.y - q3.y * q1.x;
-                        const int C3x = q1.y * q2.z - q1.z * q2.y, C3y = q1.z * q2.x - q1.x * q2.z,
-                                  C3z = q1.x * q2.y - q1.y * q2.x;
-                        const long long D = (long long)q1.x * C1x + (long long)q1.y * C1y + (long long)q1.z * C1z;
-                        lc.ac3[3]++;
-                        long long N[3] = {0, 0, 0};
-                        if (D != 0) {
-                            N[0] = (long long)q1.w * C1x + (long long)q2.w * C2x + (long long)q3.w * C3x;
-                            N[1] = (long long)q1.w * C1y + (long long)q2.w * C2y + (long long)q3.w * C3y;
-                            N[2] = (long long)q1.w * C1z + (long long)q2.w * C2z + (long long)q3.w * C3z;
-                            const i128 nn = mul64x64(N[0], N[0]) + mul64x64(N[1], N[1]) + mul64x64(N[2], N[2]);
-                            in_sigma = nn <= mul64x64(D, D) * (i128)(4 * si);
-                        }
-                        if (in_sigma) {
-                            lc.cand[3]++;
-                            const int sD = D > 0 ? 1 : -1;
-                            float y32[3] = {0.f, 0.f, 0.f};
-                            double y64[3] = {0.0, 0.0, 0.0};
-                            bool have64 = false;
-                            if (filtered) {
-                                const float rd = __frcp_rn(2.0f * __ll2float_rn(D));
-#pragma unroll
-                                for (int c = 0; c < 3; c++) y32[c] = __fmul_rn(__ll2float_rn(N[c]), rd);
-                            }
-                            auto make64 = [&]() {
-                                const double rd = 1.0 / (2.0 * (double)D);
-                                for (int c = 0; c < 3; c++) y64[c] = (double)N[c] * rd;
-                                have64 = true;
-                            };
-                            if (!filtered) make64();
-                            bool violated = false;
-#pragma unroll
-                            for (int w = 0; w < WORDS; w++) {
-                                unsigned b = S.Mrow[p3][w] & S.Mrow[k3][w] & S.Mrow[ll][w];
-                                while (b && !violated) {
-                                    const int x = 32 * w + __ffs(b) - 1;
-                                    b &= b - 1;
-                                    int decided = 0;
-                                    if (filtered) {
-                                        const float4 xf = S.qf[x];
-                                        const float t = __fmaf_rn(xf.z, y32[2], __fmaf_rn(xf.y, y32[1], __fmul_rn(xf.x, y32[0])));
-                                        const float d = __fmaf_rn(-2.0f, t, xf.w);
-                                        if (d > A.tet_eps32) decided = 1;
-                                        else if (d < -A.tet_eps32) decided = -1;
-                                        if (decided) lc.tet[0]++;
-                                    }
-                                    if (!decided) {
-                                        if (!have64) make64();
-                                        const int4 xq = S.q[x];
-                                        const double t = fma((double)xq.z, y64[2], fma((double)xq.y, y64[1], (double)xq.x * y64[0]));
-                                        const double d = fma(-2.0, t, (double)xq.w);
-                                        if (d > A.tet_eps64) decided = 1;
-                                        else if (d < -A.tet_eps64) decided = -1;
-                                        if (decided) lc.tet[1]++;
-                                    }
-                                    if (!decided) {
-                                        lc.tet[2]++;
-                                        const int4 xq = S.q[x];
-                                        const i128 qN = mul64x64(xq.x, N[0]) + mul64x64(xq.y, N[1]) + mul64x64(xq.z, N[2]);
-                                        i128 v = mul64x64(xq.w, D) - qN;
-                                        if (sD < 0) v = -v;
-                                        if (v < 0) decided = -1;
-                                        else if (v > 0) decided = 1;
-                                        else {
-                                            const long long D1 = (long long)xq.x * C1x + (long long)xq.y * C1y + (long long)xq.z * C1z;
-                                            const long long D2 = (long long)xq.x * C2x + (long long)xq.y * C2y + (long long)xq.z * C2z;
-                                            const long long D3 = (long long)xq.x * C3x + (long long)xq.y * C3y + (long long)xq.z * C3z;
-                                            const long long coef[4] = {sD * (D - D1 - D2 - D3), sD * D1, sD * D2, sD * D3};
-                                            const int g[4] = {gi, S.gid[p3], S.gid[k3], S.gid[ll]};
-                                            decided = sos_violates(4, g, coef, S.gid[x]) ? -1 : 1;
-                                        }
-                                    }
-                                    violated = decided < 0;
-                                }
-                            }
-                            pass = !violated;
-                        }
+        // ---- phase D: tetrahedra (i,p,k,l): AC3, then AC2 ----------------------
+        // Sigma^2 pairs (p,k): row r of up holds popc(T[p]) of them; pairs are taken
+        // PAIR_CHUNK at a time with a prefix over their candidate counts popc(T[p] & T[k])
+        {
+            int run = 0;
+            for (int r0 = 0; r0 < n_up; r0 += 32) {
+                int c = 0;
+                if (r0 + lane < n_up) {
+                    const int p = S.uplist[r0 + lane];
+                    for (int w = 0; w < nw; w++) c += __popc(S.Trow[p][w]);
+                }
+                int tot;
+                const int ex = warp_excl(lane, c, &tot);
+                if (r0 + lane < n_up) S.rowpre[r0 + lane] = run + ex;
+                run += tot;
+            }
+            if (lane == 0) S.rowpre[n_up] = run;
+        }
+        __syncwarp();
+        const int n_pairs = S.rowpre[n_up];
+#pragma unroll 1
+        for (int c0 = 0; c0 < n_pairs; c0 += PAIR_CHUNK) {
+            const int cn = min(PAIR_CHUNK, n_pairs - c0);
+            {
+                int run = 0;
+                for (int q0 = 0; q0 < cn; q0 += 32) {
+                    int c = 0;
+                    if (q0 + lane < cn) {
+                        const int j = c0 + q0 + lane;
+                        const int r = row_of(S.rowpre, n_up, j);
+                        const int p = S.uplist[r];
+                        const int k = nth_in_words(nw, j - S.rowpre[r], [&](int w) { return S.Trow[p][w]; });
+                        S.pairs[q0 + lane] = (unsigned short)(p | (k << 8));
+                        for (int w = 0; w < nw; w++) c += __popc(S.Trow[p][w] & S.Trow[k][w]);
                     }
-                    const int4 item = make_int4(i, valid ? S.idx[p3] : 0, valid ? S.idx[k3] : 0, valid ? S.idx[ll] : 0);
-                    if (pc.keep_candidates)
-                        append_direct(in_sigma, item, A.cand3, &cnt->n_cand_out[3], A.cap_cand[3], &cnt->err);
-                    stage_push(lane, pass, item, S.st_tet, &S.n_tet, A.tet_out, &cnt->n_tet_out, A.cap_tet, &cnt->err,
-                               DERR_OVF_TET);
-                });
-            });
+                    int tot;
+                    const int ex = warp_excl(lane, c, &tot);
+                    if (q0 + lane < cn) S.pairpre[q0 + lane] = run + ex;
+                    run += tot;
+                }
+                if (lane == 0) S.pairpre[cn] = run;
+            }
+            __syncwarp();
+            const int total = S.pairpre[cn];
+#pragma unroll 1
+            for (int base = 0; base < total; base += 32) {
+                const int j = base + lane;
+                const bool valid = j < total;
+                bool pass = false, pend = false, keep_it = false;
+                int pend_ac3 = 0;
+                int p3 = 0, k3 = 0, ll = 0;
+                if (valid) {
+                    const int q = row_of(S.pairpre, cn, j);
+                    const int code = S.pairs[q];
+                    p3 = code & 255;
+                    k3 = code >> 8;
+                    ll = nth_in_words(nw, j - S.pairpre[q], [&](int w) { return S.Trow[p3][w] & S.Trow[k3][w]; });
+                    n_ac3k++;
+                    const Ortho<R> o = ortho_tet<R>(point<R>(S, p3), point<R>(S, k3), point<R>(S, ll), T, B);
+                    if (o.ac3 > 0) {
+                        n_s3++;
+                        keep_it = true;
+                        const int r3 = ac2_scan<R>(S, nw, o, B, 3, p3, k3, ll, n_tet);
+                        pass = r3 > 0;
+                        pend = r3 == 0;
+                    } else if (o.ac3 == 0) {
+                        pend = true;
+                        pend_ac3 = 1;
+                    }
+                }
+                const int4 item = make_int4(i, valid ? S.idx[p3] : 0, valid ? S.idx[k3] : 0, valid ? S.idx[ll] : 0);
+                if (keep)
+                    append_direct(keep_it, item, A.cand3, &cnt->n_cand_out[3], A.cap_cand[3], &cnt->err, DERR_OVF_CAND);
+                append_direct(pend, make_int4(pend_ac3 ? ~i : i, item.y, item.z, item.w), A.pending, &cnt->n_pending,
+                              A.cap_pending, &cnt->err, DERR_OVF_PEND);
+                stage_push(lane, pass, item, S.st_tet, &S.n_tet, A.tet_out, &cnt->n_tet_out, A.cap_tet, &cnt->err,
+                           DERR_OVF_TET);
+            }
+            __syncwarp();
         }
-        __syncwarp();
 
-        // ---- phase E: edges (i,p): AC2 at the edge's orthocentre, exact -------
+        // ---- phase E: edges (i,p): AC2 at the edge's orthocentre ---------------
         for (int r0 = 0; r0 < n_up; r0 += 32) {
             const bool ok = r0 + lane < n_up;
             const int p = ok ? S.uplist[r0 + lane] : 0;
-            bool pass = false;
+            bool pass = false, pend = false;
             if (ok) {
-                const int4 q = S.q[p];
-                const long long D = (long long)q.x * q.x + (long long)q.y * q.y + (long long)q.z * q.z;
-                const long long a = q.w;
-                bool violated = false;
-#pragma unroll
-                for (int w = 0; w < WORDS; w++) {
-                    unsigned b = S.Mrow[p][w];
-                    while (b && !violated) {
-                        const int x = 32 * w + __ffs(b) - 1;
-                        b &= b - 1;
-                        const int4 xq = S.q[x];
-                        const long long qq = (long long)q.x * xq.x + (long long)q.y * xq.y + (long long)q.z * xq.z;
-                        const long long v = (long long)xq.w * D - a * qq;  // |.| < 2^55
-                        lc.edge++;
-                        if (v < 0) violated = true;
-                        else if (v == 0) {
-                            const long long coef[2] = {D - qq, qq};
-                            const int g[2] = {gi, S.gid[p]};
-                            violated = sos_violates(2, g, coef, S.gid[x]);
-                        }
-                    }
-                }
-                pass = !violated;
+                const Ortho<R> o = ortho_edge<R>(point<R>(S, p), B);
+                const int r1 = ac2_scan<R>(S, nw, o, B, 1, p, 0, 0, n_edge);
+                pass = r1 > 0;
+                pend = r1 == 0;
             }
-            stage_push(lane, pass, make_int2(i, ok ? S.idx[p] : 0), S.st_edge, &S.n_edge, A.edge_out, &cnt->n_edge_pass,
-                       A.cap_edge, &cnt->err, DERR_OVF_EDGE);
+            const int idp = ok ? S.idx[p] : 0;
+            append_direct(pend, make_int4(i, idp, -1, -1), A.pending, &cnt->n_pending, A.cap_pending, &cnt->err,
+                          DERR_OVF_PEND);
+            stage_push(lane, pass, make_int2(i, idp), S.st_edge, &S.n_edge, A.edge_out, &cnt->n_edge_pass, A.cap_edge,
+                       &cnt->err, DERR_OVF_EDGE);
         }
         __syncwarp();
     }
@@ -632,77 +770,315 @@ __global__ void __launch_bounds__(256) k_local(LocalArgs A) {
     stage_flush(lane, S.st_tri, &S.n_tri, A.tri_out, &cnt->n_tri_pass, A.cap_tri, &cnt->err, DERR_OVF_TRI);
     stage_flush(lane, S.st_edge, &S.n_edge, A.edge_out, &cnt->n_edge_pass, A.cap_edge, &cnt->err, DERR_OVF_EDGE);
     // counters: warp reduction, one atomic per warp and counter
-    auto red = [&](unsigned v) {
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(FULL, v, o);
-        return v;
-    };
-    unsigned vals[3 + 3 + 1 + 4 + 4];
-    int t = 0;
-    for (int k = 0; k < 3; k++) vals[t++] = red(lc.tet[k]);
-    for (int k = 0; k < 3; k++) vals[t++] = red(lc.tri[k]);
-    vals[t++] = red(lc.edge);
-    for (int k = 0; k < 4; k++) vals[t++] = red(lc.ac3[k]);
-    for (int k = 0; k < 4; k++) vals[t++] = red(lc.cand[k]);
+    const unsigned vals[9] = {n_tet, n_tri, n_edge, n_ac3e, n_ac3t, n_ac3k, n_s1, n_s2, n_s3};
+    unsigned red[9];
+#pragma unroll
+    for (int t = 0; t < 9; t++) red[t] = __reduce_add_sync(FULL, vals[t]);
     if (lane == 0) {
-        t = 0;
-        for (int k = 0; k < 3; k++) atomicAdd(&cnt->ac2_tet[k], (unsigned long long)vals[t++]);
-        for (int k = 0; k < 3; k++) atomicAdd(&cnt->ac2_tri[k], (unsigned long long)vals[t++]);
-        atomicAdd(&cnt->ac2_edge, (unsigned long long)vals[t++]);
-        for (int k = 0; k < 4; k++) atomicAdd(&cnt->ac3[k], (unsigned long long)vals[t++]);
-        for (int k = 0; k < 4; k++) atomicAdd(&cnt->n_cand[k], (unsigned long long)vals[t++]);
+        const int lvl = is32 ? 0 : 1;
+        atomicAdd(&cnt->ac2_tet[lvl], (unsigned long long)red[0]);
+        atomicAdd(&cnt->ac2_tri[lvl], (unsigned long long)red[1]);
+        atomicAdd(&cnt->ac2_edge, (unsigned long long)red[2]);
+        atomicAdd(&cnt->ac3[1], (unsigned long long)red[3]);
+        atomicAdd(&cnt->ac3[2], (unsigned long long)red[4]);
+        atomicAdd(&cnt->ac3[3], (unsigned long long)red[5]);
+        atomicAdd(&cnt->n_cand[1], (unsigned long long)red[6]);
+        atomicAdd(&cnt->n_cand[2], (unsigned long long)red[7]);
+        atomicAdd(&cnt->n_cand[3], (unsigned long long)red[8]);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// k_resolve: exact settlement of the pending simplices, one thread each
+
+__device__ __forceinline__ i128 mul64x64(long long a, long long b) { return (i128)a * (i128)b; }
+
+// The smallest input index among the candidates with a non-zero coefficient
+// decides the sign of a Delta that is exactly zero. True if Delta_eps < 0.
+__device__ __forceinline__ bool sos_violates(int nv, const int* g, const long long* coef, int gx) {
+    int best = gx;
+    int sign = -1;  // the test ball's own coefficient is negative
+    for (int k = 0; k < nv; k++)
+        if (coef[k] != 0 && g[k] < best) {
+            best = g[k];
+            sign = coef[k] > 0 ? 1 : -1;
+        }
+    return sign < 0;
+}
+
+__device__ __forceinline__ bool meet(long long D, long long s1, long long s2) {
+    const long long t = D - s1 - s2;
+    return t <= 0 || t * t <= 4 * s1 * s2;
+}
+
+__global__ void k_resolve(LocalArgs A, int64_t n_pending) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n_pending) return;
+    DevCounters* cnt = A.cnt;
+    const long long Aq = A.pc.A;
+    const int4 rec = A.pending[j];
+    const bool ac3_open = rec.x < 0;
+    const int i = ac3_open ? ~rec.x : rec.x;
+    const int v[3] = {rec.y, rec.z, rec.w};
+    const int nv = rec.z < 0 ? 1 : rec.w < 0 ? 2 : 3;
+    const int4 Pi = A.Ps[i];
+    const long long Wi = Pi.w, si = Wi + Aq;
+    const int gi = A.order[i];
+    long long q[3][3] = {{0}}, a[3] = {0, 0, 0}, sv[3] = {0, 0, 0};
+    int gv[3] = {0, 0, 0};
+    for (int t = 0; t < nv; t++) {
+        const int4 P = A.Ps[v[t]];
+        q[t][0] = P.x - Pi.x;
+        q[t][1] = P.y - Pi.y;
+        q[t][2] = P.z - Pi.z;
+        a[t] = q[t][0] * q[t][0] + q[t][1] * q[t][1] + q[t][2] * q[t][2] - P.w + Wi;
+        sv[t] = (long long)P.w + Aq;
+        gv[t] = A.order[v[t]];
+    }
+    // exact minors
+    long long det = 0, g11 = 0, g22 = 0, g12 = 0, n1 = 0, n2 = 0, C[3][3] = {{0}}, N[3] = {0, 0, 0};
+    if (nv == 1) {
+        det = q[0][0] * q[0][0] + q[0][1] * q[0][1] + q[0][2] * q[0][2];
+    } else if (nv == 2) {
+        g11 = q[0][0] * q[0][0] + q[0][1] * q[0][1] + q[0][2] * q[0][2];
+        g22 = q[1][0] * q[1][0] + q[1][1] * q[1][1] + q[1][2] * q[1][2];
+        g12 = q[0][0] * q[1][0] + q[0][1] * q[1][1] + q[0][2] * q[1][2];
+        det = g11 * g22 - g12 * g12;
+        n1 = g22 * a[0] - g12 * a[1];
+        n2 = g11 * a[1] - g12 * a[0];
+    } else {
+        for (int t = 0; t < 3; t++) {
+            const long long* b = q[(t + 1) % 3];
+            const long long* e = q[(t + 2) % 3];
+            C[t][0] = b[1] * e[2] - b[2] * e[1];
+            C[t][1] = b[2] * e[0] - b[0] * e[2];
+            C[t][2] = b[0] * e[1] - b[1] * e[0];
+        }
+        det = q[0][0] * C[0][0] + q[0][1] * C[0][1] + q[0][2] * C[0][2];
+        for (int c = 0; c < 3; c++) N[c] = a[0] * C[0][c] + a[1] * C[1][c] + a[2] * C[2][c];
+    }
+    if (ac3_open) {
+        atomicAdd(&cnt->ac3_exact, 1ull);
+        bool ok;
+        if (nv == 2)
+            ok = det > 0 && mul64x64(n1, a[0]) + mul64x64(n2, a[1]) <= (i128)(4 * det) * (i128)si;
+        else
+            ok = det != 0 && mul64x64(N[0], N[0]) + mul64x64(N[1], N[1]) + mul64x64(N[2], N[2]) <=
+                                 mul64x64(det, det) * (i128)(4 * si);
+        if (!ok) return;
+        atomicAdd(&cnt->n_cand[nv], 1ull);
+        if (A.pc.keep_candidates) {
+            const int4 item = make_int4(i, v[0], v[1], nv == 3 ? v[2] : 0);
+            const unsigned long long slot = atomicAdd(&cnt->n_cand_out[nv], 1ull);
+            if ((int64_t)slot < A.cap_cand[nv]) (nv == 3 ? A.cand3 : A.cand2)[slot] = item;
+            else atomicOr(&cnt->err, DERR_OVF_CAND);
+        }
+    }
+    // FP64 orthocentre from the exact minors and its decision threshold
+    double y[3] = {0, 0, 0}, E = 0.0;
+    if (nv == 2) {
+        const double rd = 1.0 / (2.0 * (double)det);
+        const double m1 = (double)n1 * rd, m2 = (double)n2 * rd;
+        double e = 0.0;
+        for (int c = 0; c < 3; c++) {
+            y[c] = fma(m1, (double)q[0][c], m2 * (double)q[1][c]);
+            e += fabs(m1) * fabs((double)q[0][c]) + fabs(m2) * fabs((double)q[1][c]);
+        }
+        e *= 6.05 * 1.1102230246251565e-16 * (1.0 + 1e-10);
+        E = (A.tri_k0_64 + A.tri_k1_64 * e) * (1.0 + 1e-10);
+    } else if (nv == 3) {
+        const double rd = 1.0 / (2.0 * (double)det);
+        for (int c = 0; c < 3; c++) y[c] = (double)N[c] * rd;
+        E = A.tet_eps64;
+    }
+    // candidates: neighbours of i adjacent to every vertex
+    const int64_t off = A.nb_off[i];
+    const int m = (int)(A.nb_off[i + 1] - off);
+    unsigned n64 = 0, nx = 0;
+    bool violated = false;
+    for (int e = 0; e < m && !violated; e++) {
+        const int x = A.nb[off + e];
+        if (x == v[0] || (nv >= 2 && x == v[1]) || (nv == 3 && x == v[2])) continue;
+        const int4 Px = A.Ps[x];
+        const long long sx = (long long)Px.w + Aq;
+        const long long qx[3] = {(long long)Px.x - Pi.x, (long long)Px.y - Pi.y, (long long)Px.z - Pi.z};
+        bool adj = true;
+        for (int t = 0; t < nv && adj; t++) {
+            const long long dx = qx[0] - q[t][0], dy = qx[1] - q[t][1], dz = qx[2] - q[t][2];
+            adj = meet(dx * dx + dy * dy + dz * dz, sv[t], sx);
+        }
+        if (!adj) continue;
+        const long long ax = qx[0] * qx[0] + qx[1] * qx[1] + qx[2] * qx[2] - Px.w + Wi;
+        int dec = 0;
+        if (nv >= 2) {
+            const double t = fma((double)qx[2], y[2], fma((double)qx[1], y[1], (double)qx[0] * y[0]));
+            const double d = fma(-2.0, t, (double)ax);
+            if (d > E) dec = 1;
+            else if (d < -E) dec = -1;
+        }
+        if (dec) {
+            n64++;
+        } else {
+            nx++;
+            const int gx = A.order[x];
+            if (nv == 1) {
+                const long long qq = q[0][0] * qx[0] + q[0][1] * qx[1] + q[0][2] * qx[2];
+                const long long vv = ax * det - a[0] * qq;  // |.| < 2^55
+                if (vv != 0) {
+                    dec = vv > 0 ? 1 : -1;
+                } else {
+                    const long long coef[2] = {det - qq, qq};
+                    const int g[2] = {gi, gv[0]};
+                    dec = sos_violates(2, g, coef, gx) ? -1 : 1;
+                }
+            } else if (nv == 2) {
+                const long long gx1 = q[0][0] * qx[0] + q[0][1] * qx[1] + q[0][2] * qx[2];
+                const long long gx2 = q[1][0] * qx[0] + q[1][1] * qx[1] + q[1][2] * qx[2];
+                const i128 vv = mul64x64(ax, det) - (mul64x64(n1, gx1) + mul64x64(n2, gx2));
+                if (vv != 0) {
+                    dec = vv > 0 ? 1 : -1;
+                } else {
+                    const long long c1 = g22 * gx1 - g12 * gx2, c2 = g11 * gx2 - g12 * gx1;
+                    const long long coef[3] = {det - c1 - c2, c1, c2};
+                    const int g[3] = {gi, gv[0], gv[1]};
+                    dec = sos_violates(3, g, coef, gx) ? -1 : 1;
+                }
+            } else {
+                const int sD = det > 0 ? 1 : -1;
+                i128 vv = mul64x64(ax, det) - (mul64x64(qx[0], N[0]) + mul64x64(qx[1], N[1]) + mul64x64(qx[2], N[2]));
+                if (sD < 0) vv = -vv;
+                if (vv != 0) {
+                    dec = vv > 0 ? 1 : -1;
+                } else {
+                    const long long D1 = qx[0] * C[0][0] + qx[1] * C[0][1] + qx[2] * C[0][2];
+                    const long long D2 = qx[0] * C[1][0] + qx[1] * C[1][1] + qx[2] * C[1][2];
+                    const long long D3 = qx[0] * C[2][0] + qx[1] * C[2][1] + qx[2] * C[2][2];
+                    const long long coef[4] = {sD * (det - D1 - D2 - D3), sD * D1, sD * D2, sD * D3};
+                    const int g[4] = {gi, gv[0], gv[1], gv[2]};
+                    dec = sos_violates(4, g, coef, gx) ? -1 : 1;
+                }
+            }
+        }
+        violated = dec < 0;
+    }
+    if (nv == 3) {
+        atomicAdd(&cnt->ac2_tet[1], (unsigned long long)n64);
+        atomicAdd(&cnt->ac2_tet[2], (unsigned long long)nx);
+    } else if (nv == 2) {
+        atomicAdd(&cnt->ac2_tri[1], (unsigned long long)n64);
+        atomicAdd(&cnt->ac2_tri[2], (unsigned long long)nx);
+    } else {
+        atomicAdd(&cnt->ac2_edge, (unsigned long long)(n64 + nx));
+    }
+    if (violated) return;
+    if (nv == 3) {
+        const unsigned long long slot = atomicAdd(&cnt->n_tet_out, 1ull);
+        if ((int64_t)slot < A.cap_tet) A.tet_out[slot] = make_int4(i, v[0], v[1], v[2]);
+        else atomicOr(&cnt->err, DERR_OVF_TET);
+    } else if (nv == 2) {
+        const unsigned long long slot = atomicAdd(&cnt->n_tri_pass, 1ull);
+        if ((int64_t)slot < A.cap_tri) A.tri_out[slot] = make_int4(i, v[0], v[1], 0);
+        else atomicOr(&cnt->err, DERR_OVF_TRI);
+    } else {
+        const unsigned long long slot = atomicAdd(&cnt->n_edge_pass, 1ull);
+        if ((int64_t)slot < A.cap_edge) A.edge_out[slot] = make_int2(i, v[0]);
+        else atomicOr(&cnt->err, DERR_OVF_EDGE);
     }
 }
 
 // ---------------------------------------------------------------------------
 
-template <int WORDS>
-static int launch_local(ac_ctx* c, LocalArgs& a, cudaStream_t s) {
+template <int WORDS, class R>
+static int launch_local(ac_ctx* c, const LocalArgs& a, int64_t max_items, cudaStream_t s) {
     int warps = c->opt.block_warps > 0 ? c->opt.block_warps : 8;
     if (warps > 8) warps = 8;  // __launch_bounds__(256)
     while (warps > 1 && (size_t)warps * sizeof(WarpSmem<WORDS>) > 200 * 1024) warps--;
     const size_t smem = (size_t)warps * sizeof(WarpSmem<WORDS>);
-    AC_CUDA(cudaFuncSetAttribute(k_local<WORDS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    AC_CUDA(cudaFuncSetAttribute(k_local<WORDS, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0, dev = 0, sms = 0;
-    AC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_local<WORDS>, warps * 32, smem));
+    AC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_local<WORDS, R>, warps * 32, smem));
     AC_CUDA(cudaGetDevice(&dev));
     AC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     if (per_sm < 1) return fail(AC_ERR_CUDA, "per-atom kernel does not fit on an SM");
     int64_t blocks = (int64_t)per_sm * sms;
-    int64_t need = (a.n + warps - 1) / warps;
+    int64_t need = (max_items + warps - 1) / warps;
     if (blocks > need) blocks = need;
     if (blocks < 1) blocks = 1;
-    AC_CUDA(cudaEventRecord(c->ev[8], s));
-    k_local<WORDS><<<(unsigned)blocks, warps * 32, smem, s>>>(a);
+    k_local<WORDS, R><<<(unsigned)blocks, warps * 32, smem, s>>>(a);
     AC_LAUNCHED();
-    AC_CUDA(cudaEventRecord(c->ev[9], s));
     c->local_launches++;
     return AC_OK;
 }
 
-// Threshold constants (see the header comment for the bound).
-static void set_thresholds(const PredConst& pc, int64_t wmax, LocalArgs& a) {
-    const double h = pc.h_d, H2 = h * h;
-    const double Wb = (double)wmax;
-    for (int lvl = 0; lvl < 2; lvl++) {
-        const double u = lvl == 0 ? ldexp(1.0, -24) : ldexp(1.0, -53);
-        const double g3 = 3 * u / (1 - 3 * u);
-        const double dy = 4.0001 * u;
-        const double safety = 1.0 + 8 * u;
-        // tetrahedron: u(4h^2 + Wmax) + 2 g3 (2h)(h)(1 + dy) + 2 (2h) dy h
-        const double tet = (u * (4 * H2 + Wb) + 4 * g3 * H2 * (1 + dy) + 4 * dy * H2) * safety;
-        // triangle: u(4h^2 + Wmax) + 2 g3 (2h)(h + e) + 2 (2h) e = k0 + k1 e
-        const double k0 = (u * (4 * H2 + Wb) + 4 * g3 * H2) * safety;
-        const double k1 = (4 * g3 * h + 4 * h) * safety;
-        if (lvl == 0) {
-            a.tet_eps32 = nextafterf((float)tet, INFINITY);
-            a.tri_k0_32 = nextafterf((float)k0, INFINITY);
-            a.tri_k1_32 = nextafterf((float)k1, INFINITY);
-        } else {
-            a.tet_eps64 = nextafter(tet, INFINITY);
-            a.tri_k0_64 = nextafter(k0, INFINITY);
-            a.tri_k1_64 = nextafter(k1, INFINITY);
-        }
+template <class R>
+static int launch_words(ac_ctx* c, int words, const LocalArgs& a, int64_t max_items, cudaStream_t s) {
+    return words == 1 ? launch_local<1, R>(c, a, max_items, s)
+           : words == 2 ? launch_local<2, R>(c, a, max_items, s)
+           : words == 4 ? launch_local<4, R>(c, a, max_items, s)
+                        : launch_local<8, R>(c, a, max_items, s);
+}
+
+// One per-atom pass. When some atom has more than 64 neighbours, the atoms that
+// fit in 64-bit rows run first in the narrow kernel (smaller shared-memory
+// footprint, twice the resident warps) and defer the rest to a second launch
+// with rows of `words` words over the deferred list.
+template <class R>
+static int launch_pass(ac_ctx* c, int words, LocalArgs& a, cudaStream_t s) {
+    AC_CUDA(cudaEventRecord(c->ev[8], s));
+    if (words <= 2) {
+        AC_TRY(launch_words<R>(c, words, a, a.n, s));
+    } else {
+        LocalArgs narrow = a;
+        narrow.defer = c->wide.as<int32_t>();
+        AC_TRY(launch_words<R>(c, 2, narrow, a.n, s));
+        LocalArgs wide = a;
+        wide.work = c->wide.as<int32_t>();
+        wide.n_work = &a.cnt->n_wide;
+        AC_TRY(launch_words<R>(c, words, wide, a.n, s));
     }
+    AC_CUDA(cudaEventRecord(c->ev[9], s));
+    return AC_OK;
+}
+
+// Constants of the bounds at unit roundoff u (derivation in the header comment).
+template <class R>
+static void set_bounds(double u, double h, int64_t wmax, Bounds<R>& b) {
+    auto up = [](double x) {
+        const R r = (R)(x * (1.0 + 1e-12));
+        return (double)r >= x ? r : (R)nextafter(r, (R)INFINITY);
+    };
+    const double H = 2.0 * h, g3 = 3 * u / (1 - 3 * u), s3 = sqrt(3.0) * (1 + 1e-7);
+    const double Am = 4 * h * h + (double)wmax;
+    const double slack = 1.0 + 64 * u;
+    b.H = up(H);
+    b.eC = up(2 * u * (1 + u) * H * H * slack);
+    const double eC = (double)b.eC;
+    b.eD_tet = up((g3 * (H * H * H + s3 * H * eC) + s3 * H * eC) * slack);
+    b.cN = up(6.001 * u * H * H * slack);
+    b.eG = up(g3 * H * H * slack);
+    b.eDet = up(15.01 * u * H * H * H * H * slack);
+    b.cn = up(6.01 * u * H * H * slack);
+    b.K0 = up((u * Am + 2 * g3 * H * h) * slack);
+    b.K1 = up(2 * s3 * H * (1 + g3) * slack);
+    b.k2 = up(2.01 * u);
+    b.ky = up(2.0001 * u);
+    b.ke = up(1.0001 * u);
+    b.u = up(u);
+    b.g3s = up(g3 * (1 + g3) * slack);
+    b.up1 = up(1.0 + 1.01 * u * slack);
+    b.two_up = up(2.0 * (1.0 + 2.0 * u));
+}
+
+static void set_constants(const PredConst& pc, int64_t wmax, LocalArgs& a) {
+    const double h = pc.h_d, H = 2.0 * h;
+    set_bounds<float>(ldexp(1.0, -24), h, wmax, a.b32);
+    set_bounds<double>(ldexp(1.0, -53), h, wmax, a.b64);
+    // resolve kernel: y from exact minors with relative error <= 4.0001 u64 per component
+    const double v = ldexp(1.0, -53), g3d = 3 * v / (1 - 3 * v), dy = 4.0001 * v, sf = 1.0 + 16 * v;
+    const double s3 = sqrt(3.0) * (1 + 1e-7), Am = 4 * h * h + (double)wmax;
+    a.tet_eps64 = nextafter((v * Am + 2 * g3d * H * h * (1 + dy) + 2 * dy * H * h * s3) * sf * (1 + 1e-12), INFINITY);
+    a.tri_k0_64 = nextafter((v * Am + 2 * g3d * H * h) * sf * (1 + 1e-12), INFINITY);
+    a.tri_k1_64 = nextafter((2 * g3d * H + 2 * H) * s3 * sf * (1 + 1e-12), INFINITY);
 }
 
 int run_local(ac_ctx* c, cudaStream_t s) {
@@ -721,22 +1097,21 @@ int run_local(ac_ctx* c, cudaStream_t s) {
         c->cap_tet = (int64_t)nn * 12 + 1024;
         c->cap_tri = (int64_t)nn * 16 + 1024;
         c->cap_edge = (int64_t)nn * 12 + 1024;
+        c->cap_pending = (int64_t)nn / 8 + 4096;
     }
     if (c->pc.keep_candidates && c->cap_cand[1] == 0) {
         c->cap_cand[1] = (int64_t)nn * 32 + 1024;
         c->cap_cand[2] = (int64_t)nn * 160 + 1024;
         c->cap_cand[3] = (int64_t)nn * 256 + 1024;
     }
-    int64_t wmax = 0;
-    {
-        // max W over atoms = H2 - A
-        wmax = c->pc.H2 - c->pc.A;
-    }
+    const int64_t wmax = c->pc.H2 - c->pc.A;  // max W over the atoms
     for (int attempt = 0; attempt < 4; attempt++) {
         AC_TRY(c->tet_out.reserve((size_t)c->cap_tet * sizeof(int4)));
         AC_TRY(c->tri_pass.reserve((size_t)c->cap_tri * sizeof(int4)));
         AC_TRY(c->edge_pass.reserve((size_t)c->cap_edge * sizeof(int2)));
+        AC_TRY(c->pending.reserve((size_t)c->cap_pending * sizeof(int4)));
         AC_TRY(c->vert_pass.reserve(nn));
+        if (words > 2) AC_TRY(c->wide.reserve(nn * sizeof(int32_t)));
         if (c->pc.keep_candidates) {
             AC_TRY(c->cand[1].reserve((size_t)c->cap_cand[1] * sizeof(int2)));
             AC_TRY(c->cand[2].reserve((size_t)c->cap_cand[2] * sizeof(int4)));
@@ -754,7 +1129,7 @@ int run_local(ac_ctx* c, cudaStream_t s) {
         a.nb = c->nb.as<int32_t>();
         a.n = n;
         a.pc = c->pc;
-        set_thresholds(c->pc, wmax, a);
+        set_constants(c->pc, wmax, a);
         a.tet_out = c->tet_out.as<int4>();
         a.cap_tet = c->cap_tet;
         a.tri_out = c->tri_pass.as<int4>();
@@ -762,6 +1137,8 @@ int run_local(ac_ctx* c, cudaStream_t s) {
         a.edge_out = c->edge_pass.as<int2>();
         a.cap_edge = c->cap_edge;
         a.vert_pass = c->vert_pass.as<uint8_t>();
+        a.pending = c->pending.as<int4>();
+        a.cap_pending = c->cap_pending;
         if (c->pc.keep_candidates) {
             a.cand1 = c->cand[1].as<int2>();
             a.cand2 = c->cand[2].as<int4>();
@@ -770,15 +1147,21 @@ int run_local(ac_ctx* c, cudaStream_t s) {
         }
         a.cnt = dc;
         if (n > 0) {
-            int rc = words == 1 ? launch_local<1>(c, a, s)
-                     : words == 2 ? launch_local<2>(c, a, s)
-                     : words == 4 ? launch_local<4>(c, a, s)
-                                  : launch_local<8>(c, a, s);
+            const int rc = c->pc.precision == AC_PRECISION_FILTERED ? launch_pass<float>(c, words, a, s)
+                                                                    : launch_pass<double>(c, words, a, s);
             if (rc) return rc;
         }
         AC_TRY(read_counters(c, &h, s));
         if (h.err & DERR_DEGREE) return fail(AC_ERR_CAPACITY, "neighbour list wider than the kernel's masks");
         bool again = false;
+        if ((int64_t)h.n_pending > c->cap_pending) {
+            c->cap_pending = (int64_t)(h.n_pending * 5 / 4) + 4096;
+            again = true;
+        } else if (h.n_pending > 0) {
+            k_resolve<<<(unsigned)((h.n_pending + 127) / 128), 128, 0, s>>>(a, (int64_t)h.n_pending);
+            AC_LAUNCHED();
+            AC_TRY(read_counters(c, &h, s));
+        }
         if ((int64_t)h.n_tet_out > c->cap_tet) {
             c->cap_tet = (int64_t)(h.n_tet_out * 5 / 4) + 1024;
             again = true;
@@ -796,10 +1179,7 @@ int run_local(ac_ctx* c, cudaStream_t s) {
                 c->cap_cand[d] = (int64_t)(h.n_cand_out[d] * 5 / 4) + 1024;
                 again = true;
             }
-        if (!again) {
-            // clear overflow bits that a successful pass may have left from an earlier attempt
-            return AC_OK;
-        }
+        if (!again) return AC_OK;
         unsigned zero_err = 0;
         AC_CUDA(cudaMemcpyAsync(&dc->err, &zero_err, sizeof(unsigned), cudaMemcpyHostToDevice, s));
     }
