@@ -181,8 +181,10 @@ int scan_exclusive_u32_to_u32(const uint32_t* in, uint32_t* out, int64_t n, DevB
 }
 
 int read_counters(ac_ctx* c, DevCounters* h, cudaStream_t s) {
-    AC_CUDA(cudaMemcpyAsync(h, c->counters.p, sizeof(DevCounters), cudaMemcpyDeviceToHost, s));
+    AC_CUDA(cudaMemcpyAsync(c->h_cnt, c->counters.p, sizeof(DevCounters), cudaMemcpyDeviceToHost, s));
     AC_CUDA(cudaStreamSynchronize(s));
+    *h = *c->h_cnt;
+    c->hc = *h;
     return AC_OK;
 }
 
@@ -293,8 +295,12 @@ int quantise_and_plan(ac_ctx* c, cudaStream_t s) {
                                                               c->mol_of.as<int32_t>(), c->P.as<int4>(), bbox, wmax, dc);
         AC_LAUNCHED();
     }
-    DevCounters hc;
-    AC_TRY(read_counters(c, &hc, s));
+    // one readback: counters, largest weight, per-molecule boxes
+    AC_CUDA(cudaMemcpyAsync(c->h_cnt, c->counters.p, sizeof(DevCounters), cudaMemcpyDeviceToHost, s));
+    AC_CUDA(cudaMemcpyAsync(c->h_stage, wmax, sizeof(int), cudaMemcpyDeviceToHost, s));
+    AC_CUDA(cudaMemcpyAsync(c->h_bbox, bbox, (size_t)n_mol * 6 * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    AC_CUDA(cudaStreamSynchronize(s));
+    const DevCounters hc = *c->h_cnt;
     if (hc.err & DERR_INVALID) {
         char b[128];
         snprintf(b, sizeof(b), "atom %d: non-finite value or radius <= 0", hc.bad_index);
@@ -306,11 +312,8 @@ int quantise_and_plan(ac_ctx* c, cudaStream_t s) {
                  hc.bad_index);
         return fail(AC_ERR_RANGE, b);
     }
-    int wmax_h = 0;
-    std::vector<int32_t> hb((size_t)n_mol * 6);
-    AC_CUDA(cudaMemcpyAsync(&wmax_h, wmax, sizeof(int), cudaMemcpyDeviceToHost, s));
-    AC_CUDA(cudaMemcpyAsync(hb.data(), bbox, hb.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-    AC_CUDA(cudaStreamSynchronize(s));
+    const int wmax_h = *reinterpret_cast<const int*>(c->h_stage);
+    const int32_t* hb = c->h_bbox;
 
     PredConst& pc = c->pc;
     pc.A = (int64_t)nearbyint(c->alpha * 1048576.0);
@@ -402,6 +405,18 @@ static int create_impl(const double* centres, const double* radii, const int64_t
     };
     for (int k = 0; k < 10; k++)
         if (cudaEventCreate(&c->ev[k]) != cudaSuccess) return bail(cuda_fail(cudaGetLastError(), "cudaEventCreate", __FILE__, __LINE__));
+    {
+        const size_t a0 = 64 * sizeof(int64_t), a1 = (sizeof(DevCounters) + 255) & ~(size_t)255;
+        const size_t a2 = ((size_t)6 * n_mol * sizeof(int32_t) + 255) & ~(size_t)255;
+        const size_t a3 = (size_t)7 * (n_mol + 1) * sizeof(int64_t);
+        if (cudaMallocHost(&c->h_pinned, a0 + a1 + a2 + a3) != cudaSuccess)
+            return bail(cuda_fail(cudaGetLastError(), "cudaMallocHost", __FILE__, __LINE__));
+        char* b = static_cast<char*>(c->h_pinned);
+        c->h_stage = reinterpret_cast<int64_t*>(b);
+        c->h_cnt = reinterpret_cast<DevCounters*>(b + a0);
+        c->h_bbox = reinterpret_cast<int32_t*>(b + a0 + a1);
+        c->h_molrows = reinterpret_cast<int64_t*>(b + a0 + a1 + a2);
+    }
 
     size_t nn = (size_t)(n > 0 ? n : 1);
     if ((rc = c->centres.reserve(nn * 3 * sizeof(double))) || (rc = c->radii.reserve(nn * sizeof(double))) ||
@@ -464,6 +479,8 @@ extern "C" int ac_build(ac_ctx* c, void* stream) {
     AC_CUDA(cudaEventSynchronize(c->ev[7]));
     DevCounters h;
     AC_TRY(read_counters(c, &h, s));
+    if (h.err & DERR_INTERNAL) return fail(AC_ERR_CUDA, "internal: attached simplex without a coface in the complex");
+    finish_mol_rows(c);
     ac_stats& st = c->stats;
     st.n_atoms = c->n;
     st.candidates[0] = 0;
@@ -605,6 +622,7 @@ extern "C" void ac_destroy(ac_ctx* c) {
     if (!c) return;
     for (int k = 0; k < 10; k++)
         if (c->ev[k]) cudaEventDestroy(c->ev[k]);
+    if (c->h_pinned) cudaFreeHost(c->h_pinned);
     delete c;
 }
 

@@ -70,83 +70,146 @@ __device__ __forceinline__ int4 facet_of(const int4& t, int K, int drop) {
     return make_int4(o[0], o[1], o[2], o[3]);
 }
 
-// Items: [0, nA) from a list in sorted positions (flag 1), then nB * (K+1)
-// facets of a canonical list of width K+1 (flag 0).
-struct PrepArgs {
+// Items of one dimension: [0, nA) from a list in sorted positions (a4, or a2 for
+// edges), then nB * (K + 1) facets of a canonical list of width K + 1. An item
+// is an ascending K-tuple of input indices; its bucket is its first vertex. For
+// K <= 3 the unused last component carries the flag (1: the simplex passed AC2
+// at its orthocentre, 0: a facet); for K = 4 every item is a list item (flag 1).
+struct CanonArgs {
     const int4* a4;
     const int2* a2;
     int64_t nA;
     const int4* cof;
     int64_t nB;
-    int K;
     const int32_t* order;  // sorted position -> input index
-    int4* t_out;
-    uint8_t* f_out;
-    int64_t* bucket_cnt;
+    int64_t total;
+    int64_t* bucket_cnt;   // count pass: items per bucket
+    const int64_t* off;    // scatter pass: bucket offsets
+    unsigned long long* cursor;
+    int4* T;               // scattered items
 };
 
-__global__ void k_prep(PrepArgs a) {
-    int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int K = a.K;
-    int64_t total = a.nA + a.nB * (K + 1);
-    if (j >= total) return;
+template <int K>
+__device__ __forceinline__ int4 canon_item(const CanonArgs& a, int64_t j) {
     int4 t;
-    uint8_t flag;
     if (j < a.nA) {
         if (K == 2) {
-            int2 e = a.a2[j];
+            const int2 e = a.a2[j];
             t = make_int4(a.order[e.x], a.order[e.y], -1, -1);
         } else {
-            int4 e = a.a4[j];
-            t = make_int4(a.order[e.x], a.order[e.y], K >= 3 ? a.order[e.z] : -1, K >= 4 ? a.order[e.w] : -1);
+            const int4 e = a.a4[j];
+            t = make_int4(a.order[e.x], a.order[e.y], a.order[e.z], K == 4 ? a.order[e.w] : -1);
         }
         sort_asc(t, K);
-        flag = 1;
+        if (K < 4) t.w = 1;
     } else {
-        int64_t r = j - a.nA;
-        int64_t row = r / (K + 1);
-        int drop = (int)(r % (K + 1));
+        const int64_t r = j - a.nA;
+        const int64_t row = r / (K + 1);
+        const int drop = (int)(r - row * (K + 1));
         t = facet_of(a.cof[row], K, drop);
-        flag = 0;
+        t.w = 0;  // K < 4 here: facets exist for K = 2, 3
     }
-    a.t_out[j] = t;
-    a.f_out[j] = flag;
-    atomicAdd((unsigned long long*)&a.bucket_cnt[t.x], 1ull);
+    return t;
 }
 
-__global__ void k_bucket_scatter(const int4* __restrict__ t_in, const uint8_t* __restrict__ f_in, int64_t total,
-                                 const int64_t* __restrict__ off, unsigned long long* __restrict__ cursor,
-                                 int4* __restrict__ t_out, uint8_t* __restrict__ f_out) {
-    int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= total) return;
-    int4 t = t_in[j];
-    int64_t slot = off[t.x] + (int64_t)atomicAdd(&cursor[t.x], 1ull);
-    t_out[slot] = t;
-    f_out[slot] = f_in[j];
+// Items in a warp that share a bucket add to its counter once.
+template <int K>
+__global__ void k_canon_count(CanonArgs a) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool valid = j < a.total;
+    const int lane = threadIdx.x & 31;
+    const int x = valid ? canon_item<K>(a, j).x : -1 - lane;
+    const unsigned peers = __match_any_sync(0xffffffffu, x);
+    if (valid && (peers & ((1u << lane) - 1u)) == 0)
+        atomicAdd((unsigned long long*)&a.bucket_cnt[x], (unsigned long long)__popc(peers));
 }
 
-// Warp-per-bucket version for buckets of up to WARP_SORT_MAX items: every lane
-// ranks its items against the whole bucket held in shared memory (stable rank:
-// smaller keys plus equal keys that come earlier), places them, then the first
-// of each run of equal tuples takes the OR of the run's flags. Larger buckets
-// are left to k_bucket_sort_unique (flag big).
-constexpr int WARP_SORT_MAX = 256;
-constexpr int SORT_WARPS = 4;  // 4 x 256 x 34 B = 34.8 KB static shared memory (< 48 KB)
+template <int K>
+__global__ void k_canon_scatter(CanonArgs a) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool valid = j < a.total;
+    const int lane = threadIdx.x & 31;
+    int4 t = make_int4(-1 - lane, 0, 0, 0);
+    if (valid) t = canon_item<K>(a, j);
+    const unsigned peers = __match_any_sync(0xffffffffu, t.x);
+    const int leader = __ffs(peers) - 1;
+    unsigned long long base = 0;
+    if (valid && lane == leader) base = atomicAdd(&a.cursor[t.x], (unsigned long long)__popc(peers));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (valid) a.T[a.off[t.x] + (int64_t)base + __popc(peers & ((1u << lane) - 1u))] = t;
+}
 
-__global__ void __launch_bounds__(SORT_WARPS * 32) k_bucket_sort_warp(int4* __restrict__ t, uint8_t* __restrict__ f,
-                                                                       const int64_t* __restrict__ off, int64_t n,
-                                                                       int64_t* __restrict__ uniq,
-                                                                       uint8_t* __restrict__ big) {
-    __shared__ int4 sk[SORT_WARPS][WARP_SORT_MAX];
-    __shared__ int4 so[SORT_WARPS][WARP_SORT_MAX];
-    __shared__ uint8_t sf[SORT_WARPS][WARP_SORT_MAX];
-    __shared__ uint8_t sfo[SORT_WARPS][WARP_SORT_MAX];
+// In-bucket sort and de-duplication, one warp per bucket of up to CSORT_MAX
+// items: the bucket's keys (the rest of the tuple: 64-bit (y, z) and 32-bit w)
+// sit in shared memory, every lane holds R = ceil(k/32) items in registers and
+// counts, for each, the keys before it (smaller, or equal and earlier: a stable
+// rank), then places it. The first of each run of equal tuples takes the OR of
+// the run's flags and the run is compacted to the front of the bucket.
+constexpr int CSORT_MAX = 256;
+constexpr int CSORT_WARPS = 4;
+
+struct SortSmem {
+    unsigned long long khi[CSORT_MAX];
+    unsigned long long ohi[CSORT_MAX];
+    unsigned klo[CSORT_MAX];
+    unsigned olo[CSORT_MAX];
+    unsigned char kf[CSORT_MAX];
+    unsigned char of[CSORT_MAX];
+};
+
+template <int K>
+__device__ __forceinline__ unsigned long long key_hi(const int4& t) {
+    return K == 2 ? (unsigned long long)(unsigned)t.y
+                  : ((unsigned long long)(unsigned)t.y << 32) | (unsigned long long)(unsigned)t.z;
+}
+
+template <int K, int R>
+__device__ __forceinline__ void rank_place(SortSmem& S, int k, int lane) {
+    unsigned long long h[R];
+    unsigned l[R];
+    int r[R];
+#pragma unroll
+    for (int q = 0; q < R; q++) {
+        const int i = lane + 32 * q;
+        h[q] = i < k ? S.khi[i] : ~0ull;
+        l[q] = (K == 4 && i < k) ? S.klo[i] : 0u;
+        r[q] = 0;
+    }
+#pragma unroll 4
+    for (int j = 0; j < k; j++) {
+        const unsigned long long hj = S.khi[j];
+        const unsigned lj = K == 4 ? S.klo[j] : 0u;
+#pragma unroll
+        for (int q = 0; q < R; q++) {
+            const int i = lane + 32 * q;
+            const bool eq_earlier = K == 4 ? (lj < l[q] || (lj == l[q] && j < i)) : j < i;
+            r[q] += (hj < h[q] || (hj == h[q] && eq_earlier)) ? 1 : 0;
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < R; q++) {
+        const int i = lane + 32 * q;
+        if (i < k) {
+            S.ohi[r[q]] = h[q];
+            if (K == 4) S.olo[r[q]] = l[q];
+            S.of[r[q]] = S.kf[i];
+        }
+    }
+}
+
+template <int K>
+__global__ void __launch_bounds__(CSORT_WARPS * 32) k_canon_sort(int4* __restrict__ T, const int64_t* __restrict__ off,
+                                                                  int64_t n, int64_t* __restrict__ uniq,
+                                                                  uint8_t* __restrict__ big) {
+    __shared__ SortSmem sm[CSORT_WARPS];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int64_t warps = (int64_t)gridDim.x * SORT_WARPS;
-    for (int64_t g = (int64_t)blockIdx.x * SORT_WARPS + w; g < n; g += warps) {
-        const int64_t a = off[g], b = off[g + 1];
-        const int k = (int)(b - a);
-        if (k > WARP_SORT_MAX) {
+    SortSmem& S = sm[w];
+    const int64_t warps = (int64_t)gridDim.x * CSORT_WARPS;
+    for (int64_t g = (int64_t)blockIdx.x * CSORT_WARPS + w; g < n; g += warps) {
+        const int64_t a = off[g];
+        const int64_t kb = off[g + 1] - a;
+        const int k = kb > CSORT_MAX ? CSORT_MAX + 1 : (int)kb;
+        if (k > CSORT_MAX) {
             if (lane == 0) big[g] = 1;
             continue;
         }
@@ -156,41 +219,47 @@ __global__ void __launch_bounds__(SORT_WARPS * 32) k_bucket_sort_warp(int4* __re
             continue;
         }
         for (int i = lane; i < k; i += 32) {
-            sk[w][i] = t[a + i];
-            sf[w][i] = f[a + i];
+            const int4 t = T[a + i];
+            S.khi[i] = key_hi<K>(t);
+            S.klo[i] = K == 4 ? (unsigned)t.w : 0u;
+            S.kf[i] = K == 4 ? 1 : (unsigned char)t.w;
         }
         __syncwarp();
-        for (int i = lane; i < k; i += 32) {
-            const int4 v = sk[w][i];
-            int r = 0;
-            for (int j = 0; j < k; j++) {
-                const int4 u = sk[w][j];
-                r += (less_rest(u, v) || (same(u, v) && j < i)) ? 1 : 0;
-            }
-            so[w][r] = v;
-            sfo[w][r] = sf[w][i];
-        }
+        if (k <= 32) rank_place<K, 1>(S, k, lane);
+        else if (k <= 64) rank_place<K, 2>(S, k, lane);
+        else if (k <= 128) rank_place<K, 4>(S, k, lane);
+        else rank_place<K, 8>(S, k, lane);
         __syncwarp();
-        // first of each run of equal tuples, with the OR of the run's flags
         int base = 0;
         for (int i0 = 0; i0 < k; i0 += 32) {
             const int i = i0 + lane;
             bool first = false;
-            uint8_t fl = 0;
-            int4 v = make_int4(0, 0, 0, 0);
+            unsigned char fl = 0;
+            unsigned long long hi = 0;
+            unsigned lo = 0;
             if (i < k) {
-                v = so[w][i];
-                first = i == 0 || !same(so[w][i - 1], v);
+                hi = S.ohi[i];
+                lo = K == 4 ? S.olo[i] : 0u;
+                first = i == 0 || S.ohi[i - 1] != hi || (K == 4 && S.olo[i - 1] != lo);
                 if (first) {
-                    fl = sfo[w][i];
-                    for (int j = i + 1; j < k && same(so[w][j], v); j++) fl |= sfo[w][j];
+                    fl = S.of[i];
+                    for (int j = i + 1; j < k && S.ohi[j] == hi && (K != 4 || S.olo[j] == lo); j++) fl |= S.of[j];
                 }
             }
             const unsigned bal = __ballot_sync(0xffffffffu, first);
             if (first) {
                 const int pos = base + __popc(bal & ((1u << lane) - 1u));
-                t[a + pos] = v;
-                f[a + pos] = fl;
+                int4 t;
+                t.x = (int)g;
+                if (K == 2) {
+                    t.y = (int)hi;
+                    t.z = -1;
+                } else {
+                    t.y = (int)(hi >> 32);
+                    t.z = (int)(unsigned)hi;
+                }
+                t.w = K == 4 ? (int)lo : (int)fl;
+                T[a + pos] = t;
             }
             base += __popc(bal);
         }
@@ -199,44 +268,47 @@ __global__ void __launch_bounds__(SORT_WARPS * 32) k_bucket_sort_warp(int4* __re
     }
 }
 
-// The remaining (large) buckets, one thread each.
-__global__ void k_bucket_sort_big(int4* __restrict__ t, uint8_t* __restrict__ f, const int64_t* __restrict__ off,
-                                  int64_t n, int64_t* __restrict__ uniq, const uint8_t* __restrict__ big) {
-    int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+// Buckets above CSORT_MAX items, one thread each (insertion sort).
+template <int K>
+__global__ void k_canon_sort_big(int4* __restrict__ T, const int64_t* __restrict__ off, int64_t n,
+                                 int64_t* __restrict__ uniq, const uint8_t* __restrict__ big) {
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= n || !big[g]) return;
-    int64_t a = off[g], b = off[g + 1];
+    const int64_t a = off[g], b = off[g + 1];
+    auto less = [](const int4& u, const int4& v) {
+        if (u.y != v.y) return u.y < v.y;
+        if (u.z != v.z) return u.z < v.z;
+        return K == 4 && u.w < v.w;
+    };
+    auto eq = [](const int4& u, const int4& v) { return u.y == v.y && u.z == v.z && (K != 4 || u.w == v.w); };
     for (int64_t i = a + 1; i < b; i++) {
-        int4 v = t[i];
-        uint8_t fv = f[i];
+        const int4 v = T[i];
         int64_t j = i;
-        while (j > a && less_rest(v, t[j - 1])) {
-            t[j] = t[j - 1];
-            f[j] = f[j - 1];
+        while (j > a && less(v, T[j - 1])) {
+            T[j] = T[j - 1];
             j--;
         }
-        t[j] = v;
-        f[j] = fv;
+        T[j] = v;
     }
     int64_t w = a;
     for (int64_t i = a; i < b; i++) {
-        if (w > a && same(t[w - 1], t[i])) {
-            f[w - 1] |= f[i];
+        const int4 v = T[i];
+        if (w > a && eq(T[w - 1], v)) {
+            if (K < 4) T[w - 1].w |= v.w;
         } else {
-            t[w] = t[i];
-            f[w] = f[i];
-            w++;
+            T[w++] = v;
         }
     }
     uniq[g] = w - a;
 }
 
-struct WriteArgs {
-    const int4* t;
-    const uint8_t* f;
-    const int64_t* off;   // bucket start in t
-    const int64_t* uoff;  // output row of the bucket's first unique
-    int64_t n;
-    int K;
+// Slot-parallel output: slot j of bucket g = T[j].x holds unique row j - off[g]
+// of the bucket when that is below uniq(g) = uoff[g+1] - uoff[g].
+struct CanonWriteArgs {
+    const int4* T;
+    int64_t total;
+    const int64_t* off;
+    const int64_t* uoff;
     const int32_t* mol_of;   // input index -> molecule
     const int64_t* mol_off;  // molecule -> first input index
     int4* G;                 // canonical rows, global input indices
@@ -244,85 +316,82 @@ struct WriteArgs {
     uint8_t* attached;
 };
 
-__global__ void k_bucket_write(WriteArgs a) {
-    int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= a.n) return;
-    int64_t src = a.off[g], dst = a.uoff[g], cnt = a.uoff[g + 1] - a.uoff[g];
-    int base = (int)a.mol_off[a.mol_of[g]];
-    for (int64_t k = 0; k < cnt; k++) {
-        int4 t = a.t[src + k];
-        a.G[dst + k] = t;
-        int v[4] = {t.x, t.y, t.z, t.w};
-        for (int c = 0; c < a.K; c++) a.out[(dst + k) * a.K + c] = v[c] - base;
-        a.attached[dst + k] = a.f[src + k] ? 0 : 1;
-    }
-}
-
-// Per-molecule first row: rows of molecule m start at uoff[mol_off[m]].
-__global__ void k_mol_rows(const int64_t* __restrict__ uoff, const int64_t* __restrict__ mol_off, int64_t n_mol,
-                           int64_t* __restrict__ out) {
-    int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (m > n_mol) return;
-    out[m] = uoff[mol_off[m]];
+template <int K>
+__global__ void k_canon_write(CanonWriteArgs a) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= a.total) return;
+    int4 t = a.T[j];
+    const int g = t.x;
+    const int64_t kk = j - a.off[g];
+    const int64_t u0 = a.uoff[g];
+    if (kk >= a.uoff[g + 1] - u0) return;
+    const int64_t row = u0 + kk;
+    const int flag = K == 4 ? 1 : t.w;
+    if (K < 4) t.w = -1;
+    a.G[row] = t;
+    const int base = (int)a.mol_off[a.mol_of[g]];
+    a.out[row * K + 0] = t.x - base;
+    a.out[row * K + 1] = t.y - base;
+    if (K >= 3) a.out[row * K + 2] = t.z - base;
+    if (K == 4) a.out[row * K + 3] = t.w - base;
+    a.attached[row] = flag ? 0 : 1;
 }
 
 // ---------------------------------------------------------------------------
-// canonicalise one dimension from (positions list, flag 1) + (facets of a canonical list, flag 0)
+// canonicalise one dimension
 
 struct Work {
-    DevBuf t_a, f_a, t_b, f_b, cnt, cursor, uniq, big;
+    DevBuf T, cnt, cursor, uniq, big;
 };
 
-static int canon_dim(ac_ctx* c, int d, const int4* a4, const int2* a2, int64_t nA, const int4* cof, int64_t nB,
-                     SimplexList& L, DevBuf& Gout, Work& w, cudaStream_t s) {
-    const int K = d + 1;
+template <int K>
+static int canon_dim_k(ac_ctx* c, const int4* a4, const int2* a2, int64_t nA, const int4* cof, int64_t nB,
+                       SimplexList& L, DevBuf& Gout, Work& w, cudaStream_t s) {
     const int64_t n = c->n;
     const int64_t total = nA + nB * (K + 1);
-    AC_TRY(w.t_a.reserve((size_t)(total + 1) * sizeof(int4)));
-    AC_TRY(w.f_a.reserve((size_t)(total + 1)));
-    AC_TRY(w.t_b.reserve((size_t)(total + 1) * sizeof(int4)));
-    AC_TRY(w.f_b.reserve((size_t)(total + 1)));
+    AC_TRY(w.T.reserve((size_t)(total + 1) * sizeof(int4)));
     AC_TRY(w.cnt.reserve((size_t)(n + 1) * sizeof(int64_t)));
     AC_TRY(w.cursor.reserve((size_t)(n + 1) * sizeof(int64_t)));
     AC_TRY(w.uniq.reserve((size_t)(n + 1) * sizeof(int64_t)));
+    AC_TRY(w.big.reserve((size_t)(n + 1)));
     AC_TRY(L.v0_off.reserve((size_t)(n + 1) * sizeof(int64_t)));
     int64_t* cnt = w.cnt.as<int64_t>();
     AC_CUDA(cudaMemsetAsync(cnt, 0, (size_t)(n + 1) * sizeof(int64_t), s));
     AC_CUDA(cudaMemsetAsync(w.cursor.p, 0, (size_t)(n + 1) * sizeof(int64_t), s));
+    CanonArgs ca{a4, a2, nA, cof, nB, c->order.as<int32_t>(), total, cnt, cnt, w.cursor.as<unsigned long long>(),
+                 w.T.as<int4>()};
+    const unsigned gi = (unsigned)((total + 255) / 256);
     if (total > 0) {
-        PrepArgs pa{a4, a2, nA, cof, nB, K, c->order.as<int32_t>(), w.t_a.as<int4>(), w.f_a.as<uint8_t>(), cnt};
-        k_prep<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(pa);
+        k_canon_count<K><<<gi, 256, 0, s>>>(ca);
         AC_LAUNCHED();
     }
-    AC_TRY(scan_exclusive_i64(cnt, cnt, n, c->scan_tmp, s));  // bucket offsets
-    if (total > 0) {
-        k_bucket_scatter<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(
-            w.t_a.as<int4>(), w.f_a.as<uint8_t>(), total, cnt, w.cursor.as<unsigned long long>(), w.t_b.as<int4>(),
-            w.f_b.as<uint8_t>());
-        AC_LAUNCHED();
-    }
+    AC_TRY(scan_exclusive_i64(cnt, cnt, n, c->scan_tmp, s));  // bucket offsets, in place
     int64_t* uniq = w.uniq.as<int64_t>();
+    if (total > 0) {
+        k_canon_scatter<K><<<gi, 256, 0, s>>>(ca);
+        AC_LAUNCHED();
+    }
     if (n > 0) {
-        AC_TRY(w.big.reserve((size_t)n));
-        int dev = 0, sms = 0;
+        int dev = 0, sms = 0, per_sm = 0;
         AC_CUDA(cudaGetDevice(&dev));
         AC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-        int64_t blocks = (n + SORT_WARPS - 1) / SORT_WARPS;
-        if (blocks > (int64_t)sms * 16) blocks = (int64_t)sms * 16;
-        k_bucket_sort_warp<<<(unsigned)blocks, SORT_WARPS * 32, 0, s>>>(w.t_b.as<int4>(), w.f_b.as<uint8_t>(), cnt, n,
-                                                                         uniq, w.big.as<uint8_t>());
+        AC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_canon_sort<K>, CSORT_WARPS * 32, 0));
+        // one resident wave, buckets taken grid-stride
+        int64_t blocks = (n + CSORT_WARPS - 1) / CSORT_WARPS;
+        if (blocks > (int64_t)sms * (per_sm > 0 ? per_sm : 1)) blocks = (int64_t)sms * (per_sm > 0 ? per_sm : 1);
+        k_canon_sort<K><<<(unsigned)blocks, CSORT_WARPS * 32, 0, s>>>(w.T.as<int4>(), cnt, n, uniq, w.big.as<uint8_t>());
         AC_LAUNCHED();
-        k_bucket_sort_big<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(w.t_b.as<int4>(), w.f_b.as<uint8_t>(), cnt, n,
-                                                                     uniq, w.big.as<uint8_t>());
+        k_canon_sort_big<K><<<(unsigned)((n + 127) / 128), 128, 0, s>>>(w.T.as<int4>(), cnt, n, uniq,
+                                                                       w.big.as<uint8_t>());
         AC_LAUNCHED();
     }
     int64_t* uoff = L.v0_off.as<int64_t>();
     AC_TRY(scan_exclusive_i64(uniq, uoff, n, c->scan_tmp, s));
-    int64_t count = 0;
-    AC_CUDA(cudaMemcpyAsync(&count, uoff + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    AC_CUDA(cudaMemcpyAsync(c->h_stage, uoff + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     AC_CUDA(cudaStreamSynchronize(s));
+    const int64_t count = c->h_stage[0];
     L.count = count;
-    size_t rows = (size_t)(count > 0 ? count : 1);
+    const size_t rows = (size_t)(count > 0 ? count : 1);
     AC_TRY(L.tuples.reserve(rows * K * sizeof(int32_t)));
     AC_TRY(L.attached.reserve(rows));
     AC_TRY(L.f.reserve(rows * sizeof(double)));
@@ -330,22 +399,22 @@ static int canon_dim(ac_ctx* c, int d, const int4* a4, const int2* a2, int64_t n
     AC_TRY(L.src_dim.reserve(rows));
     AC_TRY(L.src_idx.reserve(rows * sizeof(int64_t)));
     AC_TRY(Gout.reserve(rows * sizeof(int4)));
-    if (n > 0) {
-        WriteArgs wa{w.t_b.as<int4>(), w.f_b.as<uint8_t>(), cnt, uoff, n, K, c->mol_of.as<int32_t>(),
-                     c->d_moloff.as<int64_t>(), Gout.as<int4>(), L.tuples.as<int32_t>(), L.attached.as<uint8_t>()};
-        k_bucket_write<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(wa);
+    if (total > 0) {
+        CanonWriteArgs wa{w.T.as<int4>(), total, cnt, uoff, c->mol_of.as<int32_t>(), c->d_moloff.as<int64_t>(),
+                          Gout.as<int4>(), L.tuples.as<int32_t>(), L.attached.as<uint8_t>()};
+        k_canon_write<K><<<gi, 256, 0, s>>>(wa);
         AC_LAUNCHED();
     }
-    // per-molecule row ranges
-    AC_TRY(w.cursor.reserve((size_t)(c->n_mol + 1) * sizeof(int64_t)));
-    k_mol_rows<<<(unsigned)((c->n_mol + 1 + 127) / 128), 128, 0, s>>>(uoff, c->d_moloff.as<int64_t>(), c->n_mol,
-                                                                       w.cursor.as<int64_t>());
-    AC_LAUNCHED();
-    L.mol_off.assign((size_t)c->n_mol + 1, 0);
-    AC_CUDA(cudaMemcpyAsync(L.mol_off.data(), w.cursor.p, (size_t)(c->n_mol + 1) * sizeof(int64_t),
-                            cudaMemcpyDeviceToHost, s));
-    AC_CUDA(cudaStreamSynchronize(s));
     return AC_OK;
+}
+
+static int canon_dim(ac_ctx* c, int d, const int4* a4, const int2* a2, int64_t nA, const int4* cof, int64_t nB,
+                     SimplexList& L, DevBuf& Gout, Work& w, cudaStream_t s) {
+    switch (d) {
+        case 1: return canon_dim_k<2>(c, a4, a2, nA, cof, nB, L, Gout, w, s);
+        case 2: return canon_dim_k<3>(c, a4, a2, nA, cof, nB, L, Gout, w, s);
+        default: return canon_dim_k<4>(c, a4, a2, nA, cof, nB, L, Gout, w, s);
+    }
 }
 
 // Vertices (Step 5): K^0 = endpoints of K^1 + atoms whose centre passes AC2.
@@ -377,9 +446,24 @@ __global__ void k_vertex_write(const int64_t* __restrict__ voff, const uint8_t* 
     attached[r] = vert_pass[rank[g]] ? 0 : 1;
 }
 
+// First row of every molecule in each list: rows of molecule m start at
+// v0_off[mol_off[m]]. Lists 0..3 are K^0..K^3, lists 4..6 Sigma^1..Sigma^3.
+struct MolRowsArgs {
+    const int64_t* v0_off[7];
+    const int64_t* mol_off;
+    int64_t n_mol;
+    int64_t* out;  // 7 x (n_mol + 1)
+};
+
+__global__ void k_mol_rows(MolRowsArgs a) {
+    const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (m > a.n_mol) return;
+    const int64_t at = a.mol_off[m];
+    for (int l = 0; l < 7; l++) a.out[l * (a.n_mol + 1) + m] = a.v0_off[l] ? a.v0_off[l][at] : 0;
+}
+
 int canonicalise(ac_ctx* c, cudaStream_t s) {
-    DevCounters h;
-    AC_TRY(read_counters(c, &h, s));
+    const DevCounters& h = c->hc;  // counters read at the end of the per-atom pass
     if (h.err & (DERR_OVF_TET | DERR_OVF_TRI | DERR_OVF_EDGE | DERR_OVF_CAND))
         return fail(AC_ERR_CAPACITY, "per-atom output overflow");
     Work w;
@@ -398,10 +482,10 @@ int canonicalise(ac_ctx* c, cudaStream_t s) {
     {
         SimplexList& L = c->K[0];
         size_t nn = (size_t)(n > 0 ? n : 1);
-        AC_TRY(w.f_a.reserve(nn));
+        AC_TRY(w.big.reserve(nn));
         AC_TRY(w.cnt.reserve((nn + 1) * sizeof(int64_t)));
         AC_TRY(L.v0_off.reserve((nn + 1) * sizeof(int64_t)));
-        uint8_t* endpoint = w.f_a.as<uint8_t>();
+        uint8_t* endpoint = w.big.as<uint8_t>();
         AC_CUDA(cudaMemsetAsync(endpoint, 0, nn, s));
         if (c->K[1].count > 0) {
             k_mark_endpoints<<<(unsigned)((c->K[1].count + 255) / 256), 256, 0, s>>>(c->Gbuf[1].as<int4>(), c->K[1].count,
@@ -416,9 +500,9 @@ int canonicalise(ac_ctx* c, cudaStream_t s) {
         }
         int64_t* voff = L.v0_off.as<int64_t>();
         AC_TRY(scan_exclusive_i64(inK, voff, n, c->scan_tmp, s));
-        int64_t count = 0;
-        AC_CUDA(cudaMemcpyAsync(&count, voff + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        AC_CUDA(cudaMemcpyAsync(c->h_stage, voff + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
         AC_CUDA(cudaStreamSynchronize(s));
+        const int64_t count = c->h_stage[0];
         L.count = count;
         size_t rows = (size_t)(count > 0 ? count : 1);
         AC_TRY(L.tuples.reserve(rows * sizeof(int32_t)));
@@ -435,14 +519,6 @@ int canonicalise(ac_ctx* c, cudaStream_t s) {
                                                                        L.tuples.as<int32_t>(), L.attached.as<uint8_t>());
             AC_LAUNCHED();
         }
-        AC_TRY(w.cursor.reserve((size_t)(c->n_mol + 1) * sizeof(int64_t)));
-        k_mol_rows<<<(unsigned)((c->n_mol + 1 + 127) / 128), 128, 0, s>>>(voff, c->d_moloff.as<int64_t>(), c->n_mol,
-                                                                           w.cursor.as<int64_t>());
-        AC_LAUNCHED();
-        L.mol_off.assign((size_t)c->n_mol + 1, 0);
-        AC_CUDA(cudaMemcpyAsync(L.mol_off.data(), w.cursor.p, (size_t)(c->n_mol + 1) * sizeof(int64_t),
-                                cudaMemcpyDeviceToHost, s));
-        AC_CUDA(cudaStreamSynchronize(s));
     }
     // estimation-pass lists, when kept (single molecule)
     if (c->pc.keep_candidates) {
@@ -452,7 +528,28 @@ int canonicalise(ac_ctx* c, cudaStream_t s) {
                              nullptr, 0, c->C[d], c->CGbuf[d], w, s));
         }
     }
+    // per-molecule row ranges, copied to the host with the build's last transfer
+    MolRowsArgs ma{};
+    for (int d = 0; d < 4; d++) ma.v0_off[d] = c->K[d].v0_off.as<int64_t>();
+    for (int d = 1; d <= 3; d++) ma.v0_off[3 + d] = c->pc.keep_candidates ? c->C[d].v0_off.as<int64_t>() : nullptr;
+    ma.mol_off = c->d_moloff.as<int64_t>();
+    ma.n_mol = c->n_mol;
+    AC_TRY(w.cursor.reserve((size_t)7 * (c->n_mol + 1) * sizeof(int64_t)));
+    ma.out = w.cursor.as<int64_t>();
+    k_mol_rows<<<(unsigned)((c->n_mol + 1 + 127) / 128), 128, 0, s>>>(ma);
+    AC_LAUNCHED();
+    AC_CUDA(cudaMemcpyAsync(c->h_molrows, ma.out, (size_t)7 * (c->n_mol + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost,
+                            s));
     return AC_OK;
+}
+
+// Unpack the per-molecule row ranges once the stream has reached the end of the build.
+void finish_mol_rows(ac_ctx* c) {
+    const size_t m1 = (size_t)c->n_mol + 1;
+    for (int d = 0; d < 4; d++) c->K[d].mol_off.assign(c->h_molrows + d * m1, c->h_molrows + (d + 1) * m1);
+    if (c->pc.keep_candidates)
+        for (int d = 1; d <= 3; d++)
+            c->C[d].mol_off.assign(c->h_molrows + (3 + d) * m1, c->h_molrows + (4 + d) * m1);
 }
 
 // ---------------------------------------------------------------------------
@@ -634,9 +731,6 @@ int compute_filtration(ac_ctx* c, cudaStream_t s) {
             L.src_idx.as<int64_t>(), &c->counters.as<DevCounters>()->err);
         AC_LAUNCHED();
     }
-    DevCounters h;
-    AC_TRY(read_counters(c, &h, s));
-    if (h.err & DERR_INTERNAL) return fail(AC_ERR_CUDA, "internal: attached simplex without a coface in the complex");
     return AC_OK;
 }
 

@@ -166,10 +166,10 @@ int build_neighbours(ac_ctx* c, cudaStream_t s) {
                                            c->cell_start.as<uint32_t>(), c->pc, n, cntp, nullptr, nullptr, dc);
     AC_LAUNCHED();
     AC_TRY(scan_exclusive_i64(cntp, cntp, n, c->scan_tmp, s));
-    int64_t total = 0;
-    AC_CUDA(cudaMemcpyAsync(&total, cntp + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    AC_CUDA(cudaMemcpyAsync(c->h_stage, cntp + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     DevCounters h;
-    AC_TRY(read_counters(c, &h, s));
+    AC_TRY(read_counters(c, &h, s));  // also completes the copy above
+    const int64_t total = c->h_stage[0];
     if (h.err & DERR_COINCIDENT) return fail(AC_ERR_DEGENERATE, "two centres coincide after quantisation to 1/1024 A");
     c->nb_total = total;
     AC_TRY(c->nb.reserve((size_t)(total > 0 ? total : 1) * sizeof(int32_t)));

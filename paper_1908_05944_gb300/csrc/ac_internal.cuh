@@ -187,6 +187,13 @@ struct ac_ctx {
     ac::DevBuf scratch[6];
     ac::DevBuf scan_tmp;
 
+    ac::DevCounters hc{};             // host copy of the counters from the last readback
+    void* h_pinned = nullptr;         // one page-locked block holding the four readback areas below
+    int64_t* h_stage = nullptr;       // small scalars
+    ac::DevCounters* h_cnt = nullptr; // counters
+    int32_t* h_bbox = nullptr;        // 6 x n_mol bounding boxes
+    int64_t* h_molrows = nullptr;     // 7 x (n_mol + 1) per-molecule first rows
+
     ac_stats stats{};
     cudaEvent_t ev[10] = {};  // stage boundaries; ev[8], ev[9] bracket the per-atom kernel
     int local_launches = 0;
@@ -209,6 +216,7 @@ int backward(ac_ctx* c, const double* const dldf[4], double* dc, double* dr, cud
 int backward_noalloc(ac_ctx* c, const double* const dldf[4], double* dc, double* dr, cudaStream_t s);
 
 int read_counters(ac_ctx* c, DevCounters* h, cudaStream_t s);
+void finish_mol_rows(ac_ctx* c);
 
 // device helpers -------------------------------------------------------------
 

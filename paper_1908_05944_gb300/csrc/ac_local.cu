@@ -1083,8 +1083,7 @@ static void set_constants(const PredConst& pc, int64_t wmax, LocalArgs& a) {
 
 int run_local(ac_ctx* c, cudaStream_t s) {
     const int64_t n = c->n;
-    DevCounters h;
-    AC_TRY(read_counters(c, &h, s));
+    DevCounters h = c->hc;  // read after the neighbour count pass
     const int maxdeg = h.max_degree;
     int words = maxdeg <= 32 ? 1 : maxdeg <= 64 ? 2 : maxdeg <= 128 ? 4 : maxdeg <= 256 ? 8 : 0;
     if (words == 0) {
@@ -1179,7 +1178,10 @@ int run_local(ac_ctx* c, cudaStream_t s) {
                 c->cap_cand[d] = (int64_t)(h.n_cand_out[d] * 5 / 4) + 1024;
                 again = true;
             }
-        if (!again) return AC_OK;
+        if (!again) {
+            c->hc = h;
+            return AC_OK;
+        }
         unsigned zero_err = 0;
         AC_CUDA(cudaMemcpyAsync(&dc->err, &zero_err, sizeof(unsigned), cudaMemcpyHostToDevice, s));
     }
