@@ -405,6 +405,10 @@ static int create_impl(const double* centres, const double* radii, const int64_t
     };
     for (int k = 0; k < 10; k++)
         if (cudaEventCreate(&c->ev[k]) != cudaSuccess) return bail(cuda_fail(cudaGetLastError(), "cudaEventCreate", __FILE__, __LINE__));
+    if (cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess)
+        return bail(cuda_fail(cudaGetLastError(), "side stream", __FILE__, __LINE__));
     {
         const size_t a0 = 64 * sizeof(int64_t), a1 = (sizeof(DevCounters) + 255) & ~(size_t)255;
         const size_t a2 = ((size_t)6 * n_mol * sizeof(int32_t) + 255) & ~(size_t)255;
@@ -623,6 +627,9 @@ extern "C" void ac_destroy(ac_ctx* c) {
     for (int k = 0; k < 10; k++)
         if (c->ev[k]) cudaEventDestroy(c->ev[k]);
     if (c->h_pinned) cudaFreeHost(c->h_pinned);
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
+    if (c->side) cudaStreamDestroy(c->side);
     delete c;
 }
 

@@ -150,12 +150,58 @@ __global__ void k_neighbours(const int4* __restrict__ Ps, const int32_t* __restr
     }
 }
 
+// Work order of the per-atom pass: sorted positions by decreasing neighbour
+// count (ties in any order), so the costliest atoms start first and the
+// kernel's tail is short; the atoms with more than 64 neighbours form its head.
+constexpr int DEG_BINS = 258;  // counts 0..256, and 257 for anything above
+
+__device__ __forceinline__ int deg_bin(int64_t m) { return m > 256 ? 257 : (int)m; }
+
+__global__ void k_deg_hist(const int64_t* __restrict__ cnt, int64_t n, unsigned* __restrict__ hist) {
+    __shared__ unsigned h[DEG_BINS];
+    for (int t = threadIdx.x; t < DEG_BINS; t += blockDim.x) h[t] = 0;
+    __syncthreads();
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) atomicAdd(&h[deg_bin(cnt[i])], 1u);
+    __syncthreads();
+    for (int t = threadIdx.x; t < DEG_BINS; t += blockDim.x)
+        if (h[t]) atomicAdd(&hist[t], h[t]);
+}
+
+// one thread: start of each bin in decreasing order, and the head size
+__global__ void k_deg_starts(const unsigned* __restrict__ hist, unsigned* __restrict__ cursor,
+                             long long* __restrict__ n_wide) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    unsigned run = 0;
+    for (int b = DEG_BINS - 1; b >= 0; b--) {
+        cursor[b] = run;
+        run += hist[b];
+        if (b == 65) *n_wide = run;
+    }
+}
+
+__global__ void k_deg_scatter(const int64_t* __restrict__ cnt, int64_t n, unsigned* __restrict__ cursor,
+                              int32_t* __restrict__ work) {
+    __shared__ unsigned h[DEG_BINS], base[DEG_BINS];
+    for (int t = threadIdx.x; t < DEG_BINS; t += blockDim.x) h[t] = 0;
+    __syncthreads();
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int b = i < n ? deg_bin(cnt[i]) : 0;
+    const unsigned local = i < n ? atomicAdd(&h[b], 1u) : 0u;
+    __syncthreads();
+    for (int t = threadIdx.x; t < DEG_BINS; t += blockDim.x)
+        if (h[t]) base[t] = atomicAdd(&cursor[t], h[t]);
+    __syncthreads();
+    if (i < n) work[base[b] + local] = (int32_t)i;
+}
+
 int build_neighbours(ac_ctx* c, cudaStream_t s) {
     const int64_t n = c->n;
     AC_TRY(c->nb_cnt.reserve((size_t)(n + 1) * sizeof(int64_t)));
     int64_t* cntp = c->nb_cnt.as<int64_t>();
     if (n == 0) {
         c->nb_total = 0;
+        c->n_wide = 0;
         AC_CUDA(cudaMemsetAsync(cntp, 0, sizeof(int64_t), s));
         AC_TRY(c->nb.reserve(4));
         return AC_OK;
@@ -165,11 +211,26 @@ int build_neighbours(ac_ctx* c, cudaStream_t s) {
     k_neighbours<false><<<nb, 128, 0, s>>>(c->Ps.as<int4>(), c->mol_s.as<int32_t>(), c->grids.as<MolGrid>(),
                                            c->cell_start.as<uint32_t>(), c->pc, n, cntp, nullptr, nullptr, dc);
     AC_LAUNCHED();
+    // work order from the counts (before the in-place scan turns them into offsets)
+    AC_TRY(c->work.reserve((size_t)n * sizeof(int32_t)));
+    AC_TRY(c->deg.reserve(2 * DEG_BINS * sizeof(unsigned) + 64));
+    unsigned* hist = c->deg.as<unsigned>();
+    unsigned* cursor = hist + DEG_BINS;
+    long long* n_wide = reinterpret_cast<long long*>(hist + 2 * DEG_BINS);  // byte 2064: 8-aligned
+    AC_CUDA(cudaMemsetAsync(hist, 0, DEG_BINS * sizeof(unsigned), s));
+    k_deg_hist<<<nb, 128, 0, s>>>(cntp, n, hist);
+    AC_LAUNCHED();
+    k_deg_starts<<<1, 32, 0, s>>>(hist, cursor, n_wide);
+    AC_LAUNCHED();
+    k_deg_scatter<<<nb, 128, 0, s>>>(cntp, n, cursor, c->work.as<int32_t>());
+    AC_LAUNCHED();
     AC_TRY(scan_exclusive_i64(cntp, cntp, n, c->scan_tmp, s));
     AC_CUDA(cudaMemcpyAsync(c->h_stage, cntp + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    AC_CUDA(cudaMemcpyAsync(c->h_stage + 1, n_wide, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     DevCounters h;
-    AC_TRY(read_counters(c, &h, s));  // also completes the copy above
+    AC_TRY(read_counters(c, &h, s));  // also completes the copies above
     const int64_t total = c->h_stage[0];
+    c->n_wide = c->h_stage[1];
     if (h.err & DERR_COINCIDENT) return fail(AC_ERR_DEGENERATE, "two centres coincide after quantisation to 1/1024 A");
     c->nb_total = total;
     AC_TRY(c->nb.reserve((size_t)(total > 0 ? total : 1) * sizeof(int32_t)));

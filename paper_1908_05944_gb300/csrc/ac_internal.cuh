@@ -91,9 +91,8 @@ struct DevCounters {
     unsigned long long ac3[4];
     unsigned long long ac3_exact;     // AC3 decisions left to exact integers
     unsigned long long n_pending;     // simplices escalated to the resolve kernel
-    unsigned long long work_next;     // persistent-kernel work counter (all atoms)
-    unsigned long long work_next2;    // work counter over the wide-row list
-    unsigned long long n_wide;        // atoms deferred to the wide-row launch
+    unsigned long long work_next;     // persistent-kernel work counter (narrow-row launch)
+    unsigned long long work_next2;    // work counter of the wide-row launch
     unsigned int err;
     int max_degree;
     int bad_index;
@@ -173,7 +172,9 @@ struct ac_ctx {
     ac::DevBuf vert_pass; // uint8 per sorted atom
     ac::DevBuf cand[4];   // Sigma^d candidate lists when kept (int4 / int2)
     ac::DevBuf pending;   // int4 escalated simplices (see ac_local.cu)
-    ac::DevBuf wide;      // int32 atoms with more neighbours than the narrow kernel holds
+    ac::DevBuf work;      // int32 sorted positions by decreasing neighbour count
+    ac::DevBuf deg;       // degree histogram and cursors of the work order
+    int64_t n_wide = 0;   // atoms with more than 64 neighbours (the head of work)
     int64_t cap_tet = 0, cap_tri = 0, cap_edge = 0, cap_cand[4] = {0, 0, 0, 0}, cap_pending = 0;
 
     // canonical results; Gbuf/CGbuf hold the same rows as int4 of global input indices
@@ -196,6 +197,8 @@ struct ac_ctx {
 
     ac_stats stats{};
     cudaEvent_t ev[10] = {};  // stage boundaries; ev[8], ev[9] bracket the per-atom kernel
+    cudaStream_t side = nullptr;                    // wide-row launch, concurrent with the narrow one
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     int local_launches = 0;
 };
 

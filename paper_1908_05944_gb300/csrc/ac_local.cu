@@ -116,12 +116,10 @@ struct LocalArgs {
     const int64_t* nb_off;
     const int32_t* nb;
     int64_t n;
-    // Work of one launch: atoms 0..n-1 (work == nullptr), or work[0..*n_work-1].
-    // Atoms with more neighbours than the launch's rows hold go to defer[] when
-    // it is set, else they raise DERR_DEGREE.
+    // Work of one launch: the atoms work[0..n-1], taken through work_next (or
+    // work_next2 when counter2 is set, for a launch running beside another).
     const int32_t* work;
-    const unsigned long long* n_work;
-    int32_t* defer;
+    int counter2;
     PredConst pc;
     Bounds<float> b32;
     Bounds<double> b64;
@@ -483,14 +481,14 @@ __global__ void __launch_bounds__(256) k_local(LocalArgs A) {
     }
     __syncwarp();
 
-    const long long n_items = A.work ? (long long)*A.n_work : A.n;
-    unsigned long long* next = A.work ? &cnt->work_next2 : &cnt->work_next;
+    const long long n_items = A.n;
+    unsigned long long* next = A.counter2 ? &cnt->work_next2 : &cnt->work_next;
     for (;;) {
         long long i_ll = 0;
         if (lane == 0) i_ll = (long long)atomicAdd(next, 1ull);
         i_ll = __shfl_sync(FULL, i_ll, 0);
         if (i_ll >= n_items) break;
-        const int i = A.work ? A.work[i_ll] : (int)i_ll;
+        const int i = A.work[i_ll];
         const int4 Pi = A.Ps[i];
         const int Wi = Pi.w;
         const long long si = (long long)Wi + Aq;
@@ -502,10 +500,7 @@ __global__ void __launch_bounds__(256) k_local(LocalArgs A) {
             continue;
         }
         if (m > MAXM) {
-            if (lane == 0) {
-                if (A.defer) A.defer[atomicAdd(&cnt->n_wide, 1ull)] = i;  // at most n entries
-                else atomicOr(&cnt->err, DERR_DEGREE);
-            }
+            if (lane == 0) atomicOr(&cnt->err, DERR_DEGREE);
             continue;
         }
         const int nw = (m + 31) >> 5;
@@ -989,8 +984,8 @@ __global__ void k_resolve(LocalArgs A, int64_t n_pending) {
 // ---------------------------------------------------------------------------
 
 template <int WORDS, class R>
-static int launch_local(ac_ctx* c, const LocalArgs& a, int64_t max_items, cudaStream_t s) {
-    int warps = c->opt.block_warps > 0 ? c->opt.block_warps : 8;
+static int launch_local(ac_ctx* c, const LocalArgs& a, int64_t max_items, int warps_req, cudaStream_t s) {
+    int warps = warps_req > 0 ? warps_req : c->opt.block_warps > 0 ? c->opt.block_warps : 8;
     if (warps > 8) warps = 8;  // __launch_bounds__(256)
     while (warps > 1 && (size_t)warps * sizeof(WarpSmem<WORDS>) > 200 * 1024) warps--;
     const size_t smem = (size_t)warps * sizeof(WarpSmem<WORDS>);
@@ -1011,31 +1006,39 @@ static int launch_local(ac_ctx* c, const LocalArgs& a, int64_t max_items, cudaSt
 }
 
 template <class R>
-static int launch_words(ac_ctx* c, int words, const LocalArgs& a, int64_t max_items, cudaStream_t s) {
-    return words == 1 ? launch_local<1, R>(c, a, max_items, s)
-           : words == 2 ? launch_local<2, R>(c, a, max_items, s)
-           : words == 4 ? launch_local<4, R>(c, a, max_items, s)
-                        : launch_local<8, R>(c, a, max_items, s);
+static int launch_words(ac_ctx* c, int words, const LocalArgs& a, int warps, cudaStream_t s) {
+    return words == 1 ? launch_local<1, R>(c, a, a.n, warps, s)
+           : words == 2 ? launch_local<2, R>(c, a, a.n, warps, s)
+           : words == 4 ? launch_local<4, R>(c, a, a.n, warps, s)
+                        : launch_local<8, R>(c, a, a.n, warps, s);
 }
 
-// One per-atom pass. When some atom has more than 64 neighbours, the atoms that
-// fit in 64-bit rows run first in the narrow kernel (smaller shared-memory
-// footprint, twice the resident warps) and defer the rest to a second launch
-// with rows of `words` words over the deferred list.
+// One per-atom pass over the work order (decreasing neighbour count). When
+// some atom has more than 64 neighbours, those atoms (the head of the order)
+// run in a kernel with wider rows on a side stream, concurrently with the
+// narrow kernel (64-bit rows: smaller shared-memory footprint, twice the
+// resident warps) over the rest; the wide launch is small and starts first.
 template <class R>
 static int launch_pass(ac_ctx* c, int words, LocalArgs& a, cudaStream_t s) {
     AC_CUDA(cudaEventRecord(c->ev[8], s));
-    if (words <= 2) {
-        AC_TRY(launch_words<R>(c, words, a, a.n, s));
-    } else {
-        LocalArgs narrow = a;
-        narrow.defer = c->wide.as<int32_t>();
-        AC_TRY(launch_words<R>(c, 2, narrow, a.n, s));
+    const int32_t* work = c->work.as<int32_t>();
+    const int64_t n_wide = words > 2 ? c->n_wide : 0;
+    if (n_wide > 0) {
         LocalArgs wide = a;
-        wide.work = c->wide.as<int32_t>();
-        wide.n_work = &a.cnt->n_wide;
-        AC_TRY(launch_words<R>(c, words, wide, a.n, s));
+        wide.work = work;
+        wide.n = n_wide;
+        wide.counter2 = 1;
+        AC_CUDA(cudaEventRecord(c->ev_fork, s));
+        AC_CUDA(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
+        AC_TRY(launch_words<R>(c, words, wide, 4, c->side));
+        AC_CUDA(cudaEventRecord(c->ev_join, c->side));
     }
+    LocalArgs narrow = a;
+    narrow.work = work + n_wide;
+    narrow.n = a.n - n_wide;
+    narrow.counter2 = 0;
+    if (narrow.n > 0) AC_TRY(launch_words<R>(c, n_wide > 0 ? 2 : words, narrow, 0, s));
+    if (n_wide > 0) AC_CUDA(cudaStreamWaitEvent(s, c->ev_join, 0));
     AC_CUDA(cudaEventRecord(c->ev[9], s));
     return AC_OK;
 }
@@ -1110,7 +1113,6 @@ int run_local(ac_ctx* c, cudaStream_t s) {
         AC_TRY(c->edge_pass.reserve((size_t)c->cap_edge * sizeof(int2)));
         AC_TRY(c->pending.reserve((size_t)c->cap_pending * sizeof(int4)));
         AC_TRY(c->vert_pass.reserve(nn));
-        if (words > 2) AC_TRY(c->wide.reserve(nn * sizeof(int32_t)));
         if (c->pc.keep_candidates) {
             AC_TRY(c->cand[1].reserve((size_t)c->cap_cand[1] * sizeof(int2)));
             AC_TRY(c->cand[2].reserve((size_t)c->cap_cand[2] * sizeof(int4)));
