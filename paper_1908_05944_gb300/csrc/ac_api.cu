@@ -7,7 +7,9 @@
 
 #include <algorithm>
 #include <cstdio>
+#include <mutex>
 #include <new>
+#include <vector>
 
 #include "ac_internal.cuh"
 
@@ -30,13 +32,37 @@ int cuda_fail(cudaError_t e, const char* what, const char* file, int line) {
     return e == cudaErrorMemoryAllocation ? AC_ERR_OOM : AC_ERR_CUDA;
 }
 
+cudaStream_t& release_stream() {
+    static thread_local cudaStream_t s = nullptr;
+    return s;
+}
+
+// Keep up to this many freed bytes per device in the pool between builds.
+static constexpr uint64_t POOL_KEEP_BYTES = 16ull << 30;
+
+static void prepare_pool() {
+    static std::mutex mu;
+    static std::vector<int> done;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return;
+    std::lock_guard<std::mutex> g(mu);
+    for (int d : done)
+        if (d == dev) return;
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        uint64_t keep = POOL_KEEP_BYTES;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    done.push_back(dev);
+}
+
 DevBuf::~DevBuf() {
-    if (p) cudaFree(p);
+    if (p) cudaFreeAsync(p, release_stream());
 }
 
 DevBuf& DevBuf::operator=(DevBuf&& o) noexcept {
     if (this != &o) {
-        if (p) cudaFree(p);
+        if (p) cudaFreeAsync(p, release_stream());
         p = o.p;
         bytes = o.bytes;
         o.p = nullptr;
@@ -45,20 +71,21 @@ DevBuf& DevBuf::operator=(DevBuf&& o) noexcept {
     return *this;
 }
 
-int DevBuf::reserve(size_t nbytes) {
+int DevBuf::reserve(size_t nbytes, cudaStream_t s) {
     if (nbytes <= bytes && p) return AC_OK;
     if (p) {
-        cudaFree(p);
+        cudaFreeAsync(p, s);
         p = nullptr;
         bytes = 0;
     }
+    prepare_pool();
     size_t want = nbytes < 256 ? 256 : nbytes;
-    cudaError_t e = cudaMalloc(&p, want);
+    cudaError_t e = cudaMallocAsync(&p, want, s);
     if (e != cudaSuccess) {
         cudaGetLastError();
         p = nullptr;
         char buf[128];
-        snprintf(buf, sizeof(buf), "cudaMalloc of %zu bytes failed", want);
+        snprintf(buf, sizeof(buf), "cudaMallocAsync of %zu bytes failed", want);
         return fail(AC_ERR_OOM, buf);
     }
     bytes = want;
@@ -168,7 +195,7 @@ static int scan_entry(const T* in, T* out, int64_t n, DevBuf& tmp, cudaStream_t 
         need += ((sizeof(T) * (size_t)(nb + 1) + 255) & ~(size_t)255);
         if (nb == 1) break;
     }
-    AC_TRY(tmp.reserve(need + 256));
+    AC_TRY(tmp.reserve(need + 256, s));
     return scan_impl<T>(in, out, n, tmp, 0, s);
 }
 
@@ -279,8 +306,8 @@ __global__ void k_init_bbox(int32_t* bbox, int64_t n_mol) {
 // side ~ h = sqrt(r_max^2 + alpha), dense cell table over each bounding box.
 int quantise_and_plan(ac_ctx* c, cudaStream_t s) {
     const int64_t n = c->n, n_mol = c->n_mol;
-    AC_TRY(c->scratch[0].reserve((size_t)n_mol * 6 * sizeof(int32_t)));
-    AC_TRY(c->scratch[1].reserve(sizeof(int)));
+    AC_TRY(c->scratch[0].reserve((size_t)n_mol * 6 * sizeof(int32_t), s));
+    AC_TRY(c->scratch[1].reserve(sizeof(int), s));
     DevCounters* dc = c->counters.as<DevCounters>();
     AC_CUDA(cudaMemsetAsync(dc, 0, sizeof(DevCounters), s));
     const int big = INT32_MAX;
@@ -353,7 +380,7 @@ int quantise_and_plan(ac_ctx* c, cudaStream_t s) {
     pc.reach = hq > 0 ? (int32_t)((2 * hq + cell - 1) / cell) : 1;
     if (pc.reach < 1) pc.reach = 1;
     c->n_cells = total;
-    AC_TRY(c->grids.reserve((size_t)n_mol * sizeof(MolGrid)));
+    AC_TRY(c->grids.reserve((size_t)n_mol * sizeof(MolGrid), s));
     AC_CUDA(cudaMemcpyAsync(c->grids.p, grids.data(), (size_t)n_mol * sizeof(MolGrid), cudaMemcpyHostToDevice, s));
     AC_CUDA(cudaStreamSynchronize(s));
     c->stats.grid_dims[0] = grids[0].dims[0];
@@ -423,10 +450,10 @@ static int create_impl(const double* centres, const double* radii, const int64_t
     }
 
     size_t nn = (size_t)(n > 0 ? n : 1);
-    if ((rc = c->centres.reserve(nn * 3 * sizeof(double))) || (rc = c->radii.reserve(nn * sizeof(double))) ||
-        (rc = c->P.reserve(nn * sizeof(int4))) || (rc = c->mol_of.reserve(nn * sizeof(int32_t))) ||
-        (rc = c->d_moloff.reserve((size_t)(n_mol + 1) * sizeof(int64_t))) ||
-        (rc = c->counters.reserve(sizeof(DevCounters))))
+    if ((rc = c->centres.reserve(nn * 3 * sizeof(double), s)) || (rc = c->radii.reserve(nn * sizeof(double), s)) ||
+        (rc = c->P.reserve(nn * sizeof(int4), s)) || (rc = c->mol_of.reserve(nn * sizeof(int32_t), s)) ||
+        (rc = c->d_moloff.reserve((size_t)(n_mol + 1) * sizeof(int64_t), s)) ||
+        (rc = c->counters.reserve(sizeof(DevCounters), s)))
         return bail(rc);
     if (n > 0) {
         if (cudaMemcpy(c->centres.p, centres, (size_t)n * 3 * sizeof(double), cudaMemcpyDefault) != cudaSuccess ||
@@ -466,6 +493,7 @@ static float elapsed(cudaEvent_t a, cudaEvent_t b) {
 extern "C" int ac_build(ac_ctx* c, void* stream) {
     if (!c) return fail(AC_ERR_INVALID_ARG, "ctx is NULL");
     cudaStream_t s = (cudaStream_t)stream;
+    StreamScope scope(s);
     c->built = false;
     const long long launches0 = g_launch_count;
     AC_CUDA(cudaEventRecord(c->ev[0], s));
@@ -563,6 +591,7 @@ extern "C" int ac_eval_filtration(ac_ctx* c, const double* d_centres, const doub
                                   void* stream) {
     if (!c || !d_centres || !d_radii || !d_f_out) return fail(AC_ERR_INVALID_ARG, "bad argument");
     if (!c->built) return fail(AC_ERR_STATE, "no successful ac_build on this context");
+    StreamScope scope((cudaStream_t)stream);
     return eval_filtration(c, d_centres, d_radii, d_f_out, (cudaStream_t)stream);
 }
 
@@ -570,6 +599,7 @@ extern "C" int ac_backward(ac_ctx* c, const double* const d_dLdf[4], double* d_d
                            void* stream) {
     if (!c || !d_dLdf || !d_dLdcentres || !d_dLdradii) return fail(AC_ERR_INVALID_ARG, "bad argument");
     if (!c->built) return fail(AC_ERR_STATE, "no successful ac_build on this context");
+    StreamScope scope((cudaStream_t)stream);
     return backward(c, d_dLdf, d_dLdcentres, d_dLdradii, (cudaStream_t)stream);
 }
 
@@ -624,6 +654,9 @@ extern "C" int ac_get_sizes(ac_ctx* c, int64_t* n_mol, int64_t* n_atoms) {
 
 extern "C" void ac_destroy(ac_ctx* c) {
     if (!c) return;
+    // the context's buffers go back to the pool once no work can still use them
+    cudaDeviceSynchronize();
+    StreamScope scope(nullptr);
     for (int k = 0; k < 10; k++)
         if (c->ev[k]) cudaEventDestroy(c->ev[k]);
     if (c->h_pinned) cudaFreeHost(c->h_pinned);

@@ -202,7 +202,7 @@ __global__ void k_backward(const double* __restrict__ X, const double* __restric
 static int gtable(ac_ctx* c, DevBuf& tab, cudaStream_t s) {
     const int4* h[4];
     for (int d = 0; d < 4; d++) h[d] = c->Gbuf[d].as<int4>();
-    AC_TRY(tab.reserve(sizeof(h)));
+    AC_TRY(tab.reserve(sizeof(h), s));
     AC_CUDA(cudaMemcpyAsync(tab.p, h, sizeof(h), cudaMemcpyHostToDevice, s));
     return AC_OK;
 }

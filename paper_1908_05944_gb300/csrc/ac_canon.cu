@@ -140,59 +140,101 @@ __global__ void k_canon_scatter(CanonArgs a) {
 }
 
 // In-bucket sort and de-duplication, one warp per bucket of up to CSORT_MAX
-// items: the bucket's keys (the rest of the tuple: 64-bit (y, z) and 32-bit w)
-// sit in shared memory, every lane holds R = ceil(k/32) items in registers and
-// counts, for each, the keys before it (smaller, or equal and earlier: a stable
-// rank), then places it. The first of each run of equal tuples takes the OR of
-// the run's flags and the run is compacted to the front of the bucket.
+// items. The rest of each tuple becomes a sort key: K = 2: (y << 1) | flag;
+// K = 3: (y << 33) | (z << 1) | flag (y, z < 2^31); K = 4: hi = (y << 32) | z,
+// lo = w (flag 1). Keys sit in registers, R = ceil(k/32) per lane (padded to a
+// power of two with the largest key), and a bitonic network sorts them:
+// exchanges across lanes by shuffles, across a lane's registers directly.
+// Equal tuples (the flag bit aside) are then adjacent; the first of each run
+// takes the OR of the run's flags and the run is compacted to the front of
+// the bucket.
 constexpr int CSORT_MAX = 256;
 constexpr int CSORT_WARPS = 4;
 
 struct SortSmem {
-    unsigned long long khi[CSORT_MAX];
     unsigned long long ohi[CSORT_MAX];
-    unsigned klo[CSORT_MAX];
     unsigned olo[CSORT_MAX];
-    unsigned char kf[CSORT_MAX];
-    unsigned char of[CSORT_MAX];
 };
 
 template <int K>
-__device__ __forceinline__ unsigned long long key_hi(const int4& t) {
-    return K == 2 ? (unsigned long long)(unsigned)t.y
-                  : ((unsigned long long)(unsigned)t.y << 32) | (unsigned long long)(unsigned)t.z;
+__device__ __forceinline__ void make_key(const int4& t, unsigned long long& hi, unsigned& lo) {
+    const unsigned long long y = (unsigned)t.y, z = (unsigned)t.z;
+    if (K == 2) {
+        hi = (y << 1) | (unsigned)t.w;
+        lo = 0u;
+    } else if (K == 3) {
+        hi = (y << 33) | (z << 1) | (unsigned)t.w;
+        lo = 0u;
+    } else {
+        hi = (y << 32) | z;
+        lo = (unsigned)t.w;
+    }
+}
+
+template <int K>
+__device__ __forceinline__ bool key_less(unsigned long long ah, unsigned al, unsigned long long bh, unsigned bl) {
+    return K == 4 ? (ah < bh || (ah == bh && al < bl)) : ah < bh;
 }
 
 template <int K, int R>
-__device__ __forceinline__ void rank_place(SortSmem& S, int k, int lane) {
+__device__ __forceinline__ void bitonic_place(SortSmem& S, const int4* __restrict__ T, int64_t a, int k, int lane) {
     unsigned long long h[R];
     unsigned l[R];
-    int r[R];
 #pragma unroll
-    for (int q = 0; q < R; q++) {
-        const int i = lane + 32 * q;
-        h[q] = i < k ? S.khi[i] : ~0ull;
-        l[q] = (K == 4 && i < k) ? S.klo[i] : 0u;
-        r[q] = 0;
+    for (int r = 0; r < R; r++) {
+        const int e = 32 * r + lane;
+        if (e < k) {
+            make_key<K>(T[a + e], h[r], l[r]);
+        } else {
+            h[r] = ~0ull;
+            l[r] = ~0u;
+        }
     }
-#pragma unroll 4
-    for (int j = 0; j < k; j++) {
-        const unsigned long long hj = S.khi[j];
-        const unsigned lj = K == 4 ? S.klo[j] : 0u;
+    constexpr int N = 32 * R;
 #pragma unroll
-        for (int q = 0; q < R; q++) {
-            const int i = lane + 32 * q;
-            const bool eq_earlier = K == 4 ? (lj < l[q] || (lj == l[q] && j < i)) : j < i;
-            r[q] += (hj < h[q] || (hj == h[q] && eq_earlier)) ? 1 : 0;
+    for (int size = 2; size <= N; size <<= 1) {
+#pragma unroll
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            if (stride >= 32) {
+                const int rs = stride >> 5;
+#pragma unroll
+                for (int r = 0; r < R; r++) {
+                    if ((r & rs) == 0) {
+                        const int r2 = r | rs;
+                        const bool asc = ((32 * r + lane) & size) == 0;
+                        if (key_less<K>(h[r2], l[r2], h[r], l[r]) == asc) {
+                            const unsigned long long th = h[r];
+                            h[r] = h[r2];
+                            h[r2] = th;
+                            const unsigned tl = l[r];
+                            l[r] = l[r2];
+                            l[r2] = tl;
+                        }
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int r = 0; r < R; r++) {
+                    const unsigned long long oh = __shfl_xor_sync(0xffffffffu, h[r], stride);
+                    const unsigned ol = K == 4 ? __shfl_xor_sync(0xffffffffu, l[r], stride) : 0u;
+                    const bool asc = ((32 * r + lane) & size) == 0;
+                    const bool lower = (lane & stride) == 0;
+                    // the lower position keeps the smaller key when ascending
+                    const bool take = (lower == asc) ? key_less<K>(oh, ol, h[r], l[r]) : key_less<K>(h[r], l[r], oh, ol);
+                    if (take) {
+                        h[r] = oh;
+                        l[r] = ol;
+                    }
+                }
+            }
         }
     }
 #pragma unroll
-    for (int q = 0; q < R; q++) {
-        const int i = lane + 32 * q;
-        if (i < k) {
-            S.ohi[r[q]] = h[q];
-            if (K == 4) S.olo[r[q]] = l[q];
-            S.of[r[q]] = S.kf[i];
+    for (int r = 0; r < R; r++) {
+        const int e = 32 * r + lane;
+        if (e < k) {
+            S.ohi[e] = h[r];
+            if (K == 4) S.olo[e] = l[r];
         }
     }
 }
@@ -218,47 +260,46 @@ __global__ void __launch_bounds__(CSORT_WARPS * 32) k_canon_sort(int4* __restric
             if (lane == 0) uniq[g] = k;
             continue;
         }
-        for (int i = lane; i < k; i += 32) {
-            const int4 t = T[a + i];
-            S.khi[i] = key_hi<K>(t);
-            S.klo[i] = K == 4 ? (unsigned)t.w : 0u;
-            S.kf[i] = K == 4 ? 1 : (unsigned char)t.w;
-        }
+        if (k <= 32) bitonic_place<K, 1>(S, T, a, k, lane);
+        else if (k <= 64) bitonic_place<K, 2>(S, T, a, k, lane);
+        else if (k <= 128) bitonic_place<K, 4>(S, T, a, k, lane);
+        else bitonic_place<K, 8>(S, T, a, k, lane);
         __syncwarp();
-        if (k <= 32) rank_place<K, 1>(S, k, lane);
-        else if (k <= 64) rank_place<K, 2>(S, k, lane);
-        else if (k <= 128) rank_place<K, 4>(S, k, lane);
-        else rank_place<K, 8>(S, k, lane);
-        __syncwarp();
+        // same tuple: equal keys without the flag bit (K <= 3), or equal (hi, lo)
+        auto same_at = [&](int x, int y) {
+            return K == 4 ? (S.ohi[x] == S.ohi[y] && S.olo[x] == S.olo[y]) : (S.ohi[x] >> 1) == (S.ohi[y] >> 1);
+        };
         int base = 0;
         for (int i0 = 0; i0 < k; i0 += 32) {
             const int i = i0 + lane;
             bool first = false;
-            unsigned char fl = 0;
-            unsigned long long hi = 0;
-            unsigned lo = 0;
+            int fl = 0;
             if (i < k) {
-                hi = S.ohi[i];
-                lo = K == 4 ? S.olo[i] : 0u;
-                first = i == 0 || S.ohi[i - 1] != hi || (K == 4 && S.olo[i - 1] != lo);
+                first = i == 0 || !same_at(i, i - 1);
                 if (first) {
-                    fl = S.of[i];
-                    for (int j = i + 1; j < k && S.ohi[j] == hi && (K != 4 || S.olo[j] == lo); j++) fl |= S.of[j];
+                    fl = K == 4 ? 1 : (int)(S.ohi[i] & 1ull);
+                    for (int j = i + 1; j < k && same_at(j, i); j++) fl |= (int)(S.ohi[j] & 1ull);
                 }
             }
             const unsigned bal = __ballot_sync(0xffffffffu, first);
             if (first) {
                 const int pos = base + __popc(bal & ((1u << lane) - 1u));
+                const unsigned long long hi = S.ohi[i];
                 int4 t;
                 t.x = (int)g;
                 if (K == 2) {
-                    t.y = (int)hi;
+                    t.y = (int)(hi >> 1);
                     t.z = -1;
+                    t.w = fl;
+                } else if (K == 3) {
+                    t.y = (int)(hi >> 33);
+                    t.z = (int)((hi >> 1) & 0xffffffffull);
+                    t.w = fl;
                 } else {
                     t.y = (int)(hi >> 32);
                     t.z = (int)(unsigned)hi;
+                    t.w = (int)S.olo[i];
                 }
-                t.w = K == 4 ? (int)lo : (int)fl;
                 T[a + pos] = t;
             }
             base += __popc(bal);
@@ -349,12 +390,12 @@ static int canon_dim_k(ac_ctx* c, const int4* a4, const int2* a2, int64_t nA, co
                        SimplexList& L, DevBuf& Gout, Work& w, cudaStream_t s) {
     const int64_t n = c->n;
     const int64_t total = nA + nB * (K + 1);
-    AC_TRY(w.T.reserve((size_t)(total + 1) * sizeof(int4)));
-    AC_TRY(w.cnt.reserve((size_t)(n + 1) * sizeof(int64_t)));
-    AC_TRY(w.cursor.reserve((size_t)(n + 1) * sizeof(int64_t)));
-    AC_TRY(w.uniq.reserve((size_t)(n + 1) * sizeof(int64_t)));
-    AC_TRY(w.big.reserve((size_t)(n + 1)));
-    AC_TRY(L.v0_off.reserve((size_t)(n + 1) * sizeof(int64_t)));
+    AC_TRY(w.T.reserve((size_t)(total + 1) * sizeof(int4), s));
+    AC_TRY(w.cnt.reserve((size_t)(n + 1) * sizeof(int64_t), s));
+    AC_TRY(w.cursor.reserve((size_t)(n + 1) * sizeof(int64_t), s));
+    AC_TRY(w.uniq.reserve((size_t)(n + 1) * sizeof(int64_t), s));
+    AC_TRY(w.big.reserve((size_t)(n + 1), s));
+    AC_TRY(L.v0_off.reserve((size_t)(n + 1) * sizeof(int64_t), s));
     int64_t* cnt = w.cnt.as<int64_t>();
     AC_CUDA(cudaMemsetAsync(cnt, 0, (size_t)(n + 1) * sizeof(int64_t), s));
     AC_CUDA(cudaMemsetAsync(w.cursor.p, 0, (size_t)(n + 1) * sizeof(int64_t), s));
@@ -392,13 +433,13 @@ static int canon_dim_k(ac_ctx* c, const int4* a4, const int2* a2, int64_t nA, co
     const int64_t count = c->h_stage[0];
     L.count = count;
     const size_t rows = (size_t)(count > 0 ? count : 1);
-    AC_TRY(L.tuples.reserve(rows * K * sizeof(int32_t)));
-    AC_TRY(L.attached.reserve(rows));
-    AC_TRY(L.f.reserve(rows * sizeof(double)));
-    AC_TRY(L.orthosize.reserve(rows * sizeof(double)));
-    AC_TRY(L.src_dim.reserve(rows));
-    AC_TRY(L.src_idx.reserve(rows * sizeof(int64_t)));
-    AC_TRY(Gout.reserve(rows * sizeof(int4)));
+    AC_TRY(L.tuples.reserve(rows * K * sizeof(int32_t), s));
+    AC_TRY(L.attached.reserve(rows, s));
+    AC_TRY(L.f.reserve(rows * sizeof(double), s));
+    AC_TRY(L.orthosize.reserve(rows * sizeof(double), s));
+    AC_TRY(L.src_dim.reserve(rows, s));
+    AC_TRY(L.src_idx.reserve(rows * sizeof(int64_t), s));
+    AC_TRY(Gout.reserve(rows * sizeof(int4), s));
     if (total > 0) {
         CanonWriteArgs wa{w.T.as<int4>(), total, cnt, uoff, c->mol_of.as<int32_t>(), c->d_moloff.as<int64_t>(),
                           Gout.as<int4>(), L.tuples.as<int32_t>(), L.attached.as<uint8_t>()};
@@ -482,9 +523,9 @@ int canonicalise(ac_ctx* c, cudaStream_t s) {
     {
         SimplexList& L = c->K[0];
         size_t nn = (size_t)(n > 0 ? n : 1);
-        AC_TRY(w.big.reserve(nn));
-        AC_TRY(w.cnt.reserve((nn + 1) * sizeof(int64_t)));
-        AC_TRY(L.v0_off.reserve((nn + 1) * sizeof(int64_t)));
+        AC_TRY(w.big.reserve(nn, s));
+        AC_TRY(w.cnt.reserve((nn + 1) * sizeof(int64_t), s));
+        AC_TRY(L.v0_off.reserve((nn + 1) * sizeof(int64_t), s));
         uint8_t* endpoint = w.big.as<uint8_t>();
         AC_CUDA(cudaMemsetAsync(endpoint, 0, nn, s));
         if (c->K[1].count > 0) {
@@ -505,13 +546,13 @@ int canonicalise(ac_ctx* c, cudaStream_t s) {
         const int64_t count = c->h_stage[0];
         L.count = count;
         size_t rows = (size_t)(count > 0 ? count : 1);
-        AC_TRY(L.tuples.reserve(rows * sizeof(int32_t)));
-        AC_TRY(L.attached.reserve(rows));
-        AC_TRY(L.f.reserve(rows * sizeof(double)));
-        AC_TRY(L.orthosize.reserve(rows * sizeof(double)));
-        AC_TRY(L.src_dim.reserve(rows));
-        AC_TRY(L.src_idx.reserve(rows * sizeof(int64_t)));
-        AC_TRY(c->Gbuf[0].reserve(rows * sizeof(int4)));
+        AC_TRY(L.tuples.reserve(rows * sizeof(int32_t), s));
+        AC_TRY(L.attached.reserve(rows, s));
+        AC_TRY(L.f.reserve(rows * sizeof(double), s));
+        AC_TRY(L.orthosize.reserve(rows * sizeof(double), s));
+        AC_TRY(L.src_dim.reserve(rows, s));
+        AC_TRY(L.src_idx.reserve(rows * sizeof(int64_t), s));
+        AC_TRY(c->Gbuf[0].reserve(rows * sizeof(int4), s));
         if (n > 0) {
             k_vertex_write<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(voff, c->vert_pass.as<uint8_t>(),
                                                                        c->rank.as<int32_t>(), n, c->mol_of.as<int32_t>(),
@@ -534,7 +575,7 @@ int canonicalise(ac_ctx* c, cudaStream_t s) {
     for (int d = 1; d <= 3; d++) ma.v0_off[3 + d] = c->pc.keep_candidates ? c->C[d].v0_off.as<int64_t>() : nullptr;
     ma.mol_off = c->d_moloff.as<int64_t>();
     ma.n_mol = c->n_mol;
-    AC_TRY(w.cursor.reserve((size_t)7 * (c->n_mol + 1) * sizeof(int64_t)));
+    AC_TRY(w.cursor.reserve((size_t)7 * (c->n_mol + 1) * sizeof(int64_t), s));
     ma.out = w.cursor.as<int64_t>();
     k_mol_rows<<<(unsigned)((c->n_mol + 1 + 127) / 128), 128, 0, s>>>(ma);
     AC_LAUNCHED();
@@ -705,8 +746,8 @@ int compute_filtration(ac_ctx* c, cudaStream_t s) {
         SimplexList& L = c->K[d];
         const int64_t m = L.count;
         if (m == 0) continue;
-        AC_TRY(keyb.reserve((size_t)m * sizeof(unsigned long long)));
-        AC_TRY(argb.reserve((size_t)m * sizeof(unsigned long long)));
+        AC_TRY(keyb.reserve((size_t)m * sizeof(unsigned long long), s));
+        AC_TRY(argb.reserve((size_t)m * sizeof(unsigned long long), s));
         k_orthosize<<<(unsigned)((m + 127) / 128), 128, 0, s>>>(
             P, c->Gbuf[d].as<int4>(), m, d + 1, L.attached.as<uint8_t>(), L.orthosize.as<double>(), L.f.as<double>(),
             L.src_dim.as<int8_t>(), L.src_idx.as<int64_t>(), keyb.as<unsigned long long>());

@@ -70,13 +70,13 @@ __global__ void k_gather(const int32_t* __restrict__ order, const int4* __restri
 int build_grid(ac_ctx* c, cudaStream_t s) {
     const int64_t n = c->n;
     size_t nn = (size_t)(n > 0 ? n : 1);
-    AC_TRY(c->cell_of.reserve(nn * sizeof(uint32_t)));
-    AC_TRY(c->cell_cnt.reserve((size_t)(c->n_cells + 1) * sizeof(uint32_t)));
-    AC_TRY(c->cell_start.reserve((size_t)(c->n_cells + 1) * sizeof(uint32_t)));
-    AC_TRY(c->order.reserve(nn * sizeof(int32_t)));
-    AC_TRY(c->rank.reserve(nn * sizeof(int32_t)));
-    AC_TRY(c->Ps.reserve(nn * sizeof(int4)));
-    AC_TRY(c->mol_s.reserve(nn * sizeof(int32_t)));
+    AC_TRY(c->cell_of.reserve(nn * sizeof(uint32_t), s));
+    AC_TRY(c->cell_cnt.reserve((size_t)(c->n_cells + 1) * sizeof(uint32_t), s));
+    AC_TRY(c->cell_start.reserve((size_t)(c->n_cells + 1) * sizeof(uint32_t), s));
+    AC_TRY(c->order.reserve(nn * sizeof(int32_t), s));
+    AC_TRY(c->rank.reserve(nn * sizeof(int32_t), s));
+    AC_TRY(c->Ps.reserve(nn * sizeof(int4), s));
+    AC_TRY(c->mol_s.reserve(nn * sizeof(int32_t), s));
     uint32_t* cnt = c->cell_cnt.as<uint32_t>();
     uint32_t* start = c->cell_start.as<uint32_t>();
     AC_CUDA(cudaMemsetAsync(cnt, 0, (size_t)c->n_cells * sizeof(uint32_t), s));
@@ -197,13 +197,13 @@ __global__ void k_deg_scatter(const int64_t* __restrict__ cnt, int64_t n, unsign
 
 int build_neighbours(ac_ctx* c, cudaStream_t s) {
     const int64_t n = c->n;
-    AC_TRY(c->nb_cnt.reserve((size_t)(n + 1) * sizeof(int64_t)));
+    AC_TRY(c->nb_cnt.reserve((size_t)(n + 1) * sizeof(int64_t), s));
     int64_t* cntp = c->nb_cnt.as<int64_t>();
     if (n == 0) {
         c->nb_total = 0;
         c->n_wide = 0;
         AC_CUDA(cudaMemsetAsync(cntp, 0, sizeof(int64_t), s));
-        AC_TRY(c->nb.reserve(4));
+        AC_TRY(c->nb.reserve(4, s));
         return AC_OK;
     }
     const unsigned nb = (unsigned)((n + 127) / 128);
@@ -212,8 +212,8 @@ int build_neighbours(ac_ctx* c, cudaStream_t s) {
                                            c->cell_start.as<uint32_t>(), c->pc, n, cntp, nullptr, nullptr, dc);
     AC_LAUNCHED();
     // work order from the counts (before the in-place scan turns them into offsets)
-    AC_TRY(c->work.reserve((size_t)n * sizeof(int32_t)));
-    AC_TRY(c->deg.reserve(2 * DEG_BINS * sizeof(unsigned) + 64));
+    AC_TRY(c->work.reserve((size_t)n * sizeof(int32_t), s));
+    AC_TRY(c->deg.reserve(2 * DEG_BINS * sizeof(unsigned) + 64, s));
     unsigned* hist = c->deg.as<unsigned>();
     unsigned* cursor = hist + DEG_BINS;
     long long* n_wide = reinterpret_cast<long long*>(hist + 2 * DEG_BINS);  // byte 2064: 8-aligned
@@ -233,7 +233,7 @@ int build_neighbours(ac_ctx* c, cudaStream_t s) {
     c->n_wide = c->h_stage[1];
     if (h.err & DERR_COINCIDENT) return fail(AC_ERR_DEGENERATE, "two centres coincide after quantisation to 1/1024 A");
     c->nb_total = total;
-    AC_TRY(c->nb.reserve((size_t)(total > 0 ? total : 1) * sizeof(int32_t)));
+    AC_TRY(c->nb.reserve((size_t)(total > 0 ? total : 1) * sizeof(int32_t), s));
     k_neighbours<true><<<nb, 128, 0, s>>>(c->Ps.as<int4>(), c->mol_s.as<int32_t>(), c->grids.as<MolGrid>(),
                                           c->cell_start.as<uint32_t>(), c->pc, n, nullptr, cntp, c->nb.as<int32_t>(), dc);
     AC_LAUNCHED();

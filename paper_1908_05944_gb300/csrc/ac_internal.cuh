@@ -59,6 +59,11 @@ enum : uint32_t {
 // ---------------------------------------------------------------------------
 // grow-only device buffer
 
+// Device buffer from the device's stream-ordered memory pool (cudaMallocAsync),
+// which keeps freed blocks for reuse by later contexts instead of returning
+// them to the driver. Growth and release are ordered on the stream of the
+// entry point running (StreamScope), so no device-wide synchronisation is
+// needed, and a block is reused only after the work that used it.
 struct DevBuf {
     void* p = nullptr;
     size_t bytes = 0;
@@ -71,9 +76,18 @@ struct DevBuf {
     }
     DevBuf& operator=(DevBuf&& o) noexcept;
     ~DevBuf();
-    int reserve(size_t nbytes);  // keeps contents only if no growth happened
+    int reserve(size_t nbytes, cudaStream_t s);  // keeps contents only if no growth happened
     template <class T>
     T* as() const { return static_cast<T*>(p); }
+};
+
+// The stream on which buffers destroyed on this thread are released; set for
+// the duration of an entry point.
+cudaStream_t& release_stream();
+struct StreamScope {
+    cudaStream_t prev;
+    explicit StreamScope(cudaStream_t s) : prev(release_stream()) { release_stream() = s; }
+    ~StreamScope() { release_stream() = prev; }
 };
 
 // ---------------------------------------------------------------------------

@@ -33,7 +33,9 @@
 //     D = q_1.C_1, |D~ - D| <= e_D = gamma_3 (H^3 + sqrt3 H e_C) + sqrt3 H e_C;
 //     N = sum a_k C_k, |N~_c - N_c| <= e_N = 6.001 u H^2 sum|a~_k|;
 //     y = N / (2D), rho = e_D/|D~| <= 1/8, Y = max_c |y~_c|:
-//     e_y = (e_N/(2|D~|) + Y (rho + 2.01u)) (1+2.01u) / (1 - rho(1+2.01u) - 2.01u).
+//     e_y = (e_N/(2|D~|) + Y (rho + k)) (1+k) / (1 - rho(1+k) - k), k = 1.01 (u +
+//     delta_r), delta_r the reciprocal's relative error (FP32: rcp.approx,
+//     documented within 1 ulp, taken as 16u; FP64: correctly rounded, u).
 //   triangle: Gram entries by FMA, |g~ - g| <= gamma_3 H^2; det = g11 g22 - g12^2,
 //     |det~ - det| <= e_det = 15.01 u H^4; n = adj(G) a, |n~ - n| <= 6.01 u H^2
 //     (|a~_1| + |a~_2|); mu = n / (2 det) bounded as y above (e_mu); y = mu_1 q_1
@@ -71,8 +73,9 @@
 namespace ac {
 
 constexpr unsigned FULL = 0xffffffffu;
-constexpr int STAGE = 64;
+constexpr int STAGE = 32;
 constexpr int PAIR_CHUNK = 128;
+constexpr int CAND_CAP = 256;  // triangle or tetrahedron candidates written out per batch
 
 template <int WORDS>
 struct WarpSmem {
@@ -87,27 +90,32 @@ struct WarpSmem {
     unsigned Trow[M][WORDS];
     unsigned up[WORDS];
     unsigned char uplist[M];
+    unsigned char upf[M];  // edge (i, x) in Sigma^1, by position
     int n_up;
     int n_tet, n_tri, n_edge;
     int rowpre[M + 1];                // prefix sums of candidate counts per row of up
     int pairpre[PAIR_CHUNK + 1];      // prefix sums of tetrahedron candidates per Sigma^2 pair
     unsigned short pairs[PAIR_CHUNK]; // Sigma^2 pairs (p | k << 8) of the current chunk
+    unsigned cand[CAND_CAP];          // candidate codes (p | k << 8 [| l << 16]) of the current batch
     int4 st_tet[STAGE];
     int4 st_tri[STAGE];
     int2 st_edge[STAGE];
 };
 
+// Eight warps of 64-bit rows must fit four blocks per SM (228 KB, 1 KB reserved per block).
+static_assert(sizeof(WarpSmem<2>) * 8 <= 56 * 1024, "narrow per-atom kernel: 4 blocks of 8 warps per SM");
+
 // Constants of the bounds for one precision (derivation in the header comment).
 template <class R>
 struct Bounds {
     R H, K0, K1, eC, eD_tet, cN, eG, eDet, cn;
-    R k2;   // 2.01 u
+    R k2;   // >= 1.01 (u + delta_r): a reciprocal then a product (delta_r: 16u FP32, u FP64)
     R ky;   // 2.0001 u
     R ke;   // 1.0001 u
     R u;
     R g3s;    // gamma_3 (1 + gamma_3)
     R up1;    // >= 1 + 1.01 u
-    R two_up; // >= 2 (1 + 2u): 1/|X~| <= |rcp(2 X~)| two_up
+    R two_up; // >= 2 / (1 - delta_r): 1/|X~| <= |rcp(2 X~)| two_up
 };
 
 struct LocalArgs {
@@ -156,7 +164,13 @@ struct Ar<float> {
     static __device__ __forceinline__ float fma_up(float a, float b, float c) { return __fmaf_ru(a, b, c); }
     static __device__ __forceinline__ float add_up(float a, float b) { return __fadd_ru(a, b); }
     static __device__ __forceinline__ float sub_dn(float a, float b) { return __fsub_rd(a, b); }
-    static __device__ __forceinline__ float rcp(float a) { return __frcp_rn(a); }
+    // PTX rcp.approx.ftz.f32 (documented within 1 ulp of 1/a); the bounds
+    // below allow a relative error of 16u for it, not a correctly rounded one.
+    static __device__ __forceinline__ float rcp(float a) {
+        float r;
+        asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(a));
+        return r;
+    }
     static __device__ __forceinline__ float abs(float a) { return fabsf(a); }
     static __device__ __forceinline__ float max(float a, float b) { return fmaxf(a, b); }
 };
@@ -232,20 +246,6 @@ __device__ void stage_flush(const int lane, T* stage, int* n_stage, T* out, unsi
     __syncwarp();
 }
 
-template <class T>
-__device__ __forceinline__ void stage_push(const int lane, bool want, const T& item, T* stage, int* n_stage, T* out,
-                                           unsigned long long* counter, int64_t cap, unsigned* err, unsigned bit) {
-    unsigned b = __ballot_sync(FULL, want);
-    if (b == 0) return;
-    const int k = __popc(b);
-    if (*n_stage + k > STAGE) stage_flush(lane, stage, n_stage, out, counter, cap, err, bit);
-    const int cur = *n_stage;
-    if (want) stage[cur + __popc(b & lanemask_lt())] = item;
-    __syncwarp();
-    if (lane == 0) *n_stage = cur + k;
-    __syncwarp();
-}
-
 // warp-aggregated append of the lanes with want set
 template <class T>
 __device__ __forceinline__ void append_direct(bool want, const T& item, T* out, unsigned long long* counter, int64_t cap,
@@ -262,6 +262,26 @@ __device__ __forceinline__ void append_direct(bool want, const T& item, T* out, 
         if ((int64_t)slot < cap) out[slot] = item;
         else atomicOr(err, bit);
     }
+}
+
+// Staged append: items gather in shared memory and leave in runs of up to
+// STAGE; a warp step with more than STAGE items appends them directly.
+template <class T>
+__device__ __forceinline__ void stage_push(const int lane, bool want, const T& item, T* stage, int* n_stage, T* out,
+                                           unsigned long long* counter, int64_t cap, unsigned* err, unsigned bit) {
+    unsigned b = __ballot_sync(FULL, want);
+    if (b == 0) return;
+    const int k = __popc(b);
+    if (k > STAGE) {
+        append_direct(want, item, out, counter, cap, err, bit);
+        return;
+    }
+    if (*n_stage + k > STAGE) stage_flush(lane, stage, n_stage, out, counter, cap, err, bit);
+    const int cur = *n_stage;
+    if (want) stage[cur + __popc(b & lanemask_lt())] = item;
+    __syncwarp();
+    if (lane == 0) *n_stage = cur + k;
+    __syncwarp();
 }
 
 // largest r in [0, n) with pre[r] <= j (pre non-decreasing, pre[0] = 0 <= j)
@@ -328,10 +348,10 @@ __device__ __forceinline__ int ac3_from(const Ortho<R>& o, R T, const Bounds<R>&
     return 0;
 }
 
-// Bound of a quotient y = N / (2X) computed as fl(N~ r~), r~ = rcp(2 X~):
-// e = (eN/(2|X~|) + Y (rho + k)) (1 + k) / (1 - rho (1 + k) - k), k = 2.01u,
-// with rho = e_X/|X~| <= 1/8. No division: 1/|X~| <= inv = 2|r~|(1 + 2u) and
-// 1/(1 - x) <= 1 + 2x for x <= 1/2.
+// Bound of a quotient y = N / (2X) computed as fl(N~ r~), r~ = rcp(2 X~) with
+// relative error delta_r: e = (eN/(2|X~|) + Y (rho + k)) (1 + k) / (1 - rho (1 + k) - k),
+// k >= delta_r + u + delta_r u, rho = e_X/|X~| <= 1/8. No division:
+// 1/|X~| <= inv = 2|r~|/(1 - delta_r) and 1/(1 - x) <= 1 + 2x for x <= 1/2.
 template <class R>
 __device__ __forceinline__ R quotient_bound(R eN, R inv, R Y, R rho, const Bounds<R>& B) {
     using A = Ar<R>;
@@ -450,9 +470,9 @@ __device__ __forceinline__ int ac2_scan(const WarpSmem<WORDS>& S, int nw, const 
             const P4<R> v = point<R>(S, x);
             const R t = A::fma(v.z, o.y2, A::fma(v.y, o.y1, A::mul(v.x, o.y0)));
             const R d = A::fma(R(-2), t, v.w);
+            n_ok++;
             if (d < -E) return -1;
-            if (d > E) n_ok++;
-            else open = true;
+            if (!(d > E)) open = true;
         }
     }
     return open ? 0 : 1;
@@ -461,7 +481,7 @@ __device__ __forceinline__ int ac2_scan(const WarpSmem<WORDS>& S, int nw, const 
 // ---------------------------------------------------------------------------
 
 template <int WORDS, class R>
-__global__ void __launch_bounds__(256) k_local(LocalArgs A) {
+__global__ void __launch_bounds__(256, 4) k_local(LocalArgs A) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     using SM = WarpSmem<WORDS>;
     constexpr int MAXM = SM::M;
@@ -506,14 +526,46 @@ __global__ void __launch_bounds__(256) k_local(LocalArgs A) {
         const int nw = (m + 31) >> 5;
         const R T = (R)si;  // W_i + A <= 2^24: exact
 
-        // ---- phase A: load L(i); vertex AC2 (Step 5); upper edges with exact edge AC3
-        unsigned vert_bad = 0;
+        // ---- phase A: load L(i) in order of distance from p_i; vertex AC2
+        // (Step 5); upper edges with exact edge AC3. The order only changes
+        // the order of the AC2 tests: the nearest balls are the likeliest
+        // violators of the simplices around p_i, so scans stop sooner.
 #pragma unroll 1
         for (int w = 0; w < nw; w++) {
             const int e = 32 * w + lane;
-            bool upper = false;
             if (e < m) {
                 const int x = A.nb[off + e];
+                const int4 o = A.Ps[x];
+                const int qx = o.x - Pi.x, qy = o.y - Pi.y, qz = o.z - Pi.z;
+                S.idx[e] = x;
+                S.ai[e] = qx * qx + qy * qy + qz * qz;  // <= 2^26
+            }
+        }
+        __syncwarp();
+        int xr[WORDS], rr[WORDS];
+#pragma unroll
+        for (int w = 0; w < WORDS; w++) {
+            const int e = 32 * w + lane;
+            xr[w] = -1;
+            rr[w] = 0;
+            if (w < nw && e < m) {
+                const int De = S.ai[e];
+                int rank = 0;
+#pragma unroll 4
+                for (int f = 0; f < m; f++) {
+                    const int Df = S.ai[f];
+                    rank += (Df < De || (Df == De && f < e)) ? 1 : 0;
+                }
+                xr[w] = S.idx[e];
+                rr[w] = rank;
+            }
+        }
+        __syncwarp();
+        unsigned vert_bad = 0;
+#pragma unroll
+        for (int w = 0; w < WORDS; w++) {
+            if (xr[w] >= 0) {
+                const int x = xr[w], e = rr[w];
                 const int4 o = A.Ps[x];
                 const int qx = o.x - Pi.x, qy = o.y - Pi.y, qz = o.z - Pi.z;
                 const int D = qx * qx + qy * qy + qz * qz;  // <= 2^26
@@ -527,14 +579,21 @@ __global__ void __launch_bounds__(256) k_local(LocalArgs A) {
                 S.idx[e] = x;
                 // Delta_x = a_x at p_i; a tie goes against the larger input index
                 if (ax < 0 || (ax == 0 && gx < gi)) vert_bad = 1;
+                bool upper = false;
                 if (x > i) {
                     // edge AC3: (D + W_i - W_x)^2 <= 4 D (W_i + A)
                     const long long a = (long long)D + Wi - o.w;
                     upper = a * a <= 4ll * D * si;
                     n_ac3e++;
                 }
+                S.upf[e] = upper ? 1 : 0;
             }
-            const unsigned b = __ballot_sync(FULL, upper);
+        }
+        __syncwarp();
+#pragma unroll 1
+        for (int w = 0; w < nw; w++) {
+            const int e = 32 * w + lane;
+            const unsigned b = __ballot_sync(FULL, e < m && S.upf[e] != 0);
             if (lane == 0) S.up[w] = b;
         }
         if (lane == 0)
@@ -601,68 +660,82 @@ __global__ void __launch_bounds__(256) k_local(LocalArgs A) {
         __syncwarp();
 
         // ---- phase C: triangles (i,p,k): AC3, then AC2 at the orthocentre -----
-        // candidates of row r (p = uplist[r]): k in M[p] & up, k > p
-        {
-            int run = 0;
-            for (int r0 = 0; r0 < n_up; r0 += 32) {
-                int c = 0;
-                if (r0 + lane < n_up) {
-                    const int p = S.uplist[r0 + lane];
-                    for (int w = 0; w < nw; w++) c += __popc(S.Mrow[p][w] & S.up[w] & above_mask(w, p));
-                }
-                int tot;
-                const int ex = warp_excl(lane, c, &tot);
-                if (r0 + lane < n_up) S.rowpre[r0 + lane] = run + ex;
-                run += tot;
-            }
-            if (lane == 0) S.rowpre[n_up] = run;
-        }
-        __syncwarp();
-        {
-            const int total = S.rowpre[n_up];
+        // Candidates of row r (p = uplist[r]): k in M[p] & up, k > p. Rows are
+        // taken 32 at a time, one per lane; each writes its candidates as codes
+        // p | k << 8 to cand[] in row order (CAND_CAP per batch), and windows
+        // of 32 candidates read them back.
 #pragma unroll 1
-            for (int base = 0; base < total; base += 32) {
-                const int j = base + lane;
-                const bool valid = j < total;
-                bool pass = false, pend = false, keep_it = false;
-                int pend_ac3 = 0;
-                int pp = 0, kk = 0;
-                if (valid) {
-                    const int r = row_of(S.rowpre, n_up, j);
-                    pp = S.uplist[r];
-                    kk = nth_in_words(nw, j - S.rowpre[r],
-                                      [&](int w) { return S.Mrow[pp][w] & S.up[w] & above_mask(w, pp); });
-                    n_ac3t++;
-                    const Ortho<R> o = ortho_tri<R>(point<R>(S, pp), point<R>(S, kk), T, B);
-                    if (o.ac3 >= 0) {
-                        // potential, or not yet excluded: tetrahedra may build on it
-                        atomicOr(&S.Trow[pp][kk >> 5], 1u << (kk & 31));
-                        if (o.ac3 > 0) {
-                            n_s2++;
-                            keep_it = true;
-                            const int r2 = ac2_scan<R>(S, nw, o, B, 2, pp, kk, 0, n_tri);
-                            pass = r2 > 0;
-                            pend = r2 == 0;
-                        } else {
-                            pend = true;
-                            pend_ac3 = 1;
+        for (int r0 = 0; r0 < n_up; r0 += 32) {
+            const bool rv = r0 + lane < n_up;
+            const int p = rv ? S.uplist[r0 + lane] : 0;
+            int c = 0;
+            if (rv)
+                for (int w = 0; w < nw; w++) c += __popc(S.Mrow[p][w] & S.up[w] & above_mask(w, p));
+            int tot;
+            const int ex = warp_excl(lane, c, &tot);
+#pragma unroll 1
+            for (int done = 0; done < tot; done += CAND_CAP) {
+                if (c > 0 && ex < done + CAND_CAP && ex + c > done) {
+                    int t = ex;
+                    for (int w = 0; w < nw; w++) {
+                        unsigned b = S.Mrow[p][w] & S.up[w] & above_mask(w, p);
+                        while (b) {
+                            const int k = 32 * w + __ffs(b) - 1;
+                            b &= b - 1;
+                            if (t >= done && t < done + CAND_CAP) S.cand[t - done] = (unsigned)p | ((unsigned)k << 8);
+                            t++;
                         }
                     }
                 }
-                const int4 item = make_int4(i, valid ? S.idx[pp] : 0, valid ? S.idx[kk] : 0, 0);
-                if (keep)
-                    append_direct(keep_it, item, A.cand2, &cnt->n_cand_out[2], A.cap_cand[2], &cnt->err, DERR_OVF_CAND);
-                append_direct(pend, make_int4(pend_ac3 ? ~i : i, item.y, item.z, -1), A.pending, &cnt->n_pending,
-                              A.cap_pending, &cnt->err, DERR_OVF_PEND);
-                stage_push(lane, pass, item, S.st_tri, &S.n_tri, A.tri_out, &cnt->n_tri_pass, A.cap_tri, &cnt->err,
-                           DERR_OVF_TRI);
+                __syncwarp();
+                const int nbatch = min(CAND_CAP, tot - done);
+#pragma unroll 1
+                for (int base = 0; base < nbatch; base += 32) {
+                    const int j = base + lane;
+                    const bool valid = j < nbatch;
+                    bool pass = false, pend = false, keep_it = false;
+                    int pend_ac3 = 0;
+                    int pp = 0, kk = 0;
+                    if (valid) {
+                        const unsigned code = S.cand[j];
+                        pp = code & 255u;
+                        kk = code >> 8;
+                        n_ac3t++;
+                        const Ortho<R> o = ortho_tri<R>(point<R>(S, pp), point<R>(S, kk), T, B);
+                        if (o.ac3 >= 0) {
+                            // potential, or not yet excluded: tetrahedra may build on it
+                            atomicOr(&S.Trow[pp][kk >> 5], 1u << (kk & 31));
+                            if (o.ac3 > 0) {
+                                n_s2++;
+                                keep_it = true;
+                                const int r2 = ac2_scan<R>(S, nw, o, B, 2, pp, kk, 0, n_tri);
+                                pass = r2 > 0;
+                                pend = r2 == 0;
+                            } else {
+                                pend = true;
+                                pend_ac3 = 1;
+                            }
+                        }
+                    }
+                    const int4 item = make_int4(i, valid ? S.idx[pp] : 0, valid ? S.idx[kk] : 0, 0);
+                    if (keep)
+                        append_direct(keep_it, item, A.cand2, &cnt->n_cand_out[2], A.cap_cand[2], &cnt->err,
+                                      DERR_OVF_CAND);
+                    append_direct(pend, make_int4(pend_ac3 ? ~i : i, item.y, item.z, -1), A.pending, &cnt->n_pending,
+                                  A.cap_pending, &cnt->err, DERR_OVF_PEND);
+                    stage_push(lane, pass, item, S.st_tri, &S.n_tri, A.tri_out, &cnt->n_tri_pass, A.cap_tri, &cnt->err,
+                               DERR_OVF_TRI);
+                }
+                __syncwarp();
             }
         }
         __syncwarp();
 
         // ---- phase D: tetrahedra (i,p,k,l): AC3, then AC2 ----------------------
         // Sigma^2 pairs (p,k): row r of up holds popc(T[p]) of them; pairs are taken
-        // PAIR_CHUNK at a time with a prefix over their candidate counts popc(T[p] & T[k])
+        // PAIR_CHUNK at a time with a prefix over their candidate counts popc(T[p] & T[k]);
+        // their candidates l are written as codes p | k << 8 | l << 16 to cand[]
+        // (CAND_CAP per batch) and read back by windows of 32.
         {
             int run = 0;
             for (int r0 = 0; r0 < n_up; r0 += 32) {
@@ -705,40 +778,62 @@ __global__ void __launch_bounds__(256) k_local(LocalArgs A) {
             __syncwarp();
             const int total = S.pairpre[cn];
 #pragma unroll 1
-            for (int base = 0; base < total; base += 32) {
-                const int j = base + lane;
-                const bool valid = j < total;
-                bool pass = false, pend = false, keep_it = false;
-                int pend_ac3 = 0;
-                int p3 = 0, k3 = 0, ll = 0;
-                if (valid) {
-                    const int q = row_of(S.pairpre, cn, j);
-                    const int code = S.pairs[q];
-                    p3 = code & 255;
-                    k3 = code >> 8;
-                    ll = nth_in_words(nw, j - S.pairpre[q], [&](int w) { return S.Trow[p3][w] & S.Trow[k3][w]; });
-                    n_ac3k++;
-                    const Ortho<R> o = ortho_tet<R>(point<R>(S, p3), point<R>(S, k3), point<R>(S, ll), T, B);
-                    if (o.ac3 > 0) {
-                        n_s3++;
-                        keep_it = true;
-                        const int r3 = ac2_scan<R>(S, nw, o, B, 3, p3, k3, ll, n_tet);
-                        pass = r3 > 0;
-                        pend = r3 == 0;
-                    } else if (o.ac3 == 0) {
-                        pend = true;
-                        pend_ac3 = 1;
+            for (int done = 0; done < total; done += CAND_CAP) {
+                for (int q = lane; q < cn; q += 32) {
+                    const int a0 = S.pairpre[q], a1 = S.pairpre[q + 1];
+                    if (a1 <= done || a0 >= done + CAND_CAP) continue;
+                    const unsigned code = S.pairs[q];
+                    const int p = code & 255u, k = code >> 8;
+                    int t = a0;
+                    for (int w = 0; w < nw; w++) {
+                        unsigned b = S.Trow[p][w] & S.Trow[k][w];
+                        while (b) {
+                            const int l = 32 * w + __ffs(b) - 1;
+                            b &= b - 1;
+                            if (t >= done && t < done + CAND_CAP) S.cand[t - done] = code | ((unsigned)l << 16);
+                            t++;
+                        }
                     }
                 }
-                const int4 item = make_int4(i, valid ? S.idx[p3] : 0, valid ? S.idx[k3] : 0, valid ? S.idx[ll] : 0);
-                if (keep)
-                    append_direct(keep_it, item, A.cand3, &cnt->n_cand_out[3], A.cap_cand[3], &cnt->err, DERR_OVF_CAND);
-                append_direct(pend, make_int4(pend_ac3 ? ~i : i, item.y, item.z, item.w), A.pending, &cnt->n_pending,
-                              A.cap_pending, &cnt->err, DERR_OVF_PEND);
-                stage_push(lane, pass, item, S.st_tet, &S.n_tet, A.tet_out, &cnt->n_tet_out, A.cap_tet, &cnt->err,
-                           DERR_OVF_TET);
+                __syncwarp();
+                const int nbatch = min(CAND_CAP, total - done);
+#pragma unroll 1
+                for (int base = 0; base < nbatch; base += 32) {
+                    const int j = base + lane;
+                    const bool valid = j < nbatch;
+                    bool pass = false, pend = false, keep_it = false;
+                    int pend_ac3 = 0;
+                    int p3 = 0, k3 = 0, ll = 0;
+                    if (valid) {
+                        const unsigned code = S.cand[j];
+                        p3 = code & 255u;
+                        k3 = (code >> 8) & 255u;
+                        ll = code >> 16;
+                        n_ac3k++;
+                        const Ortho<R> o = ortho_tet<R>(point<R>(S, p3), point<R>(S, k3), point<R>(S, ll), T, B);
+                        if (o.ac3 > 0) {
+                            n_s3++;
+                            keep_it = true;
+                            const int r3 = ac2_scan<R>(S, nw, o, B, 3, p3, k3, ll, n_tet);
+                            pass = r3 > 0;
+                            pend = r3 == 0;
+                        } else if (o.ac3 == 0) {
+                            pend = true;
+                            pend_ac3 = 1;
+                        }
+                    }
+                    const int4 item =
+                        make_int4(i, valid ? S.idx[p3] : 0, valid ? S.idx[k3] : 0, valid ? S.idx[ll] : 0);
+                    if (keep)
+                        append_direct(keep_it, item, A.cand3, &cnt->n_cand_out[3], A.cap_cand[3], &cnt->err,
+                                      DERR_OVF_CAND);
+                    append_direct(pend, make_int4(pend_ac3 ? ~i : i, item.y, item.z, item.w), A.pending,
+                                  &cnt->n_pending, A.cap_pending, &cnt->err, DERR_OVF_PEND);
+                    stage_push(lane, pass, item, S.st_tet, &S.n_tet, A.tet_out, &cnt->n_tet_out, A.cap_tet, &cnt->err,
+                               DERR_OVF_TET);
+                }
+                __syncwarp();
             }
-            __syncwarp();
         }
 
         // ---- phase E: edges (i,p): AC2 at the edge's orthocentre ---------------
@@ -1046,6 +1141,9 @@ static int launch_pass(ac_ctx* c, int words, LocalArgs& a, cudaStream_t s) {
 // Constants of the bounds at unit roundoff u (derivation in the header comment).
 template <class R>
 static void set_bounds(double u, double h, int64_t wmax, Bounds<R>& b) {
+    // reciprocal error: FP32 rcp.approx is documented within 1 ulp (2u); 16u is
+    // taken, a wide margin at no measurable cost. FP64 is correctly rounded (u).
+    const double delta_r = sizeof(R) == 4 ? 16.0 * u : u;
     auto up = [](double x) {
         const R r = (R)(x * (1.0 + 1e-12));
         return (double)r >= x ? r : (R)nextafter(r, (R)INFINITY);
@@ -1063,13 +1161,13 @@ static void set_bounds(double u, double h, int64_t wmax, Bounds<R>& b) {
     b.cn = up(6.01 * u * H * H * slack);
     b.K0 = up((u * Am + 2 * g3 * H * h) * slack);
     b.K1 = up(2 * s3 * H * (1 + g3) * slack);
-    b.k2 = up(2.01 * u);
+    b.k2 = up((delta_r + u) * 1.01);
     b.ky = up(2.0001 * u);
     b.ke = up(1.0001 * u);
     b.u = up(u);
     b.g3s = up(g3 * (1 + g3) * slack);
     b.up1 = up(1.0 + 1.01 * u * slack);
-    b.two_up = up(2.0 * (1.0 + 2.0 * u));
+    b.two_up = up(2.0 / (1.0 - delta_r) * (1.0 + 4.0 * u));
 }
 
 static void set_constants(const PredConst& pc, int64_t wmax, LocalArgs& a) {
@@ -1108,15 +1206,15 @@ int run_local(ac_ctx* c, cudaStream_t s) {
     }
     const int64_t wmax = c->pc.H2 - c->pc.A;  // max W over the atoms
     for (int attempt = 0; attempt < 4; attempt++) {
-        AC_TRY(c->tet_out.reserve((size_t)c->cap_tet * sizeof(int4)));
-        AC_TRY(c->tri_pass.reserve((size_t)c->cap_tri * sizeof(int4)));
-        AC_TRY(c->edge_pass.reserve((size_t)c->cap_edge * sizeof(int2)));
-        AC_TRY(c->pending.reserve((size_t)c->cap_pending * sizeof(int4)));
-        AC_TRY(c->vert_pass.reserve(nn));
+        AC_TRY(c->tet_out.reserve((size_t)c->cap_tet * sizeof(int4), s));
+        AC_TRY(c->tri_pass.reserve((size_t)c->cap_tri * sizeof(int4), s));
+        AC_TRY(c->edge_pass.reserve((size_t)c->cap_edge * sizeof(int2), s));
+        AC_TRY(c->pending.reserve((size_t)c->cap_pending * sizeof(int4), s));
+        AC_TRY(c->vert_pass.reserve(nn, s));
         if (c->pc.keep_candidates) {
-            AC_TRY(c->cand[1].reserve((size_t)c->cap_cand[1] * sizeof(int2)));
-            AC_TRY(c->cand[2].reserve((size_t)c->cap_cand[2] * sizeof(int4)));
-            AC_TRY(c->cand[3].reserve((size_t)c->cap_cand[3] * sizeof(int4)));
+            AC_TRY(c->cand[1].reserve((size_t)c->cap_cand[1] * sizeof(int2), s));
+            AC_TRY(c->cand[2].reserve((size_t)c->cap_cand[2] * sizeof(int4), s));
+            AC_TRY(c->cand[3].reserve((size_t)c->cap_cand[3] * sizeof(int4), s));
         }
         // zero the per-pass counters (keep max_degree and err)
         DevCounters* dc = c->counters.as<DevCounters>();
