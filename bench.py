@@ -19,6 +19,7 @@ builds its own copy; value = atoms of all ranks / max-over-ranks time.
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import subprocess
@@ -46,7 +47,7 @@ SMS = 152
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--steps", type=int, default=100)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default="globule100k_probe")
@@ -103,7 +104,7 @@ class ClockSampler:
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self._t = threading.Thread(target=self._read, daemon=True)
             self._t.start()
@@ -147,6 +148,26 @@ class ClockSampler:
 def workload(name):
     import synth
     return synth.workload(name)
+
+
+def profiled_traffic(workload):
+    """DRAM bytes per per-atom pass from the committed ncu summary, or None when
+    the kernel source changed since that capture or the workload differs."""
+    here = os.path.dirname(os.path.abspath(__file__))
+    prof = os.path.join(here, "profiles", "k_local_globule100k.md")
+    src = os.path.join(here, "paper_1908_05944_gb300", "csrc", "ac_local.cu")
+    if workload != "globule100k_probe" or not (os.path.exists(prof) and os.path.exists(src)):
+        return None
+    fields = {}
+    for ln in open(prof):
+        if ":" in ln and ln.split(":", 1)[0] in ("traffic_bytes_per_pass", "source_sha256"):
+            k, v = ln.split(":", 1)
+            fields[k] = v.strip()
+    with open(src, "rb") as f:
+        sha = hashlib.sha256(f.read()).hexdigest()
+    if fields.get("source_sha256") != sha or "traffic_bytes_per_pass" not in fields:
+        return None
+    return int(fields["traffic_bytes_per_pass"])
 
 
 def measured_peaks():
@@ -428,7 +449,8 @@ def main():
         "gpu_launches": res["launches"],
         "roofline": {"bound": "alu", "kernel": "k_local (fused estimation + pruning)", "achieved": achieved,
                      "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved / peak_tflops if peak_tflops else None,
-                     "traffic": None,
+                     "traffic": profiled_traffic(args.workload),
+                     "traffic_unit": "bytes per pass (ncu dram read + write, both launches)",
                      "peak_basis": f"FP32 FMA: {SMS} SMs x {FP32_LANES_PER_SM} lanes x 2 x {sm_mhz:.0f} MHz "
                                    "(derived; sampled SM clock)"},
         "stage_ms": res["stats"]["ms_stage"],

@@ -1197,7 +1197,7 @@ int run_local(ac_ctx* c, cudaStream_t s) {
         c->cap_tet = (int64_t)nn * 12 + 1024;
         c->cap_tri = (int64_t)nn * 16 + 1024;
         c->cap_edge = (int64_t)nn * 12 + 1024;
-        c->cap_pending = (int64_t)nn / 8 + 4096;
+        c->cap_pending = (int64_t)nn * 2 + 4096;  // escalated simplices: about 1.3 per atom with probe radii
     }
     if (c->pc.keep_candidates && c->cap_cand[1] == 0) {
         c->cap_cand[1] = (int64_t)nn * 32 + 1024;
