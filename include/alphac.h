@@ -73,7 +73,10 @@ typedef struct {
     double cell_factor;    /* grid cell side = cell_factor * sqrt(r_max^2 + alpha); 0 = 1.0 */
     int32_t block_warps;   /* warps per block of the per-atom kernel; 0 = 8 */
     int32_t keep_candidates; /* 1: also keep the estimation-pass lists Sigma_ortho^1..3 */
-    int32_t reserved[8];
+    int32_t no_graph;        /* 1: every ac_build synchronises with the host at each list size
+                                (default 0: later builds of a context replay its first build's
+                                launch sequence as one CUDA graph, see ac_build) */
+    int32_t reserved[7];
 } ac_options;
 
 typedef struct {
@@ -92,7 +95,9 @@ typedef struct {
     double ms_total;        /* device time of the last ac_build (CUDA events) */
     double ms_stage[8];     /* grid, neighbours, per-atom pass, canonical K3, K2, K1+K0+lists, filtration,
                                and the per-atom kernel's own launch */
-    int64_t kernel_launches; /* kernels the last ac_build launched */
+    int64_t kernel_launches; /* kernels the last ac_build launched (graph nodes when replayed) */
+    int32_t replayed;        /* 1: the last ac_build ran as a CUDA graph replay */
+    int32_t host_syncs;      /* host waits for the device during the last ac_build */
 } ac_stats;
 
 /*
@@ -122,7 +127,12 @@ AC_API int ac_create_batch(const double* centres, const double* radii, const int
 /*
  * Compute the alpha complex (Steps 1-5 of Section 3.1; Sections 4.2-4.4) and
  * the filtration values. Enqueued on stream; returns after the device work is
- * finished (list sizes are read back to size the results).
+ * finished. The first build of a context reads each list size back to size
+ * the next step (a few host waits). A context's inputs never change, so later
+ * builds (unless opt.no_graph) replay the same launch sequence, captured once
+ * as a CUDA graph, with every size the first build read checked on the device;
+ * a mismatch (not expected: the computation is deterministic) makes that call
+ * fall back to a synchronised build. Results are identical either way.
  * Errors: AC_ERR_DEGENERATE, AC_ERR_CAPACITY, AC_ERR_OOM, AC_ERR_CUDA.
  */
 AC_API int ac_build(ac_ctx* ctx, void* stream);

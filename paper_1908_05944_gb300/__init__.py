@@ -43,7 +43,7 @@ EXPORTS = ["ac_create", "ac_create_batch", "ac_build", "ac_get_simplices", "ac_f
 class ac_options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("filtration", ctypes.c_int32), ("cell_factor", ctypes.c_double),
                 ("block_warps", ctypes.c_int32), ("keep_candidates", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 8)]
+                ("no_graph", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
 
 
 class ac_stats(ctypes.Structure):
@@ -52,7 +52,8 @@ class ac_stats(ctypes.Structure):
                 ("ac2_tests_tet", ctypes.c_int64 * 3), ("ac2_tests_tri", ctypes.c_int64 * 3),
                 ("ac2_tests_edge", ctypes.c_int64), ("ac3_tests", ctypes.c_int64 * 4), ("ac3_exact", ctypes.c_int64),
                 ("ms_total", ctypes.c_double),
-                ("ms_stage", ctypes.c_double * 8), ("kernel_launches", ctypes.c_int64)]
+                ("ms_stage", ctypes.c_double * 8), ("kernel_launches", ctypes.c_int64),
+                ("replayed", ctypes.c_int32), ("host_syncs", ctypes.c_int32)]
 
     def to_dict(self):
         out = {}
@@ -161,13 +162,14 @@ class _DeviceArray:
 
 
 def options(precision=AC_PRECISION_FILTERED, filtration=AC_FILTRATION_SIZE, cell_factor=0.0, block_warps=0,
-            keep_candidates=False) -> ac_options:
+            keep_candidates=False, no_graph=False) -> ac_options:
     o = ac_options()
     o.precision = precision
     o.filtration = filtration
     o.cell_factor = cell_factor
     o.block_warps = block_warps
     o.keep_candidates = 1 if keep_candidates else 0
+    o.no_graph = 1 if no_graph else 0
     return o
 
 

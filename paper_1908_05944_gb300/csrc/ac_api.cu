@@ -37,6 +37,9 @@ cudaStream_t& release_stream() {
     return s;
 }
 
+// Set while a replay is captured: every buffer must already have its size.
+static thread_local bool g_no_alloc = false;
+
 // Keep up to this many freed bytes per device in the pool between builds.
 static constexpr uint64_t POOL_KEEP_BYTES = 16ull << 30;
 
@@ -73,6 +76,7 @@ DevBuf& DevBuf::operator=(DevBuf&& o) noexcept {
 
 int DevBuf::reserve(size_t nbytes, cudaStream_t s) {
     if (nbytes <= bytes && p) return AC_OK;
+    if (g_no_alloc) return fail(AC_ERR_STATE, "a buffer would grow during graph capture");
     if (p) {
         cudaFreeAsync(p, s);
         p = nullptr;
@@ -207,9 +211,46 @@ int scan_exclusive_u32_to_u32(const uint32_t* in, uint32_t* out, int64_t n, DevB
     return scan_entry<unsigned>(in, out, n, tmp, s);
 }
 
+int sync_host(ac_ctx* c, cudaStream_t s) {
+    c->host_syncs++;
+    AC_CUDA(cudaStreamSynchronize(s));
+    return AC_OK;
+}
+
+__global__ void k_expect_i64(const int64_t* __restrict__ v, int64_t want, unsigned* __restrict__ err) {
+    if (threadIdx.x == 0 && *v != want) atomicOr(err, DERR_REPLAY);
+}
+
+__global__ void k_expect_u64(const unsigned long long* __restrict__ v, unsigned long long want, unsigned* __restrict__ err) {
+    if (threadIdx.x == 0 && *v != want) atomicOr(err, DERR_REPLAY);
+}
+
+__global__ void k_expect_i32s(const int32_t* __restrict__ v, const int32_t* __restrict__ want, int64_t n,
+                              unsigned* __restrict__ err) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < n && v[j] != want[j]) atomicOr(err, DERR_REPLAY);
+}
+
+int stage_mark(ac_ctx* c, int k, cudaStream_t s) {
+    AC_CUDA(cudaEventRecordWithFlags(c->ev[k], s, c->replaying ? cudaEventRecordExternal : cudaEventRecordDefault));
+    return AC_OK;
+}
+
+int expect_i64(ac_ctx* c, const int64_t* d_value, int64_t want, cudaStream_t s) {
+    k_expect_i64<<<1, 32, 0, s>>>(d_value, want, &c->counters.as<DevCounters>()->err);
+    AC_LAUNCHED();
+    return AC_OK;
+}
+
+int expect_u64(ac_ctx* c, const unsigned long long* d_value, unsigned long long want, cudaStream_t s) {
+    k_expect_u64<<<1, 32, 0, s>>>(d_value, want, &c->counters.as<DevCounters>()->err);
+    AC_LAUNCHED();
+    return AC_OK;
+}
+
 int read_counters(ac_ctx* c, DevCounters* h, cudaStream_t s) {
     AC_CUDA(cudaMemcpyAsync(c->h_cnt, c->counters.p, sizeof(DevCounters), cudaMemcpyDeviceToHost, s));
-    AC_CUDA(cudaStreamSynchronize(s));
+    AC_TRY(sync_host(c, s));
     *h = *c->h_cnt;
     c->hc = *h;
     return AC_OK;
@@ -292,8 +333,9 @@ __global__ void k_fill_mol(const int64_t* __restrict__ mol_off, int64_t n_mol, i
     for (int64_t i = mol_off[m] + threadIdx.x; i < mol_off[m + 1]; i += blockDim.x) mol_of[i] = (int32_t)m;
 }
 
-__global__ void k_init_bbox(int32_t* bbox, int64_t n_mol) {
+__global__ void k_init_bbox(int32_t* bbox, int64_t n_mol, DevCounters* cnt) {
     int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (m == 0) cnt->bad_index = INT32_MAX;
     if (m >= n_mol) return;
     for (int k = 0; k < 3; k++) {
         bbox[6 * m + k] = INT32_MAX;
@@ -310,23 +352,30 @@ int quantise_and_plan(ac_ctx* c, cudaStream_t s) {
     AC_TRY(c->scratch[1].reserve(sizeof(int), s));
     DevCounters* dc = c->counters.as<DevCounters>();
     AC_CUDA(cudaMemsetAsync(dc, 0, sizeof(DevCounters), s));
-    const int big = INT32_MAX;
-    AC_CUDA(cudaMemcpyAsync(&dc->bad_index, &big, sizeof(int), cudaMemcpyHostToDevice, s));
     int32_t* bbox = c->scratch[0].as<int32_t>();
     int* wmax = c->scratch[1].as<int>();
     AC_CUDA(cudaMemsetAsync(wmax, 0, sizeof(int), s));
-    k_init_bbox<<<(unsigned)((n_mol + 255) / 256), 256, 0, s>>>(bbox, n_mol);
+    k_init_bbox<<<(unsigned)((n_mol + 255) / 256), 256, 0, s>>>(bbox, n_mol, dc);
     AC_LAUNCHED();
     if (n > 0) {
         k_quantise<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(c->centres.as<double>(), c->radii.as<double>(), n,
                                                               c->mol_of.as<int32_t>(), c->P.as<int4>(), bbox, wmax, dc);
         AC_LAUNCHED();
     }
+    if (c->replaying) {
+        // the recorded plan stands; check the bounds it rests on
+        k_expect_i32s<<<(unsigned)((n_mol * 6 + 255) / 256), 256, 0, s>>>(bbox, c->rec_bbox.as<int32_t>(), n_mol * 6,
+                                                                          &dc->err);
+        AC_LAUNCHED();
+        k_expect_i32s<<<1, 32, 0, s>>>(wmax, c->rec_bbox.as<int32_t>() + n_mol * 6, 1, &dc->err);
+        AC_LAUNCHED();
+        return AC_OK;
+    }
     // one readback: counters, largest weight, per-molecule boxes
     AC_CUDA(cudaMemcpyAsync(c->h_cnt, c->counters.p, sizeof(DevCounters), cudaMemcpyDeviceToHost, s));
     AC_CUDA(cudaMemcpyAsync(c->h_stage, wmax, sizeof(int), cudaMemcpyDeviceToHost, s));
     AC_CUDA(cudaMemcpyAsync(c->h_bbox, bbox, (size_t)n_mol * 6 * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-    AC_CUDA(cudaStreamSynchronize(s));
+    AC_TRY(sync_host(c, s));
     const DevCounters hc = *c->h_cnt;
     if (hc.err & DERR_INVALID) {
         char b[128];
@@ -382,7 +431,7 @@ int quantise_and_plan(ac_ctx* c, cudaStream_t s) {
     c->n_cells = total;
     AC_TRY(c->grids.reserve((size_t)n_mol * sizeof(MolGrid), s));
     AC_CUDA(cudaMemcpyAsync(c->grids.p, grids.data(), (size_t)n_mol * sizeof(MolGrid), cudaMemcpyHostToDevice, s));
-    AC_CUDA(cudaStreamSynchronize(s));
+    AC_TRY(sync_host(c, s));  // the host copy of the grids goes out of scope
     c->stats.grid_dims[0] = grids[0].dims[0];
     c->stats.grid_dims[1] = grids[0].dims[1];
     c->stats.grid_dims[2] = grids[0].dims[2];
@@ -434,7 +483,8 @@ static int create_impl(const double* centres, const double* radii, const int64_t
         if (cudaEventCreate(&c->ev[k]) != cudaSuccess) return bail(cuda_fail(cudaGetLastError(), "cudaEventCreate", __FILE__, __LINE__));
     if (cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess ||
-        cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess)
+        cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
         return bail(cuda_fail(cudaGetLastError(), "side stream", __FILE__, __LINE__));
     {
         const size_t a0 = 64 * sizeof(int64_t), a1 = (sizeof(DevCounters) + 255) & ~(size_t)255;
@@ -486,8 +536,94 @@ extern "C" int ac_create_batch(const double* centres, const double* radii, const
 
 static float elapsed(cudaEvent_t a, cudaEvent_t b) {
     float ms = 0.f;
-    cudaEventElapsedTime(&ms, a, b);
+    if (cudaEventElapsedTime(&ms, a, b) != cudaSuccess) {
+        cudaGetLastError();  // a stage time is a statistic: leave no error behind
+        return -1.f;
+    }
     return ms;
+}
+
+// The whole path on one stream: rows a1-a13 in order.
+static int build_body(ac_ctx* c, cudaStream_t s) {
+    AC_TRY(stage_mark(c, 0, s));
+    AC_TRY(quantise_and_plan(c, s));
+    AC_TRY(build_grid(c, s));
+    AC_TRY(stage_mark(c, 1, s));
+    AC_TRY(build_neighbours(c, s));
+    AC_TRY(stage_mark(c, 2, s));
+    AC_TRY(run_local(c, s));
+    AC_TRY(stage_mark(c, 3, s));
+    AC_TRY(canonicalise(c, s));
+    AC_TRY(stage_mark(c, 6, s));
+    AC_TRY(compute_filtration(c, s));
+    AC_TRY(stage_mark(c, 7, s));
+    return AC_OK;
+}
+
+static bool same_plan(const ac_options& a, const ac_options& b) {
+    return a.precision == b.precision && a.filtration == b.filtration && a.cell_factor == b.cell_factor &&
+           a.block_warps == b.block_warps && a.keep_candidates == b.keep_candidates;
+}
+
+static void drop_graph(ac_ctx* c) {
+    if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+    if (c->graph) cudaGraphDestroy(c->graph);
+    c->graph_exec = nullptr;
+    c->graph = nullptr;
+    c->graph_launches = 0;
+}
+
+// Capture the replay sequence (build_body with the recorded sizes and the
+// device checks in place of the readbacks) as a graph, on the context's own
+// stream; the graph is then launched on the caller's.
+static int capture_replay(ac_ctx* c) {
+    cudaStream_t s = c->cap_stream;
+    AC_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    const long long l0 = g_launch_count;
+    c->replaying = true;
+    g_no_alloc = true;
+    const int rc = build_body(c, s);
+    g_no_alloc = false;
+    c->replaying = false;
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(s, &g);
+    if (rc != AC_OK || e != cudaSuccess || !g) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        return rc != AC_OK ? rc : fail(AC_ERR_CUDA, "graph capture of the build failed");
+    }
+    cudaGraphExec_t ex = nullptr;
+    if (cudaGraphInstantiate(&ex, g, 0) != cudaSuccess) {
+        cudaGraphDestroy(g);
+        cudaGetLastError();
+        return fail(AC_ERR_CUDA, "graph instantiation failed");
+    }
+    c->graph = g;
+    c->graph_exec = ex;
+    c->graph_launches = g_launch_count - l0;
+    return AC_OK;
+}
+
+// Sizes of a successful synchronised build, for the replays.
+static int record_build(ac_ctx* c, const DevCounters& post, cudaStream_t s) {
+    ac::BuildRecord& r = c->rec;
+    r.opt = c->opt;
+    r.wmax = (int)(c->pc.H2 - c->pc.A);
+    r.nb_total = c->nb_total;
+    r.n_wide = c->n_wide;
+    r.post = post;
+    r.post.err = 0;
+    r.n_pending = (int64_t)post.n_pending;
+    for (int d = 0; d < 4; d++) r.count[d] = c->K[d].count;
+    for (int d = 1; d < 4; d++) r.count[3 + d] = c->C[d].count;
+    const size_t nb = (size_t)c->n_mol * 6;
+    AC_TRY(c->rec_bbox.reserve((nb + 1) * sizeof(int32_t), s));
+    AC_CUDA(cudaMemcpyAsync(c->rec_bbox.p, c->scratch[0].p, nb * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+    AC_CUDA(cudaMemcpyAsync(c->rec_bbox.as<int32_t>() + nb, c->scratch[1].p, sizeof(int32_t), cudaMemcpyDeviceToDevice,
+                            s));
+    AC_TRY(sync_host(c, s));  // the copies finish before a replay on another stream reads them
+    r.valid = true;
+    return AC_OK;
 }
 
 extern "C" int ac_build(ac_ctx* c, void* stream) {
@@ -495,38 +631,52 @@ extern "C" int ac_build(ac_ctx* c, void* stream) {
     cudaStream_t s = (cudaStream_t)stream;
     StreamScope scope(s);
     c->built = false;
+    c->host_syncs = 0;
     const long long launches0 = g_launch_count;
-    AC_CUDA(cudaEventRecord(c->ev[0], s));
-    AC_TRY(quantise_and_plan(c, s));
-    AC_TRY(build_grid(c, s));
-    AC_CUDA(cudaEventRecord(c->ev[1], s));
-    AC_TRY(build_neighbours(c, s));
-    AC_CUDA(cudaEventRecord(c->ev[2], s));
-    AC_TRY(run_local(c, s));
-    AC_CUDA(cudaEventRecord(c->ev[3], s));
-    AC_TRY(canonicalise(c, s));
-    AC_CUDA(cudaEventRecord(c->ev[6], s));
-    AC_TRY(compute_filtration(c, s));
-    AC_CUDA(cudaEventRecord(c->ev[7], s));
-    AC_CUDA(cudaEventSynchronize(c->ev[7]));
+    bool replayed = false;
     DevCounters h;
-    AC_TRY(read_counters(c, &h, s));
+    if (c->rec.valid && !c->opt.no_graph && same_plan(c->rec.opt, c->opt)) {
+        if (!c->graph_exec && capture_replay(c) != AC_OK) {
+            drop_graph(c);
+            c->rec.valid = false;
+        }
+        if (c->graph_exec) {
+            AC_CUDA(cudaGraphLaunch(c->graph_exec, s));
+            AC_TRY(read_counters(c, &h, s));
+            if (h.err & DERR_REPLAY) {
+                // a size moved: forget the graph and build with readbacks
+                drop_graph(c);
+                c->rec.valid = false;
+                unsigned zero = 0;
+                AC_CUDA(cudaMemcpy(&c->counters.as<DevCounters>()->err, &zero, sizeof(zero), cudaMemcpyHostToDevice));
+            } else {
+                replayed = true;
+            }
+        }
+    }
+    if (!replayed) {
+        drop_graph(c);
+        AC_TRY(build_body(c, s));
+        AC_TRY(read_counters(c, &h, s));
+    }
     if (h.err & DERR_INTERNAL) return fail(AC_ERR_CUDA, "internal: attached simplex without a coface in the complex");
+    if (!replayed && !c->opt.no_graph) AC_TRY(record_build(c, h, s));
     finish_mol_rows(c);
+    const DevCounters& hl = h;  // the per-atom pass wrote them; later stages add only error bits
     ac_stats& st = c->stats;
     st.n_atoms = c->n;
     st.candidates[0] = 0;
-    for (int d = 1; d < 4; d++) st.candidates[d] = (int64_t)h.n_cand[d];
+    for (int d = 1; d < 4; d++) st.candidates[d] = (int64_t)hl.n_cand[d];
     for (int d = 0; d < 4; d++) st.simplices[d] = c->K[d].count;
     st.neighbour_pairs = c->nb_total;
-    st.max_degree = h.max_degree;
+    st.max_degree = hl.max_degree;
     for (int k = 0; k < 3; k++) {
-        st.ac2_tests_tet[k] = (int64_t)h.ac2_tet[k];
-        st.ac2_tests_tri[k] = (int64_t)h.ac2_tri[k];
+        st.ac2_tests_tet[k] = (int64_t)hl.ac2_tet[k];
+        st.ac2_tests_tri[k] = (int64_t)hl.ac2_tri[k];
     }
-    st.ac2_tests_edge = (int64_t)h.ac2_edge;
-    for (int d = 0; d < 4; d++) st.ac3_tests[d] = (int64_t)h.ac3[d];
-    st.ac3_exact = (int64_t)h.ac3_exact;
+    st.ac2_tests_edge = (int64_t)hl.ac2_edge;
+    for (int d = 0; d < 4; d++) st.ac3_tests[d] = (int64_t)hl.ac3[d];
+    st.ac3_exact = (int64_t)hl.ac3_exact;
     st.ms_stage[0] = elapsed(c->ev[0], c->ev[1]);
     st.ms_stage[1] = elapsed(c->ev[1], c->ev[2]);
     st.ms_stage[2] = elapsed(c->ev[2], c->ev[3]);
@@ -534,9 +684,11 @@ extern "C" int ac_build(ac_ctx* c, void* stream) {
     st.ms_stage[4] = elapsed(c->ev[4], c->ev[5]);
     st.ms_stage[5] = elapsed(c->ev[5], c->ev[6]);
     st.ms_stage[6] = elapsed(c->ev[6], c->ev[7]);
-    st.ms_stage[7] = c->n > 0 ? elapsed(c->ev[8], c->ev[9]) : 0.0;  // last launch of the per-atom kernel
+    st.ms_stage[7] = c->n > 0 ? elapsed(c->ev[8], c->ev[9]) : 0.0;  // the per-atom kernels
     st.ms_total = elapsed(c->ev[0], c->ev[7]);
-    st.kernel_launches = g_launch_count - launches0;
+    st.kernel_launches = replayed ? c->graph_launches : g_launch_count - launches0;
+    st.replayed = replayed ? 1 : 0;
+    st.host_syncs = c->host_syncs;
     c->built = true;
     return AC_OK;
 }
@@ -657,12 +809,14 @@ extern "C" void ac_destroy(ac_ctx* c) {
     // the context's buffers go back to the pool once no work can still use them
     cudaDeviceSynchronize();
     StreamScope scope(nullptr);
+    drop_graph(c);
     for (int k = 0; k < 10; k++)
         if (c->ev[k]) cudaEventDestroy(c->ev[k]);
     if (c->h_pinned) cudaFreeHost(c->h_pinned);
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
     if (c->ev_join) cudaEventDestroy(c->ev_join);
     if (c->side) cudaStreamDestroy(c->side);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     delete c;
 }
 

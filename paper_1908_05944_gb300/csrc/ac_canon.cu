@@ -381,9 +381,7 @@ __global__ void k_canon_write(CanonWriteArgs a) {
 // ---------------------------------------------------------------------------
 // canonicalise one dimension
 
-struct Work {
-    DevBuf T, cnt, cursor, uniq, big;
-};
+using Work = CanonWork;
 
 template <int K>
 static int canon_dim_k(ac_ctx* c, const int4* a4, const int2* a2, int64_t nA, const int4* cof, int64_t nB,
@@ -428,9 +426,14 @@ static int canon_dim_k(ac_ctx* c, const int4* a4, const int2* a2, int64_t nA, co
     }
     int64_t* uoff = L.v0_off.as<int64_t>();
     AC_TRY(scan_exclusive_i64(uniq, uoff, n, c->scan_tmp, s));
-    AC_CUDA(cudaMemcpyAsync(c->h_stage, uoff + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-    AC_CUDA(cudaStreamSynchronize(s));
-    const int64_t count = c->h_stage[0];
+    int64_t count = L.count;  // a replay keeps the recorded build's count and checks it
+    if (c->replaying) {
+        AC_TRY(expect_i64(c, uoff + n, count, s));
+    } else {
+        AC_CUDA(cudaMemcpyAsync(c->h_stage, uoff + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        AC_TRY(sync_host(c, s));
+        count = c->h_stage[0];
+    }
     L.count = count;
     const size_t rows = (size_t)(count > 0 ? count : 1);
     AC_TRY(L.tuples.reserve(rows * K * sizeof(int32_t), s));
@@ -507,15 +510,15 @@ int canonicalise(ac_ctx* c, cudaStream_t s) {
     const DevCounters& h = c->hc;  // counters read at the end of the per-atom pass
     if (h.err & (DERR_OVF_TET | DERR_OVF_TRI | DERR_OVF_EDGE | DERR_OVF_CAND))
         return fail(AC_ERR_CAPACITY, "per-atom output overflow");
-    Work w;
+    Work& w = c->cw;
     const int64_t n = c->n;
     // K^3
     AC_TRY(canon_dim(c, 3, c->tet_out.as<int4>(), nullptr, (int64_t)h.n_tet_out, nullptr, 0, c->K[3], c->Gbuf[3], w, s));
-    AC_CUDA(cudaEventRecord(c->ev[4], s));
+    AC_TRY(stage_mark(c, 4, s));
     // K^2 = unattached triangles + facets of K^3
     AC_TRY(canon_dim(c, 2, c->tri_pass.as<int4>(), nullptr, (int64_t)h.n_tri_pass, c->Gbuf[3].as<int4>(), c->K[3].count,
                      c->K[2], c->Gbuf[2], w, s));
-    AC_CUDA(cudaEventRecord(c->ev[5], s));
+    AC_TRY(stage_mark(c, 5, s));
     // K^1 = unattached edges + edges of K^2
     AC_TRY(canon_dim(c, 1, nullptr, c->edge_pass.as<int2>(), (int64_t)h.n_edge_pass, c->Gbuf[2].as<int4>(),
                      c->K[2].count, c->K[1], c->Gbuf[1], w, s));
@@ -541,9 +544,14 @@ int canonicalise(ac_ctx* c, cudaStream_t s) {
         }
         int64_t* voff = L.v0_off.as<int64_t>();
         AC_TRY(scan_exclusive_i64(inK, voff, n, c->scan_tmp, s));
-        AC_CUDA(cudaMemcpyAsync(c->h_stage, voff + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-        AC_CUDA(cudaStreamSynchronize(s));
-        const int64_t count = c->h_stage[0];
+        int64_t count = L.count;
+        if (c->replaying) {
+            AC_TRY(expect_i64(c, voff + n, count, s));
+        } else {
+            AC_CUDA(cudaMemcpyAsync(c->h_stage, voff + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+            AC_TRY(sync_host(c, s));
+            count = c->h_stage[0];
+        }
         L.count = count;
         size_t rows = (size_t)(count > 0 ? count : 1);
         AC_TRY(L.tuples.reserve(rows * sizeof(int32_t), s));
@@ -689,10 +697,12 @@ __device__ __forceinline__ int64_t find_row(const int4* __restrict__ L, const in
     return -1;
 }
 
-// pass 1: smallest coface value of every attached face
+// pass 1: smallest coface value of every attached face; the row of each
+// (coface, facet) that is an attached face is kept for pass 2 (-1 otherwise)
 __global__ void k_coface_min(const int4* __restrict__ Cof, const double* __restrict__ fc, int64_t mc, int Kc,
                              const int4* __restrict__ L, const int64_t* __restrict__ v0_off,
-                             const uint8_t* __restrict__ attached, unsigned long long* __restrict__ fkey) {
+                             const uint8_t* __restrict__ attached, unsigned long long* __restrict__ fkey,
+                             int64_t* __restrict__ rows) {
     int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= mc) return;
     int4 t = Cof[j];
@@ -700,23 +710,21 @@ __global__ void k_coface_min(const int4* __restrict__ Cof, const double* __restr
     for (int drop = 0; drop < Kc; drop++) {
         int4 face = facet_of(t, Kc - 1, drop);
         int64_t r = find_row(L, v0_off, face);
-        if (r >= 0 && attached[r]) atomicMin(&fkey[r], key);
+        const bool hit = r >= 0 && attached[r];
+        rows[j * Kc + drop] = hit ? r : -1;
+        if (hit) atomicMin(&fkey[r], key);
     }
 }
 
 // pass 2: among cofaces attaining the minimum, the first in lexicographic order
-__global__ void k_coface_arg(const int4* __restrict__ Cof, const double* __restrict__ fc, int64_t mc, int Kc,
-                             const int4* __restrict__ L, const int64_t* __restrict__ v0_off,
-                             const uint8_t* __restrict__ attached, const unsigned long long* __restrict__ fkey,
-                             unsigned long long* __restrict__ arg) {
+__global__ void k_coface_arg(const double* __restrict__ fc, int64_t mc, int Kc, const int64_t* __restrict__ rows,
+                             const unsigned long long* __restrict__ fkey, unsigned long long* __restrict__ arg) {
     int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= mc) return;
-    int4 t = Cof[j];
     unsigned long long key = order_key(fc[j]);
     for (int drop = 0; drop < Kc; drop++) {
-        int4 face = facet_of(t, Kc - 1, drop);
-        int64_t r = find_row(L, v0_off, face);
-        if (r >= 0 && attached[r] && fkey[r] == key) atomicMin(&arg[r], (unsigned long long)j);
+        const int64_t r = rows[j * Kc + drop];
+        if (r >= 0 && fkey[r] == key) atomicMin(&arg[r], (unsigned long long)j);
     }
 }
 
@@ -757,12 +765,13 @@ int compute_filtration(ac_ctx* c, cudaStream_t s) {
         AC_CUDA(cudaMemsetAsync(argb.p, 0xff, (size_t)m * sizeof(unsigned long long), s));
         if (U.count > 0) {
             const unsigned nbk = (unsigned)((U.count + 127) / 128);
+            DevBuf& rowb = c->scratch[4];
+            AC_TRY(rowb.reserve((size_t)U.count * (d + 2) * sizeof(int64_t), s));
             k_coface_min<<<nbk, 128, 0, s>>>(c->Gbuf[d + 1].as<int4>(), U.f.as<double>(), U.count, d + 2,
                                              c->Gbuf[d].as<int4>(), L.v0_off.as<int64_t>(), L.attached.as<uint8_t>(),
-                                             keyb.as<unsigned long long>());
+                                             keyb.as<unsigned long long>(), rowb.as<int64_t>());
             AC_LAUNCHED();
-            k_coface_arg<<<nbk, 128, 0, s>>>(c->Gbuf[d + 1].as<int4>(), U.f.as<double>(), U.count, d + 2,
-                                             c->Gbuf[d].as<int4>(), L.v0_off.as<int64_t>(), L.attached.as<uint8_t>(),
+            k_coface_arg<<<nbk, 128, 0, s>>>(U.f.as<double>(), U.count, d + 2, rowb.as<int64_t>(),
                                              keyb.as<unsigned long long>(), argb.as<unsigned long long>());
             AC_LAUNCHED();
         }

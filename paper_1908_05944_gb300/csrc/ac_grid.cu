@@ -107,7 +107,9 @@ __device__ __forceinline__ bool grown_meet(int64_t D, int64_t si, int64_t sx) {
     return t <= 0 || t * t <= 4 * si * sx;
 }
 
-template <bool FILL>
+// GUARD: the stencil may span 2^29 quanta or more (very coarse cells), so a
+// pair's coordinate differences are bounded before the 64-bit squares.
+template <bool FILL, bool GUARD>
 __global__ void k_neighbours(const int4* __restrict__ Ps, const int32_t* __restrict__ mol_s,
                              const MolGrid* __restrict__ grids, const uint32_t* __restrict__ cell_start,
                              PredConst pc, int64_t n, int64_t* __restrict__ nb_cnt, const int64_t* __restrict__ nb_off,
@@ -131,12 +133,25 @@ __global__ void k_neighbours(const int4* __restrict__ Ps, const int32_t* __restr
                 for (uint32_t t = a; t < b; t++) {
                     if (t == (uint32_t)s) continue;
                     int4 o = Ps[t];
-                    int64_t dx = o.x - p.x, dy = o.y - p.y, dz = o.z - p.z;
-                    int64_t D = dx * dx + dy * dy + dz * dz;
-                    if (D == 0) {
+                    int64_t dx, dy, dz;
+                    if (GUARD) {
+                        dx = (int64_t)o.x - p.x;
+                        dy = (int64_t)o.y - p.y;
+                        dz = (int64_t)o.z - p.z;
+                        // grown balls meet only within 2h <= 2^13 quanta per axis
+                        const int64_t lim = 1 << 20;
+                        if (dx >= lim || dx <= -lim || dy >= lim || dy <= -lim || dz >= lim || dz <= -lim) continue;
+                    } else {
+                        // the stencil spans less than 2^29 quanta: 32-bit differences, squares below 2^58
+                        dx = o.x - p.x;
+                        dy = o.y - p.y;
+                        dz = o.z - p.z;
+                    }
+                    if (dx == 0 && dy == 0 && dz == 0) {
                         atomicOr(&cnt->err, DERR_COINCIDENT);
                         continue;
                     }
+                    int64_t D = dx * dx + dy * dy + dz * dz;
                     int64_t sx = (int64_t)o.w + pc.A;
                     if (sx < 0 || !grown_meet(D, si, sx)) continue;
                     if (FILL) nb[w + count] = (int32_t)t;
@@ -208,7 +223,10 @@ int build_neighbours(ac_ctx* c, cudaStream_t s) {
     }
     const unsigned nb = (unsigned)((n + 127) / 128);
     DevCounters* dc = c->counters.as<DevCounters>();
-    k_neighbours<false><<<nb, 128, 0, s>>>(c->Ps.as<int4>(), c->mol_s.as<int32_t>(), c->grids.as<MolGrid>(),
+    const bool guard = (int64_t)c->pc.cell * (2 * c->pc.reach + 1) >= ((int64_t)1 << 29);
+    auto k_count = guard ? k_neighbours<false, true> : k_neighbours<false, false>;
+    auto k_fill = guard ? k_neighbours<true, true> : k_neighbours<true, false>;
+    k_count<<<nb, 128, 0, s>>>(c->Ps.as<int4>(), c->mol_s.as<int32_t>(), c->grids.as<MolGrid>(),
                                            c->cell_start.as<uint32_t>(), c->pc, n, cntp, nullptr, nullptr, dc);
     AC_LAUNCHED();
     // work order from the counts (before the in-place scan turns them into offsets)
@@ -225,16 +243,26 @@ int build_neighbours(ac_ctx* c, cudaStream_t s) {
     k_deg_scatter<<<nb, 128, 0, s>>>(cntp, n, cursor, c->work.as<int32_t>());
     AC_LAUNCHED();
     AC_TRY(scan_exclusive_i64(cntp, cntp, n, c->scan_tmp, s));
-    AC_CUDA(cudaMemcpyAsync(c->h_stage, cntp + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-    AC_CUDA(cudaMemcpyAsync(c->h_stage + 1, n_wide, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-    DevCounters h;
-    AC_TRY(read_counters(c, &h, s));  // also completes the copies above
-    const int64_t total = c->h_stage[0];
-    c->n_wide = c->h_stage[1];
-    if (h.err & DERR_COINCIDENT) return fail(AC_ERR_DEGENERATE, "two centres coincide after quantisation to 1/1024 A");
+    int64_t total = 0;
+    if (c->replaying) {
+        // sizes of the recorded build, checked on the device
+        total = c->rec.nb_total;
+        c->n_wide = c->rec.n_wide;
+        AC_TRY(expect_i64(c, cntp + n, total, s));
+        AC_TRY(expect_i64(c, reinterpret_cast<const int64_t*>(n_wide), c->n_wide, s));
+    } else {
+        AC_CUDA(cudaMemcpyAsync(c->h_stage, cntp + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        AC_CUDA(cudaMemcpyAsync(c->h_stage + 1, n_wide, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        DevCounters h;
+        AC_TRY(read_counters(c, &h, s));  // also completes the copies above
+        total = c->h_stage[0];
+        c->n_wide = c->h_stage[1];
+        if (h.err & DERR_COINCIDENT)
+            return fail(AC_ERR_DEGENERATE, "two centres coincide after quantisation to 1/1024 A");
+    }
     c->nb_total = total;
     AC_TRY(c->nb.reserve((size_t)(total > 0 ? total : 1) * sizeof(int32_t), s));
-    k_neighbours<true><<<nb, 128, 0, s>>>(c->Ps.as<int4>(), c->mol_s.as<int32_t>(), c->grids.as<MolGrid>(),
+    k_fill<<<nb, 128, 0, s>>>(c->Ps.as<int4>(), c->mol_s.as<int32_t>(), c->grids.as<MolGrid>(),
                                           c->cell_start.as<uint32_t>(), c->pc, n, nullptr, cntp, c->nb.as<int32_t>(), dc);
     AC_LAUNCHED();
     return AC_OK;

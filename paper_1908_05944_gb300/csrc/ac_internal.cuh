@@ -54,6 +54,7 @@ enum : uint32_t {
     DERR_DEGREE = 1u << 7,       // neighbour count above the kernel's mask width
     DERR_INTERNAL = 1u << 8,     // an invariant of the method failed (a bug)
     DERR_OVF_PEND = 1u << 9,     // pending (escalated) list full
+    DERR_REPLAY = 1u << 10,      // a size differs from the one recorded for the graph replay
 };
 
 // ---------------------------------------------------------------------------
@@ -147,6 +148,24 @@ struct SimplexList {
 
 }  // namespace ac
 
+namespace ac {
+// Scratch of the canonicalisation, kept by the context so rebuilds allocate nothing.
+struct CanonWork {
+    DevBuf T, cnt, cursor, uniq, big;
+};
+
+// Sizes a synchronised build read back; later builds replay with these.
+struct BuildRecord {
+    bool valid = false;
+    ac_options opt{};
+    int wmax = 0;
+    int64_t nb_total = 0, n_wide = 0;
+    int64_t n_pending = 0;  // escalated simplices before the resolve kernel
+    DevCounters post{};     // counters after the resolve kernel
+    int64_t count[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // K^0..K^3 rows, then Sigma^1..Sigma^3 rows
+};
+}  // namespace ac
+
 struct ac_ctx {
     int64_t n = 0;
     int64_t n_mol = 1;
@@ -209,6 +228,17 @@ struct ac_ctx {
     int32_t* h_bbox = nullptr;        // 6 x n_mol bounding boxes
     int64_t* h_molrows = nullptr;     // 7 x (n_mol + 1) per-molecule first rows
 
+    // graph replay of later builds
+    bool replaying = false;       // set while the replay sequence is being captured
+    ac::BuildRecord rec;
+    ac::DevBuf rec_bbox;          // int32 6 x n_mol: bounding boxes of the recorded build
+    cudaStream_t cap_stream = nullptr;  // private stream the replay is captured on (never the legacy stream)
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t graph_exec = nullptr;
+    long long graph_launches = 0; // kernels in the graph
+    int host_syncs = 0;           // host waits in the current build
+    ac::CanonWork cw;
+
     ac_stats stats{};
     cudaEvent_t ev[10] = {};  // stage boundaries; ev[8], ev[9] bracket the per-atom kernel
     cudaStream_t side = nullptr;                    // wide-row launch, concurrent with the narrow one
@@ -233,6 +263,14 @@ int backward(ac_ctx* c, const double* const dldf[4], double* dc, double* dr, cud
 int backward_noalloc(ac_ctx* c, const double* const dldf[4], double* dc, double* dr, cudaStream_t s);
 
 int read_counters(ac_ctx* c, DevCounters* h, cudaStream_t s);
+// Replay checks: set DERR_REPLAY in the counters when a device value differs
+// from the recorded one.
+int expect_i64(ac_ctx* c, const int64_t* d_value, int64_t want, cudaStream_t s);
+int expect_u64(ac_ctx* c, const unsigned long long* d_value, unsigned long long want, cudaStream_t s);
+int sync_host(ac_ctx* c, cudaStream_t s);  // cudaStreamSynchronize, counted in the build's stats
+// Record stage event k; under graph capture as an external event node, so the
+// replayed graph records it too.
+int stage_mark(ac_ctx* c, int k, cudaStream_t s);
 void finish_mol_rows(ac_ctx* c);
 
 // device helpers -------------------------------------------------------------

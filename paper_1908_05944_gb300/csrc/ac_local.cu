@@ -76,6 +76,7 @@ constexpr unsigned FULL = 0xffffffffu;
 constexpr int STAGE = 32;
 constexpr int PAIR_CHUNK = 128;
 constexpr int CAND_CAP = 256;  // triangle or tetrahedron candidates written out per batch
+constexpr int PL_CAP = 256;    // Sigma^2 pairs listed during the triangle phase
 
 template <int WORDS>
 struct WarpSmem {
@@ -95,7 +96,8 @@ struct WarpSmem {
     int n_tet, n_tri, n_edge;
     int rowpre[M + 1];                // prefix sums of candidate counts per row of up
     int pairpre[PAIR_CHUNK + 1];      // prefix sums of tetrahedron candidates per Sigma^2 pair
-    unsigned short pairs[PAIR_CHUNK]; // Sigma^2 pairs (p | k << 8) of the current chunk
+    unsigned short plist[PL_CAP];     // Sigma^2 pairs (p | k << 8) in enumeration order
+    int n_pl;                         // pairs found (the list holds them while n_pl <= PL_CAP)
     unsigned cand[CAND_CAP];          // candidate codes (p | k << 8 [| l << 16]) of the current batch
     int4 st_tet[STAGE];
     int4 st_tri[STAGE];
@@ -659,6 +661,8 @@ __global__ void __launch_bounds__(256, 4) k_local(LocalArgs A) {
         }
         __syncwarp();
 
+        if (lane == 0) S.n_pl = 0;
+        __syncwarp();
         // ---- phase C: triangles (i,p,k): AC3, then AC2 at the orthocentre -----
         // Candidates of row r (p = uplist[r]): k in M[p] & up, k > p. Rows are
         // taken 32 at a time, one per lane; each writes its candidates as codes
@@ -696,26 +700,42 @@ __global__ void __launch_bounds__(256, 4) k_local(LocalArgs A) {
                     bool pass = false, pend = false, keep_it = false;
                     int pend_ac3 = 0;
                     int pp = 0, kk = 0;
+                    Ortho<R> o;
+                    o.ac3 = -1;
                     if (valid) {
                         const unsigned code = S.cand[j];
                         pp = code & 255u;
                         kk = code >> 8;
                         n_ac3t++;
-                        const Ortho<R> o = ortho_tri<R>(point<R>(S, pp), point<R>(S, kk), T, B);
+                        o = ortho_tri<R>(point<R>(S, pp), point<R>(S, kk), T, B);
                         if (o.ac3 >= 0) {
                             // potential, or not yet excluded: tetrahedra may build on it
                             atomicOr(&S.Trow[pp][kk >> 5], 1u << (kk & 31));
                             if (o.ac3 > 0) {
                                 n_s2++;
                                 keep_it = true;
-                                const int r2 = ac2_scan<R>(S, nw, o, B, 2, pp, kk, 0, n_tri);
-                                pass = r2 > 0;
-                                pend = r2 == 0;
                             } else {
                                 pend = true;
                                 pend_ac3 = 1;
                             }
                         }
+                    }
+                    {
+                        const int r2 = keep_it ? ac2_scan<R>(S, nw, o, B, 2, pp, kk, 0, n_tri) : 1;
+                        if (keep_it) {
+                            pass = r2 > 0;
+                            pend = r2 == 0;
+                        }
+                    }
+                    {
+                        // list the pair for the tetrahedron phase (the triangle is potential or undecided)
+                        const bool tp = valid && (keep_it || pend_ac3);
+                        const unsigned bt = __ballot_sync(FULL, tp);
+                        const int slot = S.n_pl + __popc(bt & lanemask_lt());
+                        if (tp && slot < PL_CAP) S.plist[slot] = (unsigned short)(pp | (kk << 8));
+                        __syncwarp();
+                        if (lane == 0) S.n_pl += __popc(bt);
+                        __syncwarp();
                     }
                     const int4 item = make_int4(i, valid ? S.idx[pp] : 0, valid ? S.idx[kk] : 0, 0);
                     if (keep)
@@ -732,11 +752,15 @@ __global__ void __launch_bounds__(256, 4) k_local(LocalArgs A) {
         __syncwarp();
 
         // ---- phase D: tetrahedra (i,p,k,l): AC3, then AC2 ----------------------
-        // Sigma^2 pairs (p,k): row r of up holds popc(T[p]) of them; pairs are taken
-        // PAIR_CHUNK at a time with a prefix over their candidate counts popc(T[p] & T[k]);
-        // their candidates l are written as codes p | k << 8 | l << 16 to cand[]
-        // (CAND_CAP per batch) and read back by windows of 32.
-        {
+        // Sigma^2 pairs (p,k) come from the list the triangle phase wrote (or,
+        // when it overflowed, from the T rows: row r of up holds popc(T[p]) of
+        // them, located by a prefix and a binary search). Pairs are taken
+        // PAIR_CHUNK at a time with a prefix over their candidate counts
+        // popc(T[p] & T[k]); their candidates l are written as codes
+        // p | k << 8 | l << 16 to cand[] (CAND_CAP per batch) and read back by
+        // windows of 32.
+        const bool use_list = S.n_pl <= PL_CAP;
+        if (!use_list) {
             int run = 0;
             for (int r0 = 0; r0 < n_up; r0 += 32) {
                 int c = 0;
@@ -752,7 +776,7 @@ __global__ void __launch_bounds__(256, 4) k_local(LocalArgs A) {
             if (lane == 0) S.rowpre[n_up] = run;
         }
         __syncwarp();
-        const int n_pairs = S.rowpre[n_up];
+        const int n_pairs = use_list ? S.n_pl : S.rowpre[n_up];
 #pragma unroll 1
         for (int c0 = 0; c0 < n_pairs; c0 += PAIR_CHUNK) {
             const int cn = min(PAIR_CHUNK, n_pairs - c0);
@@ -762,10 +786,18 @@ __global__ void __launch_bounds__(256, 4) k_local(LocalArgs A) {
                     int c = 0;
                     if (q0 + lane < cn) {
                         const int j = c0 + q0 + lane;
-                        const int r = row_of(S.rowpre, n_up, j);
-                        const int p = S.uplist[r];
-                        const int k = nth_in_words(nw, j - S.rowpre[r], [&](int w) { return S.Trow[p][w]; });
-                        S.pairs[q0 + lane] = (unsigned short)(p | (k << 8));
+                        int p, k;
+                        if (use_list) {
+                            const unsigned code = S.plist[j];
+                            p = code & 255u;
+                            k = code >> 8;
+                        } else {
+                            // the list is not used: its first PAIR_CHUNK slots hold this chunk
+                            const int r = row_of(S.rowpre, n_up, j);
+                            p = S.uplist[r];
+                            k = nth_in_words(nw, j - S.rowpre[r], [&](int w) { return S.Trow[p][w]; });
+                            S.plist[q0 + lane] = (unsigned short)(p | (k << 8));
+                        }
                         for (int w = 0; w < nw; w++) c += __popc(S.Trow[p][w] & S.Trow[k][w]);
                     }
                     int tot;
@@ -782,7 +814,7 @@ __global__ void __launch_bounds__(256, 4) k_local(LocalArgs A) {
                 for (int q = lane; q < cn; q += 32) {
                     const int a0 = S.pairpre[q], a1 = S.pairpre[q + 1];
                     if (a1 <= done || a0 >= done + CAND_CAP) continue;
-                    const unsigned code = S.pairs[q];
+                    const unsigned code = S.plist[(use_list ? c0 : 0) + q];
                     const int p = code & 255u, k = code >> 8;
                     int t = a0;
                     for (int w = 0; w < nw; w++) {
@@ -804,22 +836,28 @@ __global__ void __launch_bounds__(256, 4) k_local(LocalArgs A) {
                     bool pass = false, pend = false, keep_it = false;
                     int pend_ac3 = 0;
                     int p3 = 0, k3 = 0, ll = 0;
+                    Ortho<R> o;
+                    o.ac3 = -1;
                     if (valid) {
                         const unsigned code = S.cand[j];
                         p3 = code & 255u;
                         k3 = (code >> 8) & 255u;
                         ll = code >> 16;
                         n_ac3k++;
-                        const Ortho<R> o = ortho_tet<R>(point<R>(S, p3), point<R>(S, k3), point<R>(S, ll), T, B);
+                        o = ortho_tet<R>(point<R>(S, p3), point<R>(S, k3), point<R>(S, ll), T, B);
                         if (o.ac3 > 0) {
                             n_s3++;
                             keep_it = true;
-                            const int r3 = ac2_scan<R>(S, nw, o, B, 3, p3, k3, ll, n_tet);
-                            pass = r3 > 0;
-                            pend = r3 == 0;
                         } else if (o.ac3 == 0) {
                             pend = true;
                             pend_ac3 = 1;
+                        }
+                    }
+                    {
+                        const int r3 = keep_it ? ac2_scan<R>(S, nw, o, B, 3, p3, k3, ll, n_tet) : 1;
+                        if (keep_it) {
+                            pass = r3 > 0;
+                            pend = r3 == 0;
                         }
                     }
                     const int4 item =
@@ -841,11 +879,15 @@ __global__ void __launch_bounds__(256, 4) k_local(LocalArgs A) {
             const bool ok = r0 + lane < n_up;
             const int p = ok ? S.uplist[r0 + lane] : 0;
             bool pass = false, pend = false;
-            if (ok) {
-                const Ortho<R> o = ortho_edge<R>(point<R>(S, p), B);
-                const int r1 = ac2_scan<R>(S, nw, o, B, 1, p, 0, 0, n_edge);
-                pass = r1 > 0;
-                pend = r1 == 0;
+            Ortho<R> o;
+            o.ac3 = -1;
+            if (ok) o = ortho_edge<R>(point<R>(S, p), B);
+            {
+                const int r1 = ok ? ac2_scan<R>(S, nw, o, B, 1, p, 0, 0, n_edge) : 1;
+                if (ok) {
+                    pass = r1 > 0;
+                    pend = r1 == 0;
+                }
             }
             const int idp = ok ? S.idx[p] : 0;
             append_direct(pend, make_int4(i, idp, -1, -1), A.pending, &cnt->n_pending, A.cap_pending, &cnt->err,
@@ -1115,7 +1157,7 @@ static int launch_words(ac_ctx* c, int words, const LocalArgs& a, int warps, cud
 // resident warps) over the rest; the wide launch is small and starts first.
 template <class R>
 static int launch_pass(ac_ctx* c, int words, LocalArgs& a, cudaStream_t s) {
-    AC_CUDA(cudaEventRecord(c->ev[8], s));
+    AC_TRY(stage_mark(c, 8, s));
     const int32_t* work = c->work.as<int32_t>();
     const int64_t n_wide = words > 2 ? c->n_wide : 0;
     if (n_wide > 0) {
@@ -1134,7 +1176,7 @@ static int launch_pass(ac_ctx* c, int words, LocalArgs& a, cudaStream_t s) {
     narrow.counter2 = 0;
     if (narrow.n > 0) AC_TRY(launch_words<R>(c, n_wide > 0 ? 2 : words, narrow, 0, s));
     if (n_wide > 0) AC_CUDA(cudaStreamWaitEvent(s, c->ev_join, 0));
-    AC_CUDA(cudaEventRecord(c->ev[9], s));
+    AC_TRY(stage_mark(c, 9, s));
     return AC_OK;
 }
 
@@ -1184,7 +1226,7 @@ static void set_constants(const PredConst& pc, int64_t wmax, LocalArgs& a) {
 
 int run_local(ac_ctx* c, cudaStream_t s) {
     const int64_t n = c->n;
-    DevCounters h = c->hc;  // read after the neighbour count pass
+    DevCounters h = c->replaying ? c->rec.post : c->hc;  // read after the neighbour count pass
     const int maxdeg = h.max_degree;
     int words = maxdeg <= 32 ? 1 : maxdeg <= 64 ? 2 : maxdeg <= 128 ? 4 : maxdeg <= 256 ? 8 : 0;
     if (words == 0) {
@@ -1249,6 +1291,21 @@ int run_local(ac_ctx* c, cudaStream_t s) {
             const int rc = c->pc.precision == AC_PRECISION_FILTERED ? launch_pass<float>(c, words, a, s)
                                                                     : launch_pass<double>(c, words, a, s);
             if (rc) return rc;
+        }
+        if (c->replaying) {
+            // the recorded build's counts, checked on the device
+            const BuildRecord& r = c->rec;
+            AC_TRY(expect_u64(c, &dc->n_pending, (unsigned long long)r.n_pending, s));
+            if (r.n_pending > 0) {
+                k_resolve<<<(unsigned)((r.n_pending + 127) / 128), 128, 0, s>>>(a, r.n_pending);
+                AC_LAUNCHED();
+            }
+            AC_TRY(expect_u64(c, &dc->n_tet_out, r.post.n_tet_out, s));
+            AC_TRY(expect_u64(c, &dc->n_tri_pass, r.post.n_tri_pass, s));
+            AC_TRY(expect_u64(c, &dc->n_edge_pass, r.post.n_edge_pass, s));
+            for (int d = 1; d < 4; d++) AC_TRY(expect_u64(c, &dc->n_cand_out[d], r.post.n_cand_out[d], s));
+            c->hc = r.post;
+            return AC_OK;
         }
         AC_TRY(read_counters(c, &h, s));
         if (h.err & DERR_DEGREE) return fail(AC_ERR_CAPACITY, "neighbour list wider than the kernel's masks");
