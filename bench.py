@@ -283,8 +283,11 @@ def run_forms(args):
         ms = time_builds(cx, steps, warm, stream, flush)
         st = cx.stats()
         n = len(r_np)
+        loc = st["ms_stage"][7]
+        tf = algorithmic_flops(st) / (loc * 1e-3) / 1e12 if loc > 0 else 0.0
         out[f"{wl}/{prec}"] = {"atoms_per_s": n * steps / (sum(ms) / 1e3), "ms_per_step": sum(ms) / steps,
-                               "simplices": st["simplices"], "local_kernel_ms": st["ms_stage"][7]}
+                               "simplices": st["simplices"], "local_kernel_ms": loc, "local_tflops": tf,
+                               "local_frac_fp32_peak_2070mhz": tf / (SMS * FP32_LANES_PER_SM * 2 * 2070e6 / 1e12)}
         cx.close()
         del cx
     # batch: one context over all molecules vs one context per molecule
@@ -295,12 +298,15 @@ def run_forms(args):
     r_all = torch.from_numpy(np.concatenate([m[1] for m in mols])).cuda()
     n_all = int(offsets[-1])
     bx = ac.AlphaComplex(c_all, r_all, 0.0, offsets=offsets)
+    tuned = bx.autotune(stream)
     ms = time_builds(bx, steps, warm, stream, flush)
     batched = n_all * steps / (sum(ms) / 1e3)
+    replayed = bx.stats()["replayed"]
     bx.close()
     del bx
-    singles = [ac.AlphaComplex(c_all[offsets[m]:offsets[m + 1]], r_all[offsets[m]:offsets[m + 1]], 0.0)
-               for m in range(len(mols))]
+    # the comparison: one context per molecule, every build synchronised (no graph)
+    singles = [ac.AlphaComplex(c_all[offsets[m]:offsets[m + 1]], r_all[offsets[m]:offsets[m + 1]], 0.0,
+                               ac.options(no_graph=True)) for m in range(len(mols))]
     for cx in singles:
         cx.build(stream)
     torch.cuda.synchronize()
@@ -315,7 +321,27 @@ def run_forms(args):
     for cx in singles:
         cx.close()
     out["batch1024_probe"] = {"n_atoms": n_all, "batched_atoms_per_s": batched, "batched_ms": sum(ms) / steps,
+                              "batched_graph_replay": bool(replayed), "autotuned": tuned,
                               "per_molecule_atoms_per_s": per_mol}
+    # backward (row a14) on the 20k globule: dL/dcentres, dL/dradii for random weights on every simplex
+    c20, r20 = workload("globule20k_probe")
+    gx = ac.AlphaComplex(torch.from_numpy(c20).cuda(), torch.from_numpy(r20).cuda(), 0.0).build(stream)
+    rng = np.random.default_rng(synth.LOSS_WEIGHT_SEED)
+    dldf = [torch.from_numpy(rng.standard_normal(gx.count(d))).cuda() for d in range(4)]
+    for _ in range(2):
+        gx.backward(dldf, stream)
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(5):
+        gx.backward(dldf, stream)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    bms = t0.elapsed_time(t1) / 5
+    out["globule20k_probe/backward"] = {"ms_per_call": bms, "atoms_per_s": len(r20) / (bms / 1e3),
+                                        "simplices": [gx.count(d) for d in range(4)]}
+    gx.close()
     return out
 
 
@@ -378,7 +404,34 @@ def cpu_baseline(args, sample_atoms=20000):
     dt = time.perf_counter() - t0
     return {"value": len(sub_r) / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
             "sample": f"{len(sub_r)}-atom sub-ball of {args.workload} around its centre, 1 run, {dt:.2f} s",
-            "simplices": int(sum(res.counts()))}
+            "simplices": int(sum(res.counts())), "parity": parity_on(sub_c, sub_r, res)}
+
+
+def parity_on(c, r, ref):
+    """The GPU complex of the same atoms against the oracle's: lists (bit-exact) and Size values."""
+    import torch
+
+    import paper_1908_05944_gb300 as ac
+
+    out = {}
+    for name, prec in (("filtered", ac.AC_PRECISION_FILTERED), ("plain_fp64", ac.AC_PRECISION_PLAIN_FP64)):
+        cx = ac.AlphaComplex(torch.from_numpy(c).cuda(), torch.from_numpy(r).cuda(), 0.0, ac.options(precision=prec))
+        cx.build()
+        same, rel = True, []
+        for d in range(4):
+            got = cx.simplices(d).cpu().numpy()
+            same &= got.shape == ref.simplices[d].shape and bool(np.array_equal(got, ref.simplices[d]))
+            same &= bool(np.array_equal(cx.attached(d).cpu().numpy().astype(bool), ref.attached[d]))
+            if same:
+                f, g = cx.filtration_values(d).cpu().numpy(), ref.f[d]
+                nz = g != 0
+                same &= bool(np.array_equal(f[~nz], g[~nz]))
+                rel.append(np.abs(f[nz] - g[nz]) / np.abs(g[nz]))
+        cx.close()
+        rel = np.concatenate(rel) if rel else np.zeros(1)
+        out[name] = {"lists_equal": same, "f_rel_err_max": float(rel.max()), "f_rel_err_p50": float(np.median(rel)),
+                     "f_rel_err_p99": float(np.percentile(rel, 99))}
+    return out
 
 
 def sub_ball(c, r, k):

@@ -133,82 +133,112 @@ __device__ T block_excl_scan(T v, T* total) {
     return r;
 }
 
-template <class T>
-__global__ void k_scan_reduce(const T* in, int64_t n, T* partial) {
-    int64_t base = (int64_t)blockIdx.x * SCAN_TILE;
-    T s = 0;
-    for (int k = 0; k < SCAN_ITEMS; k++) {
-        int64_t i = base + (int64_t)k * SCAN_THREADS + threadIdx.x;
-        if (i < n) s += in[i];
-    }
-    __shared__ T tot;
-    block_excl_scan<T>(s, &tot);
-    if (threadIdx.x == 0) partial[blockIdx.x] = tot;
-}
+// Single-pass exclusive scan (decoupled look-back): tiles take their index
+// from a counter in launch order, publish their sum, then add the sums (or the
+// inclusive prefix, once known) of the tiles before them. A tile only waits
+// on tiles that took an earlier index and are therefore running; the wait is
+// bounded all the same and sets DERR_TIMEOUT if it ever runs out.
+struct ScanState {
+    unsigned next_tile;
+    unsigned pad;
+};
 
 template <class T>
-__global__ void k_scan_apply(const T* in, T* out, int64_t n, const T* partial_excl) {
-    int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_lookback(const T* in, T* out, int64_t n, ScanState* st,
+                                                                 int* flags, T* agg, T* inc, unsigned* err) {
+    __shared__ int tile_s;
+    __shared__ T prefix_s;
+    __shared__ T total_s;
+    if (threadIdx.x == 0) tile_s = (int)atomicAdd(&st->next_tile, 1u);
+    __syncthreads();
+    const int tile = tile_s;
+    const int64_t base = (int64_t)tile * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
     T v[SCAN_ITEMS];
-    T s = 0;
+    T sum = 0;
+#pragma unroll
     for (int k = 0; k < SCAN_ITEMS; k++) {
-        int64_t i = base + k;
+        const int64_t i = base + k;
         v[k] = i < n ? in[i] : T(0);
-        s += v[k];
+        sum += v[k];
     }
-    __shared__ T tot;
-    T pre = block_excl_scan<T>(s, &tot) + partial_excl[blockIdx.x];
+    T pre = block_excl_scan<T>(sum, &total_s);  // prefix within the tile
+    if (threadIdx.x == 0) {
+        const T total = total_s;
+        volatile int* vf = flags;
+        T acc = 0;
+        if (tile == 0) {
+            inc[0] = total;
+            __threadfence();
+            vf[0] = 2;
+        } else {
+            agg[tile] = total;
+            __threadfence();
+            vf[tile] = 1;
+            int p = tile - 1;
+            long long spins = 0;
+            while (p >= 0) {
+                const int f = vf[p];
+                if (f == 0) {
+                    if (++spins > (1ll << 24)) {  // far beyond any real wait (microseconds): give up, flag it
+                        atomicOr(err, DERR_TIMEOUT);
+                        break;
+                    }
+                    continue;
+                }
+                __threadfence();
+                if (f == 2) {
+                    acc += *(volatile T*)&inc[p];
+                    break;
+                }
+                acc += *(volatile T*)&agg[p];
+                p--;
+            }
+            inc[tile] = acc + total;
+            __threadfence();
+            vf[tile] = 2;
+        }
+        prefix_s = acc;
+    }
+    __syncthreads();
+    pre += prefix_s;
+    // out has n + 1 entries: out[n] is the total (the inputs past n count as 0)
+#pragma unroll
     for (int k = 0; k < SCAN_ITEMS; k++) {
-        int64_t i = base + k;
-        if (i < n) out[i] = pre;
+        const int64_t i = base + k;
+        if (i <= n) out[i] = pre;
         pre += v[k];
     }
-    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) out[n] = partial_excl[blockIdx.x] + tot;
 }
 
 template <class T>
-static int scan_impl(const T* in, T* out, int64_t n, DevBuf& tmp, size_t tmp_off, cudaStream_t s) {
+static int scan_entry(const T* in, T* out, int64_t n, DevBuf& tmp, DevCounters* dc, cudaStream_t s) {
     if (n <= 0) {
         AC_CUDA(cudaMemsetAsync(out, 0, sizeof(T), s));
         return AC_OK;
     }
-    int64_t nb = (n + SCAN_TILE - 1) / SCAN_TILE;
-    size_t need = tmp_off + sizeof(T) * (size_t)(nb + 1);
-    // the recursion nests partial arrays after each other in tmp; reserve generously up front
-    if (need > tmp.bytes) return fail(AC_ERR_OOM, "scan scratch too small");
-    T* partial = reinterpret_cast<T*>(static_cast<char*>(tmp.p) + tmp_off);
-    if (nb == 1) {
-        // one tile: the block offset is zero
-        AC_CUDA(cudaMemsetAsync(partial, 0, sizeof(T), s));
-    } else {
-        k_scan_reduce<T><<<(unsigned)nb, SCAN_THREADS, 0, s>>>(in, n, partial);
-        AC_LAUNCHED();
-        size_t next_off = tmp_off + ((sizeof(T) * (size_t)(nb + 1) + 255) & ~(size_t)255);
-        AC_TRY(scan_impl<T>(partial, partial, nb, tmp, next_off, s));
-    }
-    k_scan_apply<T><<<(unsigned)nb, SCAN_THREADS, 0, s>>>(in, out, n, partial);
+    const int64_t tiles = n / SCAN_TILE + 1;  // n + 1 outputs
+    // state: counter, flags (int per tile), aggregates and inclusive prefixes (T per tile)
+    const size_t flags_off = 64, agg_off = (flags_off + (size_t)tiles * sizeof(int) + 63) & ~(size_t)63;
+    const size_t inc_off = (agg_off + (size_t)tiles * sizeof(T) + 63) & ~(size_t)63;
+    const size_t need = inc_off + (size_t)tiles * sizeof(T);
+    AC_TRY(tmp.reserve(need, s));
+    char* b = static_cast<char*>(tmp.p);
+    AC_CUDA(cudaMemsetAsync(b, 0, agg_off, s));  // counter and flags
+    k_scan_lookback<T><<<(unsigned)tiles, SCAN_THREADS, 0, s>>>(in, out, n, reinterpret_cast<ScanState*>(b),
+                                                                 reinterpret_cast<int*>(b + flags_off),
+                                                                 reinterpret_cast<T*>(b + agg_off),
+                                                                 reinterpret_cast<T*>(b + inc_off), &dc->err);
     AC_LAUNCHED();
     return AC_OK;
 }
 
-template <class T>
-static int scan_entry(const T* in, T* out, int64_t n, DevBuf& tmp, cudaStream_t s) {
-    size_t need = 0;
-    for (int64_t m = n; m > 0; m = (m + SCAN_TILE - 1) / SCAN_TILE) {
-        int64_t nb = (m + SCAN_TILE - 1) / SCAN_TILE;
-        need += ((sizeof(T) * (size_t)(nb + 1) + 255) & ~(size_t)255);
-        if (nb == 1) break;
-    }
-    AC_TRY(tmp.reserve(need + 256, s));
-    return scan_impl<T>(in, out, n, tmp, 0, s);
+int scan_exclusive_i64(ac_ctx* c, const int64_t* in, int64_t* out, int64_t n, cudaStream_t s) {
+    return scan_entry<long long>(reinterpret_cast<const long long*>(in), reinterpret_cast<long long*>(out), n,
+                                 c->scan_tmp, c->counters.as<DevCounters>(), s);
 }
 
-int scan_exclusive_i64(const int64_t* in, int64_t* out, int64_t n, DevBuf& tmp, cudaStream_t s) {
-    return scan_entry<long long>(reinterpret_cast<const long long*>(in), reinterpret_cast<long long*>(out), n, tmp, s);
-}
-
-int scan_exclusive_u32_to_u32(const uint32_t* in, uint32_t* out, int64_t n, DevBuf& tmp, cudaStream_t s) {
-    return scan_entry<unsigned>(in, out, n, tmp, s);
+int scan_exclusive_u32_to_u32(ac_ctx* c, const uint32_t* in, uint32_t* out, int64_t n, cudaStream_t s) {
+    return scan_entry<unsigned>(in, out, n, c->scan_tmp, c->counters.as<DevCounters>(), s);
 }
 
 int sync_host(ac_ctx* c, cudaStream_t s) {
@@ -660,6 +690,11 @@ extern "C" int ac_build(ac_ctx* c, void* stream) {
         AC_TRY(read_counters(c, &h, s));
     }
     if (h.err & DERR_INTERNAL) return fail(AC_ERR_CUDA, "internal: attached simplex without a coface in the complex");
+    if (h.err & DERR_TIMEOUT) {
+        drop_graph(c);
+        c->rec.valid = false;
+        return fail(AC_ERR_TIMEOUT, "a bounded device wait (scan look-back) ran out");
+    }
     if (!replayed && !c->opt.no_graph) AC_TRY(record_build(c, h, s));
     finish_mol_rows(c);
     const DevCounters& hl = h;  // the per-atom pass wrote them; later stages add only error bits

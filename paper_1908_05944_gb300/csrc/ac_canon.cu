@@ -18,6 +18,8 @@
 // below 4 * 2^-53).
 #include <math.h>
 
+#include <type_traits>
+
 #include "ac_internal.cuh"
 
 namespace ac {
@@ -171,22 +173,29 @@ __device__ __forceinline__ void make_key(const int4& t, unsigned long long& hi, 
     }
 }
 
-template <int K>
-__device__ __forceinline__ bool key_less(unsigned long long ah, unsigned al, unsigned long long bh, unsigned bl) {
+template <int K, class H>
+__device__ __forceinline__ bool key_less(H ah, unsigned al, H bh, unsigned bl) {
     return K == 4 ? (ah < bh || (ah == bh && al < bl)) : ah < bh;
 }
 
+// register type of the high key: edges' keys (y << 1 | flag, y < 2^31) fit 32 bits
+template <int K>
+using KeyHi = typename std::conditional<K == 2, unsigned, unsigned long long>::type;
+
 template <int K, int R>
 __device__ __forceinline__ void bitonic_place(SortSmem& S, const int4* __restrict__ T, int64_t a, int k, int lane) {
-    unsigned long long h[R];
+    using H = KeyHi<K>;
+    H h[R];
     unsigned l[R];
 #pragma unroll
     for (int r = 0; r < R; r++) {
         const int e = 32 * r + lane;
         if (e < k) {
-            make_key<K>(T[a + e], h[r], l[r]);
+            unsigned long long hi;
+            make_key<K>(T[a + e], hi, l[r]);
+            h[r] = (H)hi;
         } else {
-            h[r] = ~0ull;
+            h[r] = (H)~0ull;
             l[r] = ~0u;
         }
     }
@@ -203,7 +212,7 @@ __device__ __forceinline__ void bitonic_place(SortSmem& S, const int4* __restric
                         const int r2 = r | rs;
                         const bool asc = ((32 * r + lane) & size) == 0;
                         if (key_less<K>(h[r2], l[r2], h[r], l[r]) == asc) {
-                            const unsigned long long th = h[r];
+                            const H th = h[r];
                             h[r] = h[r2];
                             h[r2] = th;
                             const unsigned tl = l[r];
@@ -215,7 +224,7 @@ __device__ __forceinline__ void bitonic_place(SortSmem& S, const int4* __restric
             } else {
 #pragma unroll
                 for (int r = 0; r < R; r++) {
-                    const unsigned long long oh = __shfl_xor_sync(0xffffffffu, h[r], stride);
+                    const H oh = __shfl_xor_sync(0xffffffffu, h[r], stride);
                     const unsigned ol = K == 4 ? __shfl_xor_sync(0xffffffffu, l[r], stride) : 0u;
                     const bool asc = ((32 * r + lane) & size) == 0;
                     const bool lower = (lane & stride) == 0;
@@ -233,7 +242,7 @@ __device__ __forceinline__ void bitonic_place(SortSmem& S, const int4* __restric
     for (int r = 0; r < R; r++) {
         const int e = 32 * r + lane;
         if (e < k) {
-            S.ohi[e] = h[r];
+            S.ohi[e] = (unsigned long long)h[r];
             if (K == 4) S.olo[e] = l[r];
         }
     }
@@ -404,7 +413,7 @@ static int canon_dim_k(ac_ctx* c, const int4* a4, const int2* a2, int64_t nA, co
         k_canon_count<K><<<gi, 256, 0, s>>>(ca);
         AC_LAUNCHED();
     }
-    AC_TRY(scan_exclusive_i64(cnt, cnt, n, c->scan_tmp, s));  // bucket offsets, in place
+    AC_TRY(scan_exclusive_i64(c, cnt, cnt, n, s));  // bucket offsets, in place
     int64_t* uniq = w.uniq.as<int64_t>();
     if (total > 0) {
         k_canon_scatter<K><<<gi, 256, 0, s>>>(ca);
@@ -425,7 +434,7 @@ static int canon_dim_k(ac_ctx* c, const int4* a4, const int2* a2, int64_t nA, co
         AC_LAUNCHED();
     }
     int64_t* uoff = L.v0_off.as<int64_t>();
-    AC_TRY(scan_exclusive_i64(uniq, uoff, n, c->scan_tmp, s));
+    AC_TRY(scan_exclusive_i64(c, uniq, uoff, n, s));
     int64_t count = L.count;  // a replay keeps the recorded build's count and checks it
     if (c->replaying) {
         AC_TRY(expect_i64(c, uoff + n, count, s));
@@ -543,7 +552,7 @@ int canonicalise(ac_ctx* c, cudaStream_t s) {
             AC_LAUNCHED();
         }
         int64_t* voff = L.v0_off.as<int64_t>();
-        AC_TRY(scan_exclusive_i64(inK, voff, n, c->scan_tmp, s));
+        AC_TRY(scan_exclusive_i64(c, inK, voff, n, s));
         int64_t count = L.count;
         if (c->replaying) {
             AC_TRY(expect_i64(c, voff + n, count, s));

@@ -88,7 +88,7 @@ int build_grid(ac_ctx* c, cudaStream_t s) {
     k_cell_keys<<<nb, 256, 0, s>>>(c->P.as<int4>(), c->mol_of.as<int32_t>(), c->grids.as<MolGrid>(), c->pc.cell, n,
                                    c->cell_of.as<uint32_t>(), cnt);
     AC_LAUNCHED();
-    AC_TRY(scan_exclusive_u32_to_u32(cnt, start, c->n_cells, c->scan_tmp, s));
+    AC_TRY(scan_exclusive_u32_to_u32(c, cnt, start, c->n_cells, s));
     AC_CUDA(cudaMemsetAsync(cnt, 0, (size_t)c->n_cells * sizeof(uint32_t), s));
     k_scatter<<<nb, 256, 0, s>>>(c->cell_of.as<uint32_t>(), start, n, cnt, c->order.as<int32_t>());
     AC_LAUNCHED();
@@ -242,7 +242,7 @@ int build_neighbours(ac_ctx* c, cudaStream_t s) {
     AC_LAUNCHED();
     k_deg_scatter<<<nb, 128, 0, s>>>(cntp, n, cursor, c->work.as<int32_t>());
     AC_LAUNCHED();
-    AC_TRY(scan_exclusive_i64(cntp, cntp, n, c->scan_tmp, s));
+    AC_TRY(scan_exclusive_i64(c, cntp, cntp, n, s));
     int64_t total = 0;
     if (c->replaying) {
         // sizes of the recorded build, checked on the device

@@ -55,6 +55,7 @@ enum : uint32_t {
     DERR_INTERNAL = 1u << 8,     // an invariant of the method failed (a bug)
     DERR_OVF_PEND = 1u << 9,     // pending (escalated) list full
     DERR_REPLAY = 1u << 10,      // a size differs from the one recorded for the graph replay
+    DERR_TIMEOUT = 1u << 11,     // a bounded device wait ran out
 };
 
 // ---------------------------------------------------------------------------
@@ -249,8 +250,9 @@ struct ac_ctx {
 namespace ac {
 
 // launchers (each returns AC_OK or an AC_ERR_*)
-int scan_exclusive_i64(const int64_t* in, int64_t* out, int64_t n, DevBuf& tmp, cudaStream_t s);
-int scan_exclusive_u32_to_u32(const uint32_t* in, uint32_t* out, int64_t n, DevBuf& tmp, cudaStream_t s);
+// exclusive scans: n inputs -> n + 1 outputs (out[n] = total); in may alias out
+int scan_exclusive_i64(ac_ctx* c, const int64_t* in, int64_t* out, int64_t n, cudaStream_t s);
+int scan_exclusive_u32_to_u32(ac_ctx* c, const uint32_t* in, uint32_t* out, int64_t n, cudaStream_t s);
 
 int quantise_and_plan(ac_ctx* c, cudaStream_t s);
 int build_grid(ac_ctx* c, cudaStream_t s);
