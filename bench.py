@@ -323,6 +323,28 @@ def run_forms(args):
     out["batch1024_probe"] = {"n_atoms": n_all, "batched_atoms_per_s": batched, "batched_ms": sum(ms) / steps,
                               "batched_graph_replay": bool(replayed), "autotuned": tuned,
                               "per_molecule_atoms_per_s": per_mol}
+    # alpha sweep (the filtration restricted): one build at alpha = 2 A^2, then the complexes at 21 alphas in
+    # [0, 2] by exact thresholds on Size, against 21 separate builds
+    cg, rg = workload("globule100k_probe")
+    tc, tr = torch.from_numpy(cg).cuda(), torch.from_numpy(rg).cuda()
+    alphas2 = [0.1 * k for k in range(21)]
+    sx = ac.AlphaComplex(tc, tr, 2.0).build(stream)
+    sx.build(stream)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    sx.build(stream)
+    sizes = [[sx.subcomplex_mask(d, a2, -1, stream)[1] for d in range(4)] for a2 in alphas2]
+    torch.cuda.synchronize()
+    sweep_ms = (time.perf_counter() - t0) * 1e3
+    sx.close()
+    t0 = time.perf_counter()
+    for a2 in alphas2:
+        bx2 = ac.AlphaComplex(tc, tr, a2).build(stream)
+        bx2.close()
+    torch.cuda.synchronize()
+    builds_ms = (time.perf_counter() - t0) * 1e3
+    out["globule100k_probe/alpha_sweep"] = {"alphas": len(alphas2), "sweep_ms": sweep_ms, "separate_builds_ms": builds_ms,
+                                           "simplices_at_0_and_2": [sizes[0], sizes[-1]]}
     # backward (row a14) on the 20k globule: dL/dcentres, dL/dradii for random weights on every simplex
     c20, r20 = workload("globule20k_probe")
     gx = ac.AlphaComplex(torch.from_numpy(c20).cuda(), torch.from_numpy(r20).cuda(), 0.0).build(stream)

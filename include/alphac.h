@@ -214,6 +214,21 @@ AC_API int ac_backward_noalloc(ac_ctx* ctx, const double* const d_dLdf[4], doubl
  */
 AC_API int ac_autotune(ac_ctx* ctx, void* stream, ac_options* chosen);
 
+/*
+ * The alpha complex at a smaller alpha from a built one (the filtration
+ * restricted; the alpha sweep of Section 6): K_alpha2 = {sigma in K_alpha :
+ * Size(sigma) <= alpha2} (Section 2.4, inclusive), decided exactly on the
+ * rational Size (not on its FP64 rounding). alpha2 is quantised like alpha
+ * (rint(2^20 alpha2)) and must not exceed the context's alpha.
+ * d_flags: caller-owned DEVICE array of the list's length (ac_get_simplices'
+ * count for dim and mol); entry j is set to 1 if row j is in K_alpha2, else 0.
+ * *count_in receives the number of rows set. Synchronises the stream.
+ * Errors: AC_ERR_INVALID_ARG (bad dim/mol, NULL, alpha2 > alpha), AC_ERR_STATE
+ * (no build yet), AC_ERR_CUDA.
+ */
+AC_API int ac_subcomplex(ac_ctx* ctx, int dim, int64_t mol, double alpha2, uint8_t* d_flags, int64_t* count_in,
+                         void* stream);
+
 /* Counters and stage times of the last ac_build. */
 AC_API int ac_get_stats(ac_ctx* ctx, ac_stats* out);
 

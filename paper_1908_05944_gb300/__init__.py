@@ -36,8 +36,8 @@ AC_FILTRATION_ORTHOSIZE = 1
 
 # every symbol include/alphac.h declares
 EXPORTS = ["ac_create", "ac_create_batch", "ac_build", "ac_get_simplices", "ac_filtration_values", "ac_attached_flags",
-           "ac_get_candidates", "ac_eval_filtration", "ac_backward", "ac_backward_noalloc", "ac_autotune", "ac_get_stats",
-           "ac_get_sizes", "ac_destroy", "ac_error_string", "ac_last_error_detail"]
+           "ac_get_candidates", "ac_eval_filtration", "ac_backward", "ac_backward_noalloc", "ac_autotune",
+           "ac_subcomplex", "ac_get_stats", "ac_get_sizes", "ac_destroy", "ac_error_string", "ac_last_error_detail"]
 
 
 class ac_options(ctypes.Structure):
@@ -90,6 +90,7 @@ def _declare(lib):
     lib.ac_backward.argtypes = [vp, vp, vp, vp, vp]
     lib.ac_backward_noalloc.argtypes = [vp, vp, vp, vp, vp]
     lib.ac_autotune.argtypes = [vp, vp, P(ac_options)]
+    lib.ac_subcomplex.argtypes = [vp, i32, i64, dbl, vp, P(i64), vp]
     lib.ac_get_stats.argtypes = [vp, P(ac_stats)]
     lib.ac_get_sizes.argtypes = [vp, P(i64), P(i64)]
     lib.ac_destroy.argtypes = [vp]
@@ -245,6 +246,25 @@ class AlphaComplex:
         o = ac_options()
         _check(lib().ac_autotune(self._h, _stream_ptr(stream), ctypes.byref(o)), "ac_autotune")
         return {"cell_factor": o.cell_factor, "block_warps": o.block_warps}
+
+    def subcomplex_mask(self, dim: int, alpha2: float, mol: int = -1, stream=None):
+        """uint8 CUDA mask of the rows of list dim that are in K_alpha2 (alpha2 <= alpha), and their number."""
+        import torch
+        m = self.count(dim, mol)
+        flags = torch.empty(max(m, 1), dtype=torch.uint8, device="cuda")
+        cnt = ctypes.c_int64()
+        _check(lib().ac_subcomplex(self._h, dim, mol, float(alpha2), flags.data_ptr(), ctypes.byref(cnt),
+                                   _stream_ptr(stream)), "ac_subcomplex")
+        return flags[:m], cnt.value
+
+    def subcomplex(self, alpha2: float, mol: int = -1, stream=None):
+        """The alpha complex at alpha2 <= alpha from this build: per dimension (simplices, Size values)."""
+        out = []
+        for d in range(4):
+            mask, _ = self.subcomplex_mask(d, alpha2, mol, stream)
+            keep = mask.bool()
+            out.append((self.simplices(d, mol)[keep], self.filtration_values(d, mol)[keep]))
+        return out
 
     def stats(self) -> dict:
         s = ac_stats()

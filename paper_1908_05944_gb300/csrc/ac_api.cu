@@ -797,6 +797,17 @@ extern "C" int ac_backward_noalloc(ac_ctx* c, const double* const d_dLdf[4], dou
     return backward_noalloc(c, d_dLdf, d_dLdcentres, d_dLdradii, (cudaStream_t)stream);
 }
 
+extern "C" int ac_subcomplex(ac_ctx* c, int dim, int64_t mol, double alpha2, uint8_t* d_flags, int64_t* count_in,
+                             void* stream) {
+    int64_t first = 0, count = 0;
+    AC_TRY(get_list(c, c ? c->K : nullptr, dim, mol, &first, &count));
+    if (!count_in || (count > 0 && !d_flags)) return fail(AC_ERR_INVALID_ARG, "bad argument");
+    if (!(alpha2 <= c->alpha)) return fail(AC_ERR_INVALID_ARG, "alpha2 must not exceed the context's alpha");
+    if (!(alpha2 * 1048576.0 > -9.2e18)) return fail(AC_ERR_INVALID_ARG, "alpha2 out of range");
+    StreamScope scope((cudaStream_t)stream);
+    return subcomplex_flags(c, dim, first, count, alpha2, d_flags, count_in, (cudaStream_t)stream);
+}
+
 extern "C" int ac_autotune(ac_ctx* c, void* stream, ac_options* chosen) {
     if (!c) return fail(AC_ERR_INVALID_ARG, "ctx is NULL");
     // grid cell side (in units of h) and warps per block of the per-atom kernel

@@ -621,11 +621,26 @@ __device__ __forceinline__ double i128_to_double(i128 x) {
     return neg ? -r : r;
 }
 
+// OrthoSize of a simplex of global input indices (ascending, K entries) as an
+// exact rational num / den in quanta^2 (den > 0).
+__device__ void orthosize_rational(const int4* __restrict__ P, const int4& t, int K, i128& num, i128& den);
+
 // OrthoSize in A^2 of a simplex of global input indices (ascending, K entries).
 __device__ double orthosize_exact(const int4* __restrict__ P, const int4& t, int K) {
+    i128 num, den;
+    orthosize_rational(P, t, K, num, den);
+    if (K == 1) return (double)(long long)num * 9.5367431640625e-07;  // 2^-20, exact
+    return i128_to_double(num) / i128_to_double(den) * 9.5367431640625e-07;
+}
+
+__device__ void orthosize_rational(const int4* __restrict__ P, const int4& t, int K, i128& num, i128& den) {
     const int4 p0 = P[t.x];
     const long long W0 = p0.w;
-    if (K == 1) return -(double)W0 * 9.5367431640625e-07;  // 2^-20
+    if (K == 1) {
+        num = -(i128)W0;
+        den = 1;
+        return;
+    }
     int v[4] = {t.x, t.y, t.z, t.w};
     long long q[3][3], a[3];
     for (int k = 1; k < K; k++) {
@@ -635,7 +650,6 @@ __device__ double orthosize_exact(const int4* __restrict__ P, const int4& t, int
         q[k - 1][2] = pk.z - p0.z;
         a[k - 1] = q[k - 1][0] * q[k - 1][0] + q[k - 1][1] * q[k - 1][1] + q[k - 1][2] * q[k - 1][2] - pk.w + W0;
     }
-    i128 num, den;
     if (K == 2) {
         long long D = q[0][0] * q[0][0] + q[0][1] * q[0][1] + q[0][2] * q[0][2];
         num = (i128)a[0] * a[0] - (i128)4 * D * W0;
@@ -666,7 +680,6 @@ __device__ double orthosize_exact(const int4* __restrict__ P, const int4& t, int
         num = nn - DD * (4 * W0);
         den = DD * 4;
     }
-    return i128_to_double(num) / i128_to_double(den) * 9.5367431640625e-07;
 }
 
 __global__ void k_orthosize(const int4* __restrict__ P, const int4* __restrict__ G, int64_t m, int K,
@@ -753,6 +766,50 @@ __global__ void k_coface_apply(int64_t m, const uint8_t* __restrict__ attached, 
     f[j] = key_value(fkey[j]);
     src_dim[j] = csrc_dim[a];
     src_idx[j] = csrc_idx[a];
+}
+
+// Sub-complex at alpha2 <= alpha (the filtration restricted): a simplex is in
+// K_alpha2 iff Size <= alpha2 (Section 2.4). Size is the OrthoSize of the
+// simplex's source (itself when unattached, else the coface its value came
+// from), compared exactly: num <= A2 den.
+__global__ void k_subcomplex(const int4* __restrict__ P, const int4* __restrict__ const* G, const int8_t* __restrict__ src_dim,
+                             const int64_t* __restrict__ src_idx, int64_t first, int64_t m, long long A2,
+                             uint8_t* __restrict__ flags, unsigned long long* __restrict__ n_in) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    bool in = false;
+    if (j < m) {
+        const int sd = src_dim[first + j];
+        const int4 t = G[sd][src_idx[first + j]];
+        i128 num, den;
+        orthosize_rational(P, t, sd + 1, num, den);
+        in = num <= (i128)A2 * den;
+        flags[j] = in ? 1 : 0;
+    }
+    const unsigned b = __ballot_sync(0xffffffffu, in);
+    if ((threadIdx.x & 31) == 0 && b) atomicAdd(n_in, (unsigned long long)__popc(b));
+}
+
+int subcomplex_flags(ac_ctx* c, int dim, int64_t first, int64_t m, double alpha2, uint8_t* flags, int64_t* count,
+                     cudaStream_t s) {
+    const long long A2 = (long long)nearbyint(alpha2 * 1048576.0);
+    AC_TRY(c->scratch[6].reserve(sizeof(unsigned long long) + 4 * sizeof(int4*), s));
+    unsigned long long* n_in = c->scratch[6].as<unsigned long long>();
+    const int4** g = reinterpret_cast<const int4**>(n_in + 1);
+    const int4* gh[4];
+    for (int d = 0; d < 4; d++) gh[d] = c->Gbuf[d].as<int4>();
+    AC_CUDA(cudaMemcpyAsync(g, gh, sizeof(gh), cudaMemcpyHostToDevice, s));
+    AC_CUDA(cudaMemsetAsync(n_in, 0, sizeof(unsigned long long), s));
+    if (m > 0) {
+        SimplexList& L = c->K[dim];
+        k_subcomplex<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(c->P.as<int4>(), g, L.src_dim.as<int8_t>(),
+                                                                  L.src_idx.as<int64_t>(), first, m, A2, flags, n_in);
+        AC_LAUNCHED();
+    }
+    unsigned long long h = 0;
+    AC_CUDA(cudaMemcpyAsync(&h, n_in, sizeof(h), cudaMemcpyDeviceToHost, s));
+    AC_CUDA(cudaStreamSynchronize(s));
+    *count = (int64_t)h;
+    return AC_OK;
 }
 
 int compute_filtration(ac_ctx* c, cudaStream_t s) {

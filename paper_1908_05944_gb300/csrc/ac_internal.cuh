@@ -219,7 +219,7 @@ struct ac_ctx {
 
     // scratch
     ac::DevBuf counters;  // DevCounters
-    ac::DevBuf scratch[6];
+    ac::DevBuf scratch[7];
     ac::DevBuf scan_tmp;
 
     ac::DevCounters hc{};             // host copy of the counters from the last readback
@@ -263,6 +263,8 @@ int compute_filtration(ac_ctx* c, cudaStream_t s);
 int eval_filtration(ac_ctx* c, const double* centres, const double* radii, double* const f_out[4], cudaStream_t s);
 int backward(ac_ctx* c, const double* const dldf[4], double* dc, double* dr, cudaStream_t s);
 int backward_noalloc(ac_ctx* c, const double* const dldf[4], double* dc, double* dr, cudaStream_t s);
+int subcomplex_flags(ac_ctx* c, int dim, int64_t first, int64_t m, double alpha2, uint8_t* flags, int64_t* count,
+                     cudaStream_t s);
 
 int read_counters(ac_ctx* c, DevCounters* h, cudaStream_t s);
 // Replay checks: set DERR_REPLAY in the counters when a device value differs
