@@ -247,18 +247,21 @@ int sync_host(ac_ctx* c, cudaStream_t s) {
     return AC_OK;
 }
 
-__global__ void k_expect_i64(const int64_t* __restrict__ v, int64_t want, unsigned* __restrict__ err) {
-    if (threadIdx.x == 0 && *v != want) atomicOr(err, DERR_REPLAY);
-}
-
-__global__ void k_expect_u64(const unsigned long long* __restrict__ v, unsigned long long want, unsigned* __restrict__ err) {
-    if (threadIdx.x == 0 && *v != want) atomicOr(err, DERR_REPLAY);
-}
-
-__global__ void k_expect_i32s(const int32_t* __restrict__ v, const int32_t* __restrict__ want, int64_t n,
-                              unsigned* __restrict__ err) {
-    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (j < n && v[j] != want[j]) atomicOr(err, DERR_REPLAY);
+// One thread per check gathered during the capture (they all read values
+// that stay in place until the end of the build).
+__global__ void k_check_expects(const ExpectEntry* __restrict__ t, int n, unsigned* __restrict__ err) {
+    const int j = threadIdx.x;
+    if (j >= n) return;
+    const ExpectEntry e = t[j];
+    bool ok = true;
+    if (e.kind == 0) ok = *static_cast<const long long*>(e.p) == e.want;
+    else if (e.kind == 1) ok = *static_cast<const unsigned long long*>(e.p) == (unsigned long long)e.want;
+    else {
+        const int32_t* a = static_cast<const int32_t*>(e.p);
+        const int32_t* b = static_cast<const int32_t*>(e.ref);
+        for (int k = 0; k < e.count && ok; k++) ok = a[k] == b[k];
+    }
+    if (!ok) atomicOr(err, DERR_REPLAY);
 }
 
 int stage_mark(ac_ctx* c, int k, cudaStream_t s) {
@@ -266,16 +269,23 @@ int stage_mark(ac_ctx* c, int k, cudaStream_t s) {
     return AC_OK;
 }
 
-int expect_i64(ac_ctx* c, const int64_t* d_value, int64_t want, cudaStream_t s) {
-    k_expect_i64<<<1, 32, 0, s>>>(d_value, want, &c->counters.as<DevCounters>()->err);
-    AC_LAUNCHED();
+static int add_expect(ac_ctx* c, const ExpectEntry& e) {
+    if ((int)c->expects.size() >= MAX_EXPECTS) return fail(AC_ERR_CAPACITY, "too many replay checks");
+    c->expects.push_back(e);
     return AC_OK;
 }
 
-int expect_u64(ac_ctx* c, const unsigned long long* d_value, unsigned long long want, cudaStream_t s) {
-    k_expect_u64<<<1, 32, 0, s>>>(d_value, want, &c->counters.as<DevCounters>()->err);
-    AC_LAUNCHED();
-    return AC_OK;
+int expect_i64(ac_ctx* c, const int64_t* d_value, int64_t want, cudaStream_t) {
+    return add_expect(c, ExpectEntry{d_value, nullptr, (long long)want, 0, 1});
+}
+
+int expect_u64(ac_ctx* c, const unsigned long long* d_value, unsigned long long want, cudaStream_t) {
+    return add_expect(c, ExpectEntry{d_value, nullptr, (long long)want, 1, 1});
+}
+
+int expect_i32s(ac_ctx* c, const int32_t* d_values, const int32_t* d_ref, int64_t count) {
+    if (count > INT32_MAX) return fail(AC_ERR_CAPACITY, "replay check too long");
+    return add_expect(c, ExpectEntry{d_values, d_ref, 0, 2, (int)count});
 }
 
 int read_counters(ac_ctx* c, DevCounters* h, cudaStream_t s) {
@@ -394,11 +404,8 @@ int quantise_and_plan(ac_ctx* c, cudaStream_t s) {
     }
     if (c->replaying) {
         // the recorded plan stands; check the bounds it rests on
-        k_expect_i32s<<<(unsigned)((n_mol * 6 + 255) / 256), 256, 0, s>>>(bbox, c->rec_bbox.as<int32_t>(), n_mol * 6,
-                                                                          &dc->err);
-        AC_LAUNCHED();
-        k_expect_i32s<<<1, 32, 0, s>>>(wmax, c->rec_bbox.as<int32_t>() + n_mol * 6, 1, &dc->err);
-        AC_LAUNCHED();
+        AC_TRY(expect_i32s(c, bbox, c->rec_bbox.as<int32_t>(), n_mol * 6));
+        AC_TRY(expect_i32s(c, wmax, c->rec_bbox.as<int32_t>() + n_mol * 6, 1));
         return AC_OK;
     }
     // one readback: counters, largest weight, per-molecule boxes
@@ -586,6 +593,12 @@ static int build_body(ac_ctx* c, cudaStream_t s) {
     AC_TRY(canonicalise(c, s));
     AC_TRY(stage_mark(c, 6, s));
     AC_TRY(compute_filtration(c, s));
+    if (c->replaying && !c->expects.empty()) {
+        // every recorded size, checked once the build's values are in place
+        k_check_expects<<<1, MAX_EXPECTS, 0, s>>>(c->expect_table.as<ExpectEntry>(), (int)c->expects.size(),
+                                                  &c->counters.as<DevCounters>()->err);
+        AC_LAUNCHED();
+    }
     AC_TRY(stage_mark(c, 7, s));
     return AC_OK;
 }
@@ -608,6 +621,9 @@ static void drop_graph(ac_ctx* c) {
 // stream; the graph is then launched on the caller's.
 static int capture_replay(ac_ctx* c) {
     cudaStream_t s = c->cap_stream;
+    c->expects.clear();
+    AC_TRY(c->expect_table.reserve(MAX_EXPECTS * sizeof(ExpectEntry), s));
+    AC_CUDA(cudaStreamSynchronize(s));
     AC_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
     const long long l0 = g_launch_count;
     c->replaying = true;
@@ -627,6 +643,15 @@ static int capture_replay(ac_ctx* c) {
         cudaGraphDestroy(g);
         cudaGetLastError();
         return fail(AC_ERR_CUDA, "graph instantiation failed");
+    }
+    // the checks the graph runs: their table sits at a fixed address the graph captured
+    if (!c->expects.empty() &&
+        cudaMemcpy(c->expect_table.p, c->expects.data(), c->expects.size() * sizeof(ExpectEntry),
+                   cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaGraphExecDestroy(ex);
+        cudaGraphDestroy(g);
+        cudaGetLastError();
+        return fail(AC_ERR_CUDA, "upload of the replay checks failed");
     }
     c->graph = g;
     c->graph_exec = ex;

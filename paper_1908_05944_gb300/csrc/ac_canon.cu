@@ -248,10 +248,39 @@ __device__ __forceinline__ void bitonic_place(SortSmem& S, const int4* __restric
     }
 }
 
+// Buckets above CSORT_MAX items (rare): one lane, insertion sort then de-duplication.
+template <int K>
+__device__ void sort_big_bucket(int4* __restrict__ T, int64_t a, int64_t b, int64_t* __restrict__ uniq_g) {
+    auto less = [](const int4& u, const int4& v) {
+        if (u.y != v.y) return u.y < v.y;
+        if (u.z != v.z) return u.z < v.z;
+        return K == 4 && u.w < v.w;
+    };
+    auto eq = [](const int4& u, const int4& v) { return u.y == v.y && u.z == v.z && (K != 4 || u.w == v.w); };
+    for (int64_t i = a + 1; i < b; i++) {
+        const int4 v = T[i];
+        int64_t j = i;
+        while (j > a && less(v, T[j - 1])) {
+            T[j] = T[j - 1];
+            j--;
+        }
+        T[j] = v;
+    }
+    int64_t w = a;
+    for (int64_t i = a; i < b; i++) {
+        const int4 v = T[i];
+        if (w > a && eq(T[w - 1], v)) {
+            if (K < 4) T[w - 1].w |= v.w;
+        } else {
+            T[w++] = v;
+        }
+    }
+    *uniq_g = w - a;
+}
+
 template <int K>
 __global__ void __launch_bounds__(CSORT_WARPS * 32) k_canon_sort(int4* __restrict__ T, const int64_t* __restrict__ off,
-                                                                  int64_t n, int64_t* __restrict__ uniq,
-                                                                  uint8_t* __restrict__ big) {
+                                                                  int64_t n, int64_t* __restrict__ uniq) {
     __shared__ SortSmem sm[CSORT_WARPS];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     SortSmem& S = sm[w];
@@ -261,10 +290,10 @@ __global__ void __launch_bounds__(CSORT_WARPS * 32) k_canon_sort(int4* __restric
         const int64_t kb = off[g + 1] - a;
         const int k = kb > CSORT_MAX ? CSORT_MAX + 1 : (int)kb;
         if (k > CSORT_MAX) {
-            if (lane == 0) big[g] = 1;
+            if (lane == 0) sort_big_bucket<K>(T, a, a + kb, &uniq[g]);
+            __syncwarp();
             continue;
         }
-        if (lane == 0) big[g] = 0;
         if (k <= 1) {
             if (lane == 0) uniq[g] = k;
             continue;
@@ -316,40 +345,6 @@ __global__ void __launch_bounds__(CSORT_WARPS * 32) k_canon_sort(int4* __restric
         if (lane == 0) uniq[g] = base;
         __syncwarp();
     }
-}
-
-// Buckets above CSORT_MAX items, one thread each (insertion sort).
-template <int K>
-__global__ void k_canon_sort_big(int4* __restrict__ T, const int64_t* __restrict__ off, int64_t n,
-                                 int64_t* __restrict__ uniq, const uint8_t* __restrict__ big) {
-    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= n || !big[g]) return;
-    const int64_t a = off[g], b = off[g + 1];
-    auto less = [](const int4& u, const int4& v) {
-        if (u.y != v.y) return u.y < v.y;
-        if (u.z != v.z) return u.z < v.z;
-        return K == 4 && u.w < v.w;
-    };
-    auto eq = [](const int4& u, const int4& v) { return u.y == v.y && u.z == v.z && (K != 4 || u.w == v.w); };
-    for (int64_t i = a + 1; i < b; i++) {
-        const int4 v = T[i];
-        int64_t j = i;
-        while (j > a && less(v, T[j - 1])) {
-            T[j] = T[j - 1];
-            j--;
-        }
-        T[j] = v;
-    }
-    int64_t w = a;
-    for (int64_t i = a; i < b; i++) {
-        const int4 v = T[i];
-        if (w > a && eq(T[w - 1], v)) {
-            if (K < 4) T[w - 1].w |= v.w;
-        } else {
-            T[w++] = v;
-        }
-    }
-    uniq[g] = w - a;
 }
 
 // Slot-parallel output: slot j of bucket g = T[j].x holds unique row j - off[g]
@@ -427,10 +422,7 @@ static int canon_dim_k(ac_ctx* c, const int4* a4, const int2* a2, int64_t nA, co
         // one resident wave, buckets taken grid-stride
         int64_t blocks = (n + CSORT_WARPS - 1) / CSORT_WARPS;
         if (blocks > (int64_t)sms * (per_sm > 0 ? per_sm : 1)) blocks = (int64_t)sms * (per_sm > 0 ? per_sm : 1);
-        k_canon_sort<K><<<(unsigned)blocks, CSORT_WARPS * 32, 0, s>>>(w.T.as<int4>(), cnt, n, uniq, w.big.as<uint8_t>());
-        AC_LAUNCHED();
-        k_canon_sort_big<K><<<(unsigned)((n + 127) / 128), 128, 0, s>>>(w.T.as<int4>(), cnt, n, uniq,
-                                                                       w.big.as<uint8_t>());
+        k_canon_sort<K><<<(unsigned)blocks, CSORT_WARPS * 32, 0, s>>>(w.T.as<int4>(), cnt, n, uniq);
         AC_LAUNCHED();
     }
     int64_t* uoff = L.v0_off.as<int64_t>();

@@ -155,6 +155,17 @@ struct CanonWork {
     DevBuf T, cnt, cursor, uniq, big;
 };
 
+// A size a replay checks on the device: *p (kind 0: int64, 1: uint64) equals
+// want, or (kind 2) the count int32 at p equal those at ref.
+struct ExpectEntry {
+    const void* p;
+    const void* ref;
+    long long want;
+    int kind;
+    int count;
+};
+constexpr int MAX_EXPECTS = 64;
+
 // Sizes a synchronised build read back; later builds replay with these.
 struct BuildRecord {
     bool valid = false;
@@ -234,6 +245,8 @@ struct ac_ctx {
     ac::BuildRecord rec;
     ac::DevBuf rec_bbox;          // int32 6 x n_mol: bounding boxes of the recorded build
     cudaStream_t cap_stream = nullptr;  // private stream the replay is captured on (never the legacy stream)
+    std::vector<ac::ExpectEntry> expects;  // checks gathered while capturing, run by one kernel at the end
+    ac::DevBuf expect_table;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t graph_exec = nullptr;
     long long graph_launches = 0; // kernels in the graph
@@ -271,6 +284,7 @@ int read_counters(ac_ctx* c, DevCounters* h, cudaStream_t s);
 // from the recorded one.
 int expect_i64(ac_ctx* c, const int64_t* d_value, int64_t want, cudaStream_t s);
 int expect_u64(ac_ctx* c, const unsigned long long* d_value, unsigned long long want, cudaStream_t s);
+int expect_i32s(ac_ctx* c, const int32_t* d_values, const int32_t* d_ref, int64_t count);
 int sync_host(ac_ctx* c, cudaStream_t s);  // cudaStreamSynchronize, counted in the build's stats
 // Record stage event k; under graph capture as an external event node, so the
 // replayed graph records it too.

@@ -194,3 +194,22 @@ def test_rebuild_is_deterministic():
     for d in range(4):
         assert np.array_equal(first[d], gpu.simplices(d).cpu().numpy())
         assert np.array_equal(fv[d], gpu.filtration_values(d).cpu().numpy())
+
+
+def test_star_with_oversized_buckets():
+    """Atom 0 at the centre of 250 atoms on a sphere: 496 tetrahedra, 744 triangles and 250 edges share
+    their first vertex, beyond one warp's sort (256 items), and atom 0 has 250 neighbours (widest rows)."""
+    k = 250
+    i = np.arange(k) + 0.5
+    phi = np.arccos(1 - 2 * i / k)
+    th = np.pi * (1 + 5 ** 0.5) * i
+    pts = np.stack([np.cos(th) * np.sin(phi), np.sin(th) * np.sin(phi), np.cos(phi)], 1) * 2.0
+    c = np.vstack([[0.0, 0.0, 0.0], pts])
+    r = np.full(len(c), 1.0)
+    r[0] = 1.6
+    ref = oracle.alpha_complex(c, r, 0.5)
+    assert (ref.simplices[3][:, 0] == 0).sum() > 256
+    gpu = run_gpu(c, r, 0.5)
+    assert_same_complex(gpu, ref)
+    gpu.build()  # and its replay
+    assert_same_complex(gpu, ref)
