@@ -631,6 +631,39 @@ __global__ void __launch_bounds__(256, 4) k_local(LocalArgs A) {
         // The rows only filter candidates, so they may hold more than the exact
         // relation: |q_e - q_p|^2 rounded down <= (sqrt s_p + sqrt s_e)^2 rounded up
         // keeps every pair whose grown balls meet (and a few more at the margin).
+        if constexpr (WORDS <= 2) {
+            // each lane keeps its columns in registers across the rows
+            float cx[WORDS], cy[WORDS], cz[WORDS], cr[WORDS];
+            bool cv[WORDS];
+#pragma unroll
+            for (int w = 0; w < WORDS; w++) {
+                const int e = 32 * w + lane;
+                cv[w] = w < nw && e < m;
+                const float4 qe = S.qf[cv[w] ? e : 0];
+                cx[w] = qe.x;
+                cy[w] = qe.y;
+                cz[w] = qe.z;
+                cr[w] = S.rs[cv[w] ? e : 0];
+            }
+#pragma unroll 1
+            for (int r = 0; r < n_up; r++) {
+                const int p = S.uplist[r];
+                const float4 qp = S.qf[p];
+                const float rp = S.rs[p];
+#pragma unroll
+                for (int w = 0; w < WORDS; w++) {
+                    const float dx = cx[w] - qp.x, dy = cy[w] - qp.y, dz = cz[w] - qp.z;  // exact: |.| <= 2^14
+                    const float d2 = __fmaf_rd(dz, dz, __fmaf_rd(dy, dy, __fmul_rd(dx, dx)));
+                    const float rr = __fadd_ru(rp, cr[w]);
+                    const bool adj = cv[w] && 32 * w + lane != p && d2 <= __fmul_ru(rr, rr);
+                    const unsigned b = __ballot_sync(FULL, adj);  // words past nw come out empty
+                    if (lane == 0) {
+                        S.Mrow[p][w] = b;
+                        S.Trow[p][w] = 0u;
+                    }
+                }
+            }
+        } else {
 #pragma unroll 1
         for (int r = 0; r < n_up; r++) {
             const int p = S.uplist[r];
@@ -658,6 +691,7 @@ __global__ void __launch_bounds__(256, 4) k_local(LocalArgs A) {
                     S.Mrow[p][w] = 0u;
                     S.Trow[p][w] = 0u;
                 }
+        }
         }
         __syncwarp();
 
