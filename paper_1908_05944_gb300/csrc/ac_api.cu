@@ -553,6 +553,7 @@ static int create_impl(const double* centres, const double* radii, const int64_t
     k_fill_mol<<<(unsigned)n_mol, 256, 0, s>>>(c->d_moloff.as<int64_t>(), n_mol, c->mol_of.as<int32_t>());
     if (cudaGetLastError() != cudaSuccess) return bail(cuda_fail(cudaGetLastError(), "k_fill_mol", __FILE__, __LINE__));
     if ((rc = quantise_and_plan(c, s))) return bail(rc);
+    c->plan_fresh = true;
     *out = c;
     return AC_OK;
 }
@@ -583,7 +584,10 @@ static float elapsed(cudaEvent_t a, cudaEvent_t b) {
 // The whole path on one stream: rows a1-a13 in order.
 static int build_body(ac_ctx* c, cudaStream_t s) {
     AC_TRY(stage_mark(c, 0, s));
-    AC_TRY(quantise_and_plan(c, s));
+    // the inputs were quantised and the grid planned by ac_create: a first
+    // build does not repeat it (every later build, replayed or not, does)
+    if (c->plan_fresh && !c->replaying) c->plan_fresh = false;
+    else AC_TRY(quantise_and_plan(c, s));
     AC_TRY(build_grid(c, s));
     AC_TRY(stage_mark(c, 1, s));
     AC_TRY(build_neighbours(c, s));
@@ -835,6 +839,7 @@ extern "C" int ac_subcomplex(ac_ctx* c, int dim, int64_t mol, double alpha2, uin
 
 extern "C" int ac_autotune(ac_ctx* c, void* stream, ac_options* chosen) {
     if (!c) return fail(AC_ERR_INVALID_ARG, "ctx is NULL");
+    c->plan_fresh = false;  // every trial plans its own grid
     // grid cell side (in units of h) and warps per block of the per-atom kernel
     const double factors[4] = {1.0, 1.25, 1.5, 2.0};
     const int warps[3] = {4, 6, 8};

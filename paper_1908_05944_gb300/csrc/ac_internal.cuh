@@ -186,6 +186,7 @@ struct ac_ctx {
     ac_options opt{};
     ac::PredConst pc{};
     bool built = false;
+    bool plan_fresh = false;  // ac_create just quantised and planned; the first build reuses that
 
     // inputs
     ac::DevBuf centres;  // double n x 3 (input order)

@@ -540,7 +540,9 @@ __global__ void __launch_bounds__(256, 4) k_local(LocalArgs A) {
                 const int4 o = A.Ps[x];
                 const int qx = o.x - Pi.x, qy = o.y - Pi.y, qz = o.z - Pi.z;
                 S.idx[e] = x;
-                S.ai[e] = qx * qx + qy * qy + qz * qz;  // <= 2^26
+                const int D = qx * qx + qy * qy + qz * qz;  // in (0, 2^26]
+                // narrow rows: one 32-bit key D * 64 + e, unique (D = 2^26 wraps to e, below every other key)
+                S.ai[e] = WORDS <= 2 ? (int)((unsigned)D * 64u + (unsigned)e) : D;
             }
         }
         __syncwarp();
@@ -553,10 +555,15 @@ __global__ void __launch_bounds__(256, 4) k_local(LocalArgs A) {
             if (w < nw && e < m) {
                 const int De = S.ai[e];
                 int rank = 0;
+                if constexpr (WORDS <= 2) {
 #pragma unroll 4
-                for (int f = 0; f < m; f++) {
-                    const int Df = S.ai[f];
-                    rank += (Df < De || (Df == De && f < e)) ? 1 : 0;
+                    for (int f = 0; f < m; f++) rank += (unsigned)S.ai[f] < (unsigned)De ? 1 : 0;
+                } else {
+#pragma unroll 4
+                    for (int f = 0; f < m; f++) {
+                        const int Df = S.ai[f];
+                        rank += (Df < De || (Df == De && f < e)) ? 1 : 0;
+                    }
                 }
                 xr[w] = S.idx[e];
                 rr[w] = rank;
