@@ -818,100 +818,149 @@ __global__ void __launch_bounds__(256, 4) k_local(LocalArgs A) {
         }
         __syncwarp();
         const int n_pairs = use_list ? S.n_pl : S.rowpre[n_up];
+        // pair j of the enumeration: from the list, or located in the T rows
+        auto pair_code = [&](int j) -> unsigned {
+            if (use_list) return S.plist[j];
+            const int r = row_of(S.rowpre, n_up, j);
+            const int p = S.uplist[r];
+            const int k = nth_in_words(nw, j - S.rowpre[r], [&](int w) { return S.Trow[p][w]; });
+            return (unsigned)(p | (k << 8));
+        };
+        // AC3 then AC2 for the batch of candidate codes in cand[0, nbatch), 32 per window
+        auto tet_windows = [&](int nbatch) {
 #pragma unroll 1
-        for (int c0 = 0; c0 < n_pairs; c0 += PAIR_CHUNK) {
-            const int cn = min(PAIR_CHUNK, n_pairs - c0);
-            {
-                int run = 0;
-                for (int q0 = 0; q0 < cn; q0 += 32) {
-                    int c = 0;
-                    if (q0 + lane < cn) {
-                        const int j = c0 + q0 + lane;
-                        int p, k;
-                        if (use_list) {
-                            const unsigned code = S.plist[j];
-                            p = code & 255u;
-                            k = code >> 8;
-                        } else {
-                            // the list is not used: its first PAIR_CHUNK slots hold this chunk
-                            const int r = row_of(S.rowpre, n_up, j);
-                            p = S.uplist[r];
-                            k = nth_in_words(nw, j - S.rowpre[r], [&](int w) { return S.Trow[p][w]; });
-                            S.plist[q0 + lane] = (unsigned short)(p | (k << 8));
-                        }
-                        for (int w = 0; w < nw; w++) c += __popc(S.Trow[p][w] & S.Trow[k][w]);
+            for (int base = 0; base < nbatch; base += 32) {
+                const int j = base + lane;
+                const bool valid = j < nbatch;
+                bool pass = false, pend = false, keep_it = false;
+                int pend_ac3 = 0;
+                int p3 = 0, k3 = 0, ll = 0;
+                Ortho<R> o;
+                o.ac3 = -1;
+                if (valid) {
+                    const unsigned code = S.cand[j];
+                    p3 = code & 255u;
+                    k3 = (code >> 8) & 255u;
+                    ll = code >> 16;
+                    n_ac3k++;
+                    o = ortho_tet<R>(point<R>(S, p3), point<R>(S, k3), point<R>(S, ll), T, B);
+                    if (o.ac3 > 0) {
+                        n_s3++;
+                        keep_it = true;
+                    } else if (o.ac3 == 0) {
+                        pend = true;
+                        pend_ac3 = 1;
                     }
-                    int tot;
-                    const int ex = warp_excl(lane, c, &tot);
-                    if (q0 + lane < cn) S.pairpre[q0 + lane] = run + ex;
-                    run += tot;
                 }
-                if (lane == 0) S.pairpre[cn] = run;
+                {
+                    const int r3 = keep_it ? ac2_scan<R>(S, nw, o, B, 3, p3, k3, ll, n_tet) : 1;
+                    if (keep_it) {
+                        pass = r3 > 0;
+                        pend = r3 == 0;
+                    }
+                }
+                const int4 item = make_int4(i, valid ? S.idx[p3] : 0, valid ? S.idx[k3] : 0, valid ? S.idx[ll] : 0);
+                if (keep)
+                    append_direct(keep_it, item, A.cand3, &cnt->n_cand_out[3], A.cap_cand[3], &cnt->err,
+                                  DERR_OVF_CAND);
+                append_direct(pend, make_int4(pend_ac3 ? ~i : i, item.y, item.z, item.w), A.pending, &cnt->n_pending,
+                              A.cap_pending, &cnt->err, DERR_OVF_PEND);
+                stage_push(lane, pass, item, S.st_tet, &S.n_tet, A.tet_out, &cnt->n_tet_out, A.cap_tet, &cnt->err,
+                           DERR_OVF_TET);
             }
             __syncwarp();
-            const int total = S.pairpre[cn];
+        };
+        if constexpr (WORDS <= 2) {
+            // narrow rows: a lane takes PAIRS_PER_LANE consecutive pairs and keeps their
+            // candidate masks T[p] & T[k] in registers; a prefix over the lanes places
+            // its candidates in enumeration order
+            constexpr int PPL = 2;
 #pragma unroll 1
-            for (int done = 0; done < total; done += CAND_CAP) {
-                for (int q = lane; q < cn; q += 32) {
-                    const int a0 = S.pairpre[q], a1 = S.pairpre[q + 1];
-                    if (a1 <= done || a0 >= done + CAND_CAP) continue;
-                    const unsigned code = S.plist[(use_list ? c0 : 0) + q];
-                    const int p = code & 255u, k = code >> 8;
-                    int t = a0;
-                    for (int w = 0; w < nw; w++) {
-                        unsigned b = S.Trow[p][w] & S.Trow[k][w];
-                        while (b) {
-                            const int l = 32 * w + __ffs(b) - 1;
-                            b &= b - 1;
-                            if (t >= done && t < done + CAND_CAP) S.cand[t - done] = code | ((unsigned)l << 16);
-                            t++;
-                        }
+            for (int c0 = 0; c0 < n_pairs; c0 += 32 * PPL) {
+                unsigned code[PPL], mk0[PPL], mk1[PPL];
+                int mine = 0;
+#pragma unroll
+                for (int t = 0; t < PPL; t++) {
+                    const int j = c0 + PPL * lane + t;
+                    code[t] = 0u;
+                    mk0[t] = mk1[t] = 0u;
+                    if (j < n_pairs) {
+                        code[t] = pair_code(j);
+                        const int p = code[t] & 255u, k = code[t] >> 8;
+                        mk0[t] = S.Trow[p][0] & S.Trow[k][0];
+                        if (WORDS > 1) mk1[t] = S.Trow[p][WORDS - 1] & S.Trow[k][WORDS - 1];
+                        mine += __popc(mk0[t]) + __popc(mk1[t]);
                     }
                 }
-                __syncwarp();
-                const int nbatch = min(CAND_CAP, total - done);
+                int total;
+                const int ex = warp_excl(lane, mine, &total);
 #pragma unroll 1
-                for (int base = 0; base < nbatch; base += 32) {
-                    const int j = base + lane;
-                    const bool valid = j < nbatch;
-                    bool pass = false, pend = false, keep_it = false;
-                    int pend_ac3 = 0;
-                    int p3 = 0, k3 = 0, ll = 0;
-                    Ortho<R> o;
-                    o.ac3 = -1;
-                    if (valid) {
-                        const unsigned code = S.cand[j];
-                        p3 = code & 255u;
-                        k3 = (code >> 8) & 255u;
-                        ll = code >> 16;
-                        n_ac3k++;
-                        o = ortho_tet<R>(point<R>(S, p3), point<R>(S, k3), point<R>(S, ll), T, B);
-                        if (o.ac3 > 0) {
-                            n_s3++;
-                            keep_it = true;
-                        } else if (o.ac3 == 0) {
-                            pend = true;
-                            pend_ac3 = 1;
+                for (int done = 0; done < total; done += CAND_CAP) {
+                    if (ex < done + CAND_CAP && ex + mine > done) {
+                        int t = ex;
+#pragma unroll
+                        for (int u = 0; u < PPL; u++) {
+#pragma unroll
+                            for (int w = 0; w < WORDS; w++) {
+                                unsigned b = w == 0 ? mk0[u] : mk1[u];
+                                while (b) {
+                                    const int l = 32 * w + __ffs(b) - 1;
+                                    b &= b - 1;
+                                    if (t >= done && t < done + CAND_CAP)
+                                        S.cand[t - done] = code[u] | ((unsigned)l << 16);
+                                    t++;
+                                }
+                            }
                         }
                     }
-                    {
-                        const int r3 = keep_it ? ac2_scan<R>(S, nw, o, B, 3, p3, k3, ll, n_tet) : 1;
-                        if (keep_it) {
-                            pass = r3 > 0;
-                            pend = r3 == 0;
+                    __syncwarp();
+                    tet_windows(min(CAND_CAP, total - done));
+                }
+            }
+        } else {
+#pragma unroll 1
+            for (int c0 = 0; c0 < n_pairs; c0 += PAIR_CHUNK) {
+                const int cn = min(PAIR_CHUNK, n_pairs - c0);
+                {
+                    int run = 0;
+                    for (int q0 = 0; q0 < cn; q0 += 32) {
+                        int c = 0;
+                        if (q0 + lane < cn) {
+                            const unsigned code = pair_code(c0 + q0 + lane);
+                            const int p = code & 255u, k = code >> 8;
+                            if (!use_list) S.plist[q0 + lane] = (unsigned short)code;  // chunk-local copy
+                            for (int w = 0; w < nw; w++) c += __popc(S.Trow[p][w] & S.Trow[k][w]);
                         }
+                        int tot;
+                        const int ex = warp_excl(lane, c, &tot);
+                        if (q0 + lane < cn) S.pairpre[q0 + lane] = run + ex;
+                        run += tot;
                     }
-                    const int4 item =
-                        make_int4(i, valid ? S.idx[p3] : 0, valid ? S.idx[k3] : 0, valid ? S.idx[ll] : 0);
-                    if (keep)
-                        append_direct(keep_it, item, A.cand3, &cnt->n_cand_out[3], A.cap_cand[3], &cnt->err,
-                                      DERR_OVF_CAND);
-                    append_direct(pend, make_int4(pend_ac3 ? ~i : i, item.y, item.z, item.w), A.pending,
-                                  &cnt->n_pending, A.cap_pending, &cnt->err, DERR_OVF_PEND);
-                    stage_push(lane, pass, item, S.st_tet, &S.n_tet, A.tet_out, &cnt->n_tet_out, A.cap_tet, &cnt->err,
-                               DERR_OVF_TET);
+                    if (lane == 0) S.pairpre[cn] = run;
                 }
                 __syncwarp();
+                const int total = S.pairpre[cn];
+#pragma unroll 1
+                for (int done = 0; done < total; done += CAND_CAP) {
+                    for (int q = lane; q < cn; q += 32) {
+                        const int a0 = S.pairpre[q], a1 = S.pairpre[q + 1];
+                        if (a1 <= done || a0 >= done + CAND_CAP) continue;
+                        const unsigned code = S.plist[(use_list ? c0 : 0) + q];
+                        const int p = code & 255u, k = code >> 8;
+                        int t = a0;
+                        for (int w = 0; w < nw; w++) {
+                            unsigned b = S.Trow[p][w] & S.Trow[k][w];
+                            while (b) {
+                                const int l = 32 * w + __ffs(b) - 1;
+                                b &= b - 1;
+                                if (t >= done && t < done + CAND_CAP) S.cand[t - done] = code | ((unsigned)l << 16);
+                                t++;
+                            }
+                        }
+                    }
+                    __syncwarp();
+                    tet_windows(min(CAND_CAP, total - done));
+                }
             }
         }
 
