@@ -130,32 +130,40 @@ __global__ void k_neighbours(const int4* __restrict__ Ps, const int32_t* __restr
             for (int y = y0; y <= y1; y++) {
                 int64_t row = g.cell_base + ((int64_t)z * g.dims[1] + y) * g.dims[0];
                 uint32_t a = cell_start[row + x0], b = cell_start[row + x1 + 1];
-                for (uint32_t t = a; t < b; t++) {
-                    if (t == (uint32_t)s) continue;
-                    int4 o = Ps[t];
-                    int64_t dx, dy, dz;
-                    if (GUARD) {
-                        dx = (int64_t)o.x - p.x;
-                        dy = (int64_t)o.y - p.y;
-                        dz = (int64_t)o.z - p.z;
-                        // grown balls meet only within 2h <= 2^13 quanta per axis
-                        const int64_t lim = 1 << 20;
-                        if (dx >= lim || dx <= -lim || dy >= lim || dy <= -lim || dz >= lim || dz <= -lim) continue;
-                    } else {
-                        // the stencil spans less than 2^29 quanta: 32-bit differences, squares below 2^58
-                        dx = o.x - p.x;
-                        dy = o.y - p.y;
-                        dz = o.z - p.z;
+                // four candidates per step: their loads are issued together
+                for (uint32_t t0 = a; t0 < b; t0 += 4) {
+                    int4 ov[4];
+#pragma unroll
+                    for (int u = 0; u < 4; u++) ov[u] = Ps[t0 + u < b ? t0 + u : a];
+#pragma unroll
+                    for (int u = 0; u < 4; u++) {
+                        const uint32_t t = t0 + u;
+                        if (t >= b || t == (uint32_t)s) continue;
+                        const int4 o = ov[u];
+                        int64_t dx, dy, dz;
+                        if (GUARD) {
+                            dx = (int64_t)o.x - p.x;
+                            dy = (int64_t)o.y - p.y;
+                            dz = (int64_t)o.z - p.z;
+                            // grown balls meet only within 2h <= 2^13 quanta per axis
+                            const int64_t lim = 1 << 20;
+                            if (dx >= lim || dx <= -lim || dy >= lim || dy <= -lim || dz >= lim || dz <= -lim) continue;
+                        } else {
+                            // the stencil spans less than 2^29 quanta: 32-bit differences, squares below 2^58
+                            dx = o.x - p.x;
+                            dy = o.y - p.y;
+                            dz = o.z - p.z;
+                        }
+                        if (dx == 0 && dy == 0 && dz == 0) {
+                            atomicOr(&cnt->err, DERR_COINCIDENT);
+                            continue;
+                        }
+                        const int64_t D = dx * dx + dy * dy + dz * dz;
+                        const int64_t sx = (int64_t)o.w + pc.A;
+                        if (sx < 0 || !grown_meet(D, si, sx)) continue;
+                        if (FILL) nb[w + count] = (int32_t)t;
+                        count++;
                     }
-                    if (dx == 0 && dy == 0 && dz == 0) {
-                        atomicOr(&cnt->err, DERR_COINCIDENT);
-                        continue;
-                    }
-                    int64_t D = dx * dx + dy * dy + dz * dz;
-                    int64_t sx = (int64_t)o.w + pc.A;
-                    if (sx < 0 || !grown_meet(D, si, sx)) continue;
-                    if (FILL) nb[w + count] = (int32_t)t;
-                    count++;
                 }
             }
     }
