@@ -669,6 +669,7 @@ static int record_build(ac_ctx* c, const DevCounters& post, cudaStream_t s) {
     r.opt = c->opt;
     r.wmax = (int)(c->pc.H2 - c->pc.A);
     r.nb_total = c->nb_total;
+    r.nb_stride = c->nb_stride;
     r.n_wide = c->n_wide;
     r.post = post;
     r.post.err = 0;
@@ -702,8 +703,8 @@ extern "C" int ac_build(ac_ctx* c, void* stream) {
         if (c->graph_exec) {
             AC_CUDA(cudaGraphLaunch(c->graph_exec, s));
             AC_TRY(read_counters(c, &h, s));
-            if (h.err & DERR_REPLAY) {
-                // a size moved: forget the graph and build with readbacks
+            if (h.err & (DERR_REPLAY | DERR_DEGREE)) {
+                // a size moved (or a row outgrew the recorded masks): forget the graph and build with readbacks
                 drop_graph(c);
                 c->rec.valid = false;
                 unsigned zero = 0;

@@ -109,67 +109,86 @@ __device__ __forceinline__ bool grown_meet(int64_t D, int64_t si, int64_t sx) {
 
 // GUARD: the stencil may span 2^29 quanta or more (very coarse cells), so a
 // pair's coordinate differences are bounded before the 64-bit squares.
-template <bool FILL, bool GUARD>
+// MODE: NB_COUNT counts L(i); NB_CSR writes it at the offsets nb_off (a scan of
+// the counts); NB_PADDED counts it and writes its first NB_STRIDE entries to the
+// row nb[s * NB_STRIDE ..] in the same pass.
+enum { NB_COUNT = 0, NB_CSR = 1, NB_PADDED = 2 };
+
+struct GridView {
+    const int4* Ps;
+    const int32_t* mol_s;
+    const MolGrid* grids;
+    const uint32_t* cell_start;
+};
+
+template <int MODE, bool GUARD>
 __global__ void k_neighbours(const int4* __restrict__ Ps, const int32_t* __restrict__ mol_s,
                              const MolGrid* __restrict__ grids, const uint32_t* __restrict__ cell_start,
                              PredConst pc, int64_t n, int64_t* __restrict__ nb_cnt, const int64_t* __restrict__ nb_off,
                              int32_t* __restrict__ nb, DevCounters* __restrict__ cnt) {
-    int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= n) return;
-    int4 p = Ps[s];
-    int64_t si = (int64_t)p.w + pc.A;
-    int64_t count = 0, w = FILL ? nb_off[s] : 0;
-    if (si >= 0) {
-        MolGrid g = grids[mol_s[s]];
-        const int cell = pc.cell, R = pc.reach;
-        int cx = (p.x - g.org[0]) / cell, cy = (p.y - g.org[1]) / cell, cz = (p.z - g.org[2]) / cell;
-        int z0 = max(cz - R, 0), z1 = min(cz + R, g.dims[2] - 1);
-        int y0 = max(cy - R, 0), y1 = min(cy + R, g.dims[1] - 1);
-        int x0 = max(cx - R, 0), x1 = min(cx + R, g.dims[0] - 1);
-        for (int z = z0; z <= z1; z++)
-            for (int y = y0; y <= y1; y++) {
-                int64_t row = g.cell_base + ((int64_t)z * g.dims[1] + y) * g.dims[0];
-                uint32_t a = cell_start[row + x0], b = cell_start[row + x1 + 1];
-                // four candidates per step: their loads are issued together
-                for (uint32_t t0 = a; t0 < b; t0 += 4) {
-                    int4 ov[4];
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t count = 0;
+    if (s < n) {
+        int4 p = Ps[s];
+        int64_t si = (int64_t)p.w + pc.A;
+        const int64_t w = MODE == NB_CSR ? nb_off[s] : MODE == NB_PADDED ? s * NB_STRIDE : 0;
+        if (si >= 0) {
+            MolGrid g = grids[mol_s[s]];
+            const int cell = pc.cell, R = pc.reach;
+            int cx = (p.x - g.org[0]) / cell, cy = (p.y - g.org[1]) / cell, cz = (p.z - g.org[2]) / cell;
+            int z0 = max(cz - R, 0), z1 = min(cz + R, g.dims[2] - 1);
+            int y0 = max(cy - R, 0), y1 = min(cy + R, g.dims[1] - 1);
+            int x0 = max(cx - R, 0), x1 = min(cx + R, g.dims[0] - 1);
+            for (int z = z0; z <= z1; z++)
+                for (int y = y0; y <= y1; y++) {
+                    int64_t row = g.cell_base + ((int64_t)z * g.dims[1] + y) * g.dims[0];
+                    uint32_t a = cell_start[row + x0], b = cell_start[row + x1 + 1];
+                    // four candidates per step: their loads are issued together
+                    for (uint32_t t0 = a; t0 < b; t0 += 4) {
+                        int4 ov[4];
 #pragma unroll
-                    for (int u = 0; u < 4; u++) ov[u] = Ps[t0 + u < b ? t0 + u : a];
+                        for (int u = 0; u < 4; u++) ov[u] = Ps[t0 + u < b ? t0 + u : a];
 #pragma unroll
-                    for (int u = 0; u < 4; u++) {
-                        const uint32_t t = t0 + u;
-                        if (t >= b || t == (uint32_t)s) continue;
-                        const int4 o = ov[u];
-                        int64_t dx, dy, dz;
-                        if (GUARD) {
-                            dx = (int64_t)o.x - p.x;
-                            dy = (int64_t)o.y - p.y;
-                            dz = (int64_t)o.z - p.z;
-                            // grown balls meet only within 2h <= 2^13 quanta per axis
-                            const int64_t lim = 1 << 20;
-                            if (dx >= lim || dx <= -lim || dy >= lim || dy <= -lim || dz >= lim || dz <= -lim) continue;
-                        } else {
-                            // the stencil spans less than 2^29 quanta: 32-bit differences, squares below 2^58
-                            dx = o.x - p.x;
-                            dy = o.y - p.y;
-                            dz = o.z - p.z;
+                        for (int u = 0; u < 4; u++) {
+                            const uint32_t t = t0 + u;
+                            if (t >= b || t == (uint32_t)s) continue;
+                            const int4 o = ov[u];
+                            int64_t dx, dy, dz;
+                            if (GUARD) {
+                                dx = (int64_t)o.x - p.x;
+                                dy = (int64_t)o.y - p.y;
+                                dz = (int64_t)o.z - p.z;
+                                // grown balls meet only within 2h <= 2^13 quanta per axis
+                                const int64_t lim = 1 << 20;
+                                if (dx >= lim || dx <= -lim || dy >= lim || dy <= -lim || dz >= lim || dz <= -lim) continue;
+                            } else {
+                                // the stencil spans less than 2^29 quanta: 32-bit differences, squares below 2^58
+                                dx = o.x - p.x;
+                                dy = o.y - p.y;
+                                dz = o.z - p.z;
+                            }
+                            if (dx == 0 && dy == 0 && dz == 0) {
+                                atomicOr(&cnt->err, DERR_COINCIDENT);
+                                continue;
+                            }
+                            const int64_t D = dx * dx + dy * dy + dz * dz;
+                            const int64_t sx = (int64_t)o.w + pc.A;
+                            if (sx < 0 || !grown_meet(D, si, sx)) continue;
+                            if (MODE == NB_CSR || (MODE == NB_PADDED && count < NB_STRIDE)) nb[w + count] = (int32_t)t;
+                            count++;
                         }
-                        if (dx == 0 && dy == 0 && dz == 0) {
-                            atomicOr(&cnt->err, DERR_COINCIDENT);
-                            continue;
-                        }
-                        const int64_t D = dx * dx + dy * dy + dz * dz;
-                        const int64_t sx = (int64_t)o.w + pc.A;
-                        if (sx < 0 || !grown_meet(D, si, sx)) continue;
-                        if (FILL) nb[w + count] = (int32_t)t;
-                        count++;
                     }
                 }
-            }
+        }
+        if (MODE != NB_CSR) {
+            nb_cnt[s] = count;
+            atomicMax(&cnt->max_degree, (int)count);
+        }
     }
-    if (!FILL) {
-        nb_cnt[s] = count;
-        atomicMax(&cnt->max_degree, (int)count);
+    if (MODE != NB_CSR) {
+        // every lane of the warp reaches here (no early exit above)
+        const unsigned tot = __reduce_add_sync(0xffffffffu, (unsigned)count);
+        if ((threadIdx.x & 31) == 0 && tot) atomicAdd(&cnt->nb_sum, (unsigned long long)tot);
     }
 }
 
@@ -218,6 +237,10 @@ __global__ void k_deg_scatter(const int64_t* __restrict__ cnt, int64_t n, unsign
     if (i < n) work[base[b] + local] = (int32_t)i;
 }
 
+// L(i) for every atom. With at most NB_STRIDE neighbours per atom (always so
+// for atomic radii and a 1.4 A probe) one pass counts and writes padded rows;
+// otherwise the counts are scanned into offsets and a second pass writes the
+// compact lists. The work order of the per-atom pass comes from the counts.
 int build_neighbours(ac_ctx* c, cudaStream_t s) {
     const int64_t n = c->n;
     AC_TRY(c->nb_cnt.reserve((size_t)(n + 1) * sizeof(int64_t), s));
@@ -225,6 +248,7 @@ int build_neighbours(ac_ctx* c, cudaStream_t s) {
     if (n == 0) {
         c->nb_total = 0;
         c->n_wide = 0;
+        c->nb_stride = 0;
         AC_CUDA(cudaMemsetAsync(cntp, 0, sizeof(int64_t), s));
         AC_TRY(c->nb.reserve(4, s));
         return AC_OK;
@@ -232,12 +256,19 @@ int build_neighbours(ac_ctx* c, cudaStream_t s) {
     const unsigned nb = (unsigned)((n + 127) / 128);
     DevCounters* dc = c->counters.as<DevCounters>();
     const bool guard = (int64_t)c->pc.cell * (2 * c->pc.reach + 1) >= ((int64_t)1 << 29);
-    auto k_count = guard ? k_neighbours<false, true> : k_neighbours<false, false>;
-    auto k_fill = guard ? k_neighbours<true, true> : k_neighbours<true, false>;
-    k_count<<<nb, 128, 0, s>>>(c->Ps.as<int4>(), c->mol_s.as<int32_t>(), c->grids.as<MolGrid>(),
-                                           c->cell_start.as<uint32_t>(), c->pc, n, cntp, nullptr, nullptr, dc);
+    // a replay keeps the recorded layout; a synchronised build tries the padded one
+    const bool padded = c->replaying ? c->rec.nb_stride == NB_STRIDE : true;
+    const GridView g{c->Ps.as<int4>(), c->mol_s.as<int32_t>(), c->grids.as<MolGrid>(), c->cell_start.as<uint32_t>()};
+    if (padded) {
+        AC_TRY(c->nb.reserve((size_t)n * NB_STRIDE * sizeof(int32_t), s));
+        auto k = guard ? k_neighbours<NB_PADDED, true> : k_neighbours<NB_PADDED, false>;
+        k<<<nb, 128, 0, s>>>(g.Ps, g.mol_s, g.grids, g.cell_start, c->pc, n, cntp, nullptr, c->nb.as<int32_t>(), dc);
+    } else {
+        auto k = guard ? k_neighbours<NB_COUNT, true> : k_neighbours<NB_COUNT, false>;
+        k<<<nb, 128, 0, s>>>(g.Ps, g.mol_s, g.grids, g.cell_start, c->pc, n, cntp, nullptr, nullptr, dc);
+    }
     AC_LAUNCHED();
-    // work order from the counts (before the in-place scan turns them into offsets)
+    // work order from the counts (before a scan turns them into offsets)
     AC_TRY(c->work.reserve((size_t)n * sizeof(int32_t), s));
     AC_TRY(c->deg.reserve(2 * DEG_BINS * sizeof(unsigned) + 64, s));
     unsigned* hist = c->deg.as<unsigned>();
@@ -250,28 +281,32 @@ int build_neighbours(ac_ctx* c, cudaStream_t s) {
     AC_LAUNCHED();
     k_deg_scatter<<<nb, 128, 0, s>>>(cntp, n, cursor, c->work.as<int32_t>());
     AC_LAUNCHED();
-    AC_TRY(scan_exclusive_i64(c, cntp, cntp, n, s));
     int64_t total = 0;
+    bool compact = !padded;
     if (c->replaying) {
         // sizes of the recorded build, checked on the device
         total = c->rec.nb_total;
         c->n_wide = c->rec.n_wide;
-        AC_TRY(expect_i64(c, cntp + n, total, s));
+        AC_TRY(expect_u64(c, &dc->nb_sum, (unsigned long long)total, s));
         AC_TRY(expect_i64(c, reinterpret_cast<const int64_t*>(n_wide), c->n_wide, s));
     } else {
-        AC_CUDA(cudaMemcpyAsync(c->h_stage, cntp + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
         AC_CUDA(cudaMemcpyAsync(c->h_stage + 1, n_wide, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
         DevCounters h;
-        AC_TRY(read_counters(c, &h, s));  // also completes the copies above
-        total = c->h_stage[0];
+        AC_TRY(read_counters(c, &h, s));  // also completes the copy above
+        total = (int64_t)h.nb_sum;
         c->n_wide = c->h_stage[1];
         if (h.err & DERR_COINCIDENT)
             return fail(AC_ERR_DEGENERATE, "two centres coincide after quantisation to 1/1024 A");
+        if (h.max_degree > NB_STRIDE) compact = true;  // rows too short: redo as compact lists
     }
     c->nb_total = total;
+    c->nb_stride = compact ? 0 : NB_STRIDE;
+    if (!compact) return AC_OK;
+    AC_TRY(scan_exclusive_i64(c, cntp, cntp, n, s));
+    if (c->replaying) AC_TRY(expect_i64(c, cntp + n, total, s));
     AC_TRY(c->nb.reserve((size_t)(total > 0 ? total : 1) * sizeof(int32_t), s));
-    k_fill<<<nb, 128, 0, s>>>(c->Ps.as<int4>(), c->mol_s.as<int32_t>(), c->grids.as<MolGrid>(),
-                                          c->cell_start.as<uint32_t>(), c->pc, n, nullptr, cntp, c->nb.as<int32_t>(), dc);
+    auto k_fill = guard ? k_neighbours<NB_CSR, true> : k_neighbours<NB_CSR, false>;
+    k_fill<<<nb, 128, 0, s>>>(g.Ps, g.mol_s, g.grids, g.cell_start, c->pc, n, nullptr, cntp, c->nb.as<int32_t>(), dc);
     AC_LAUNCHED();
     return AC_OK;
 }

@@ -113,7 +113,12 @@ struct DevCounters {
     int max_degree;
     int bad_index;
     int pad;
+    unsigned long long nb_sum;        // neighbour pairs counted (sum of |L(i)|)
 };
+
+// Row length of the padded neighbour layout: L(i) at nb[i * NB_STRIDE ..]
+// when no atom has more neighbours, else a compact list at scanned offsets.
+constexpr int NB_STRIDE = 128;
 
 // Grid of one molecule: origin (quanta), cell side, dims, first global cell.
 struct MolGrid {
@@ -172,6 +177,7 @@ struct BuildRecord {
     ac_options opt{};
     int wmax = 0;
     int64_t nb_total = 0, n_wide = 0;
+    int nb_stride = 0;      // layout of the neighbour lists (0: compact)
     int64_t n_pending = 0;  // escalated simplices before the resolve kernel
     DevCounters post{};     // counters after the resolve kernel
     int64_t count[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // K^0..K^3 rows, then Sigma^1..Sigma^3 rows
@@ -207,9 +213,12 @@ struct ac_ctx {
     ac::DevBuf mol_s;     // int32 molecule, sorted
 
     // neighbour lists (sorted positions)
-    ac::DevBuf nb_cnt;   // int64 n+1 (counts, then exclusive offsets)
+    // nb_stride == NB_STRIDE: counts in nb_cnt, L(i) at nb[i * NB_STRIDE];
+    // nb_stride == 0: nb_cnt holds exclusive offsets (n + 1) into a compact nb
+    ac::DevBuf nb_cnt;   // int64 n+1
     ac::DevBuf nb;       // int32
     int64_t nb_total = 0;
+    int nb_stride = 0;
 
     // per-atom pass outputs (sorted positions)
     ac::DevBuf tet_out;   // int4

@@ -123,8 +123,11 @@ struct Bounds {
 struct LocalArgs {
     const int4* Ps;
     const int32_t* order;
+    // L(i): nb[i * nb_stride ..], nb_off[i] entries, when nb_stride > 0;
+    // else nb[nb_off[i] .. nb_off[i + 1]]
     const int64_t* nb_off;
     const int32_t* nb;
+    int nb_stride;
     int64_t n;
     // Work of one launch: the atoms work[0..n-1], taken through work_next (or
     // work_next2 when counter2 is set, for a launch running beside another).
@@ -515,13 +518,13 @@ __global__ void __launch_bounds__(256, 4) k_local(LocalArgs A) {
         const int Wi = Pi.w;
         const long long si = (long long)Wi + Aq;
         const int gi = A.order[i];
-        const int64_t off = A.nb_off[i];
-        const int m = (int)(A.nb_off[i + 1] - off);
+        const int64_t off = A.nb_stride ? (int64_t)i * A.nb_stride : A.nb_off[i];
+        const int m = (int)(A.nb_stride ? A.nb_off[i] : A.nb_off[i + 1] - off);
         if (si < 0) {
             if (lane == 0) A.vert_pass[i] = 0;
             continue;
         }
-        if (m > MAXM) {
+        if (m > MAXM || (A.nb_stride && m > A.nb_stride)) {
             if (lane == 0) atomicOr(&cnt->err, DERR_DEGREE);
             continue;
         }
@@ -1114,14 +1117,21 @@ __global__ void k_resolve(LocalArgs A, int64_t n_pending) {
         E = A.tet_eps64;
     }
     // candidates: neighbours of i adjacent to every vertex
-    const int64_t off = A.nb_off[i];
-    const int m = (int)(A.nb_off[i + 1] - off);
+    const int64_t off = A.nb_stride ? (int64_t)i * A.nb_stride : A.nb_off[i];
+    const int m = A.nb_stride ? min((int)A.nb_off[i], A.nb_stride) : (int)(A.nb_off[i + 1] - off);
     unsigned n64 = 0, nx = 0;
     bool violated = false;
+    // the next candidate's record is fetched while this one is tested
+    int x_next = m > 0 ? A.nb[off] : 0;
+    int4 P_next = m > 0 ? A.Ps[x_next] : make_int4(0, 0, 0, 0);
     for (int e = 0; e < m && !violated; e++) {
-        const int x = A.nb[off + e];
+        const int x = x_next;
+        const int4 Px = P_next;
+        if (e + 1 < m) {
+            x_next = A.nb[off + e + 1];
+            P_next = A.Ps[x_next];
+        }
         if (x == v[0] || (nv >= 2 && x == v[1]) || (nv == 3 && x == v[2])) continue;
-        const int4 Px = A.Ps[x];
         const long long sx = (long long)Px.w + Aq;
         const long long qx[3] = {(long long)Px.x - Pi.x, (long long)Px.y - Pi.y, (long long)Px.z - Pi.z};
         bool adj = true;
@@ -1358,6 +1368,7 @@ int run_local(ac_ctx* c, cudaStream_t s) {
         a.order = c->order.as<int32_t>();
         a.nb_off = c->nb_cnt.as<int64_t>();
         a.nb = c->nb.as<int32_t>();
+        a.nb_stride = c->nb_stride;
         a.n = n;
         a.pc = c->pc;
         set_constants(c->pc, wmax, a);
