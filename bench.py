@@ -290,6 +290,30 @@ def run_forms(args):
                                "local_frac_fp32_peak_2070mhz": tf / (SMS * FP32_LANES_PER_SM * 2 * 2070e6 / 1e12)}
         cx.close()
         del cx
+    # out-of-core build (Section 4.6): host arrays in, host lists out, z-slabs of at most max_core atoms
+    # plus halo on the device at a time; against one whole-molecule build with the same host round trip
+    c3, r3 = workload("shell3m_probe")
+    t0 = time.perf_counter()
+    whole = ac.AlphaComplex(c3, r3, 0.0).build(stream)
+    host = [(whole.simplices(d).cpu().numpy(), whole.attached(d).cpu().numpy(),
+             whole.filtration_values(d).cpu().numpy()) for d in range(4)]
+    whole_s = time.perf_counter() - t0
+    whole.close()
+    del whole
+    for max_core in (1_000_000, 250_000):
+        t0 = time.perf_counter()
+        ch = ac.ChunkedComplex(c3, r3, 0.0, max_core, stream=stream)
+        chunk_s = time.perf_counter() - t0
+        st = ch.stats()
+        equal = all(np.array_equal(ch.simplices(d), host[d][0]) and np.array_equal(ch.attached(d), host[d][1])
+                    and np.array_equal(ch.filtration_values(d), host[d][2]) for d in range(4))
+        out[f"shell3m_probe/chunked_{max_core}"] = {
+            "atoms_per_s": len(r3) / chunk_s, "wall_ms": chunk_s * 1e3, "n_chunks": st["n_chunks"],
+            "subset_max": st["subset_max"], "halo_overhead": st["subset_total"] / len(r3) - 1.0,
+            "ms_plan": st["ms_plan"], "ms_device": st["ms_device"], "ms_assemble": st["ms_assemble"],
+            "equal_to_whole_build": bool(equal), "whole_build_host_round_trip_ms": whole_s * 1e3}
+        del ch
+    del host
     # batch: one context over all molecules vs one context per molecule
     sizes = synth.batch_sizes(4, 1024)
     mols = [synth.globule(1000 + m, int(n), probe=True) for m, n in enumerate(sizes)]

@@ -229,6 +229,81 @@ AC_API int ac_autotune(ac_ctx* ctx, void* stream, ac_options* chosen);
 AC_API int ac_subcomplex(ac_ctx* ctx, int dim, int64_t mol, double alpha2, uint8_t* d_flags, int64_t* count_in,
                          void* stream);
 
+/*
+ * ---- Out-of-core build: host-resident inputs and results ----------------
+ *
+ * For a molecule whose lists do not fit in device memory at once (Section
+ * 4.6: partitions processed one at a time with their border, results copied
+ * back to host memory): the atoms are cut into
+ * slabs along z, and each slab is built on the GPU as the alpha complex of its
+ * atoms plus a halo, the atoms within reach of the slab (|dZ| <= 2 h, in
+ * quanta, h = ceil(sqrt(r_max^2 + alpha))). A simplex belongs to the slab that
+ * holds its first (smallest-index) vertex. Every simplex with that vertex in
+ * the slab, its AC2 and AC3 decisions, its attached flag and its Size depend
+ * only on atoms whose grown balls meet that vertex's (the simplex's cofaces
+ * contain the vertex; their violators are common neighbours of their
+ * vertices), so the halo makes each slab's share exactly that of the whole
+ * molecule, and no simplex is produced twice (Section 4.6 removes duplicates
+ * instead). The shares are brought to host memory and placed in order of
+ * their first vertex: the result equals what ac_build returns for the whole
+ * molecule, list for list.
+ */
+typedef struct ac_chunked ac_chunked;
+
+typedef struct {
+    int64_t n_chunks;      /* slabs with at least one atom */
+    int64_t reach;         /* halo width in quanta (2 h) */
+    int64_t core_max;      /* most atoms in one slab */
+    int64_t subset_max;    /* most atoms in one slab plus its halo (what one device build holds) */
+    int64_t subset_total;  /* atoms built over all slabs (halo atoms counted in every slab) */
+    double ms_plan;        /* host: quantised z, slab cuts, slab membership (wall clock) */
+    double ms_device;      /* wall clock of the slab builds, incl. host<->device copies */
+    double ms_assemble;    /* host: placement of the shares in first-vertex order */
+} ac_chunked_stats;
+
+/*
+ * The slab cut alone (host only; no GPU needed). centres n x 3 and radii n
+ * are HOST doubles (A). Slab k holds the atoms with thresholds[k] <= Z <
+ * thresholds[k+1], Z = rint(1024 z); the cuts keep at most max_core_atoms
+ * atoms in a slab unless more than that share one cut interval (a run of
+ * atoms with the same Z, or, for z spans above 2^22 quanta, the same
+ * 2^-22 of the span). thresholds: caller array of cap entries, filled with
+ * *n_chunks + 1 values; *reach = 2 ceil(sqrt(max W + A)) quanta (0 if no ball
+ * survives alpha). Errors: AC_ERR_INVALID_ARG (NULL, n < 0, max_core_atoms
+ * < 1, NaN/Inf, radius <= 0, cap too small: *n_chunks is still set),
+ * AC_ERR_RANGE (as ac_create).
+ */
+AC_API int ac_chunk_plan(const double* centres, const double* radii, int64_t n, double alpha, int64_t max_core_atoms,
+                         int64_t* thresholds, int64_t cap, int64_t* n_chunks, int64_t* reach);
+
+/*
+ * Build the alpha complex of n HOST balls slab by slab (see above), at most
+ * max_core_atoms atoms per slab (plus halo) on the device at a time. opt as
+ * for ac_create (keep_candidates must be 0). The slabs run one after another
+ * on stream; *out receives a result whose lists live in host memory (read
+ * them with ac_chunked_simplices; free with ac_chunked_free). Synchronous.
+ * Errors: those of ac_chunk_plan, ac_create and ac_build, AC_ERR_OOM (host
+ * memory). On error *out is NULL.
+ */
+AC_API int ac_build_chunked(const double* centres, const double* radii, int64_t n, double alpha,
+                            const ac_options* opt, int64_t max_core_atoms, void* stream, ac_chunked** out);
+
+/*
+ * Host pointers to dimension dim of a chunked result: tuples (count, dim+1)
+ * int32 input indices, ascending in a row, rows lexicographically sorted;
+ * f: the filtration values (opt.filtration); attached: the attached flags
+ * (as ac_attached_flags). Owned by the result. Any output pointer may be NULL.
+ * Errors: AC_ERR_INVALID_ARG (NULL result, dim outside 0..3).
+ */
+AC_API int ac_chunked_simplices(const ac_chunked* res, int dim, const int32_t** tuples, const double** f,
+                                const uint8_t** attached, int64_t* count);
+
+/* Slab counts and times of a chunked build. Errors: AC_ERR_INVALID_ARG. */
+AC_API int ac_chunked_info(const ac_chunked* res, ac_chunked_stats* out);
+
+/* Free a chunked result. NULL is a no-op. */
+AC_API void ac_chunked_free(ac_chunked* res);
+
 /* Counters and stage times of the last ac_build. */
 AC_API int ac_get_stats(ac_ctx* ctx, ac_stats* out);
 

@@ -37,7 +37,8 @@ AC_FILTRATION_ORTHOSIZE = 1
 # every symbol include/alphac.h declares
 EXPORTS = ["ac_create", "ac_create_batch", "ac_build", "ac_get_simplices", "ac_filtration_values", "ac_attached_flags",
            "ac_get_candidates", "ac_eval_filtration", "ac_backward", "ac_backward_noalloc", "ac_autotune",
-           "ac_subcomplex", "ac_get_stats", "ac_get_sizes", "ac_destroy", "ac_error_string", "ac_last_error_detail"]
+           "ac_subcomplex", "ac_chunk_plan", "ac_build_chunked", "ac_chunked_simplices", "ac_chunked_info",
+           "ac_chunked_free", "ac_get_stats", "ac_get_sizes", "ac_destroy", "ac_error_string", "ac_last_error_detail"]
 
 
 class ac_options(ctypes.Structure):
@@ -61,6 +62,12 @@ class ac_stats(ctypes.Structure):
             v = getattr(self, name)
             out[name] = list(v) if isinstance(v, ctypes.Array) else v
         return out
+
+
+class ac_chunked_stats(ctypes.Structure):
+    _fields_ = [("n_chunks", ctypes.c_int64), ("reach", ctypes.c_int64), ("core_max", ctypes.c_int64),
+                ("subset_max", ctypes.c_int64), ("subset_total", ctypes.c_int64), ("ms_plan", ctypes.c_double),
+                ("ms_device", ctypes.c_double), ("ms_assemble", ctypes.c_double)]
 
 
 class AlphacError(RuntimeError):
@@ -91,6 +98,12 @@ def _declare(lib):
     lib.ac_backward_noalloc.argtypes = [vp, vp, vp, vp, vp]
     lib.ac_autotune.argtypes = [vp, vp, P(ac_options)]
     lib.ac_subcomplex.argtypes = [vp, i32, i64, dbl, vp, P(i64), vp]
+    lib.ac_chunk_plan.argtypes = [vp, vp, i64, dbl, i64, vp, i64, P(i64), P(i64)]
+    lib.ac_build_chunked.argtypes = [vp, vp, i64, dbl, P(ac_options), i64, vp, P(vp)]
+    lib.ac_chunked_simplices.argtypes = [vp, i32, P(vp), P(vp), P(vp), P(i64)]
+    lib.ac_chunked_info.argtypes = [vp, P(ac_chunked_stats)]
+    lib.ac_chunked_free.argtypes = [vp]
+    lib.ac_chunked_free.restype = None
     lib.ac_get_stats.argtypes = [vp, P(ac_stats)]
     lib.ac_get_sizes.argtypes = [vp, P(i64), P(i64)]
     lib.ac_destroy.argtypes = [vp]
@@ -100,7 +113,7 @@ def _declare(lib):
     lib.ac_last_error_detail.argtypes = []
     lib.ac_last_error_detail.restype = ctypes.c_char_p
     for name in EXPORTS:
-        if name not in ("ac_destroy", "ac_error_string", "ac_last_error_detail"):
+        if name not in ("ac_destroy", "ac_chunked_free", "ac_error_string", "ac_last_error_detail"):
             getattr(lib, name).restype = ctypes.c_int
 
 
@@ -307,6 +320,105 @@ class AlphaComplex:
         h, self._h = self._h, None
         if h:
             lib().ac_destroy(h)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _host_f64(a, shape_tail=()):
+    if hasattr(a, "data_ptr"):
+        if a.is_cuda:
+            raise ValueError("the chunked build takes host arrays (the molecule need not fit on the device)")
+        a = a.detach().numpy()
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def chunk_plan(centres, radii, alpha: float = 0.0, max_core_atoms: int = 1 << 21):
+    """Slab cuts of a chunked build (host only): (thresholds int64 (k+1,), reach in quanta)."""
+    c = _host_f64(centres)
+    r = _host_f64(radii)
+    n = int(r.shape[0])
+    if c.shape != (n, 3):
+        raise ValueError(f"centres must be ({n}, 3), got {c.shape}")
+    k = ctypes.c_int64()
+    reach = ctypes.c_int64()
+    L = lib()
+    rc = L.ac_chunk_plan(c.ctypes.data if n else None, r.ctypes.data if n else None, n, float(alpha),
+                         int(max_core_atoms), None, 0, ctypes.byref(k), ctypes.byref(reach))
+    if rc != AC_OK and rc != AC_ERR_INVALID_ARG:
+        _check(rc, "ac_chunk_plan")
+    thr = np.zeros(k.value + 1, dtype=np.int64)
+    _check(L.ac_chunk_plan(c.ctypes.data if n else None, r.ctypes.data if n else None, n, float(alpha),
+                           int(max_core_atoms), thr.ctypes.data, len(thr), ctypes.byref(k), ctypes.byref(reach)),
+           "ac_chunk_plan")
+    return thr[:k.value + 1] if n else thr[:0], reach.value
+
+
+class ChunkedComplex:
+    """ac_build_chunked: the alpha complex of host-resident balls, built slab by slab.
+
+    Results are numpy arrays in host memory (copies), equal to what
+    AlphaComplex gives for the whole molecule.
+    """
+
+    def __init__(self, centres, radii, alpha: float = 0.0, max_core_atoms: int = 1 << 21,
+                 opt: ac_options | None = None, stream=None):
+        self._h = None
+        c = _host_f64(centres)
+        r = _host_f64(radii)
+        n = int(r.shape[0])
+        if c.shape != (n, 3):
+            raise ValueError(f"centres must be ({n}, 3), got {c.shape}")
+        o = opt if opt is not None else options()
+        h = ctypes.c_void_p()
+        _check(lib().ac_build_chunked(c.ctypes.data if n else None, r.ctypes.data if n else None, n, float(alpha),
+                                      ctypes.byref(o), int(max_core_atoms), _stream_ptr(stream), ctypes.byref(h)),
+               "ac_build_chunked")
+        self._h = h
+        self.n = n
+        self.alpha = alpha
+
+    def _get(self, dim):
+        t, f, a = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p()
+        cnt = ctypes.c_int64()
+        _check(lib().ac_chunked_simplices(self._h, dim, ctypes.byref(t), ctypes.byref(f), ctypes.byref(a),
+                                          ctypes.byref(cnt)), "ac_chunked_simplices")
+        return t.value, f.value, a.value, cnt.value
+
+    @staticmethod
+    def _copy(ptr, count, ctype, shape, dtype):
+        if count == 0:
+            return np.zeros(shape, dtype=dtype)
+        buf = (ctype * int(np.prod(shape))).from_address(ptr)
+        return np.frombuffer(buf, dtype=dtype).reshape(shape).copy()
+
+    def simplices(self, dim: int):
+        t, _, _, n = self._get(dim)
+        return self._copy(t, n, ctypes.c_int32, (n, dim + 1), np.int32)
+
+    def filtration_values(self, dim: int):
+        _, f, _, n = self._get(dim)
+        return self._copy(f, n, ctypes.c_double, (n,), np.float64)
+
+    def attached(self, dim: int):
+        _, _, a, n = self._get(dim)
+        return self._copy(a, n, ctypes.c_uint8, (n,), np.uint8)
+
+    def count(self, dim: int) -> int:
+        return self._get(dim)[3]
+
+    def stats(self) -> dict:
+        st = ac_chunked_stats()
+        _check(lib().ac_chunked_info(self._h, ctypes.byref(st)), "ac_chunked_info")
+        return {name: getattr(st, name) for name, _ in st._fields_}
+
+    def close(self):
+        h, self._h = self._h, None
+        if h:
+            lib().ac_chunked_free(h)
 
     def __del__(self):
         try:
