@@ -507,6 +507,8 @@ __global__ void k_mol_rows(MolRowsArgs a) {
     for (int l = 0; l < 7; l++) a.out[l * (a.n_mol + 1) + m] = a.v0_off[l] ? a.v0_off[l][at] : 0;
 }
 
+static int fork_orthosize(ac_ctx* c, int d, cudaStream_t s);
+
 int canonicalise(ac_ctx* c, cudaStream_t s) {
     const DevCounters& h = c->hc;  // counters read at the end of the per-atom pass
     if (h.err & (DERR_OVF_TET | DERR_OVF_TRI | DERR_OVF_EDGE | DERR_OVF_CAND))
@@ -515,14 +517,17 @@ int canonicalise(ac_ctx* c, cudaStream_t s) {
     const int64_t n = c->n;
     // K^3
     AC_TRY(canon_dim(c, 3, c->tet_out.as<int4>(), nullptr, (int64_t)h.n_tet_out, nullptr, 0, c->K[3], c->Gbuf[3], w, s));
+    AC_TRY(fork_orthosize(c, 3, s));
     AC_TRY(stage_mark(c, 4, s));
     // K^2 = unattached triangles + facets of K^3
     AC_TRY(canon_dim(c, 2, c->tri_pass.as<int4>(), nullptr, (int64_t)h.n_tri_pass, c->Gbuf[3].as<int4>(), c->K[3].count,
                      c->K[2], c->Gbuf[2], w, s));
+    AC_TRY(fork_orthosize(c, 2, s));
     AC_TRY(stage_mark(c, 5, s));
     // K^1 = unattached edges + edges of K^2
     AC_TRY(canon_dim(c, 1, nullptr, c->edge_pass.as<int2>(), (int64_t)h.n_edge_pass, c->Gbuf[2].as<int4>(),
                      c->K[2].count, c->K[1], c->Gbuf[1], w, s));
+    AC_TRY(fork_orthosize(c, 1, s));
     // K^0
     {
         SimplexList& L = c->K[0];
@@ -570,6 +575,7 @@ int canonicalise(ac_ctx* c, cudaStream_t s) {
             AC_LAUNCHED();
         }
     }
+    AC_TRY(fork_orthosize(c, 0, s));
     // estimation-pass lists, when kept (single molecule)
     if (c->pc.keep_candidates) {
         for (int d = 1; d <= 3; d++) {
@@ -804,21 +810,37 @@ int subcomplex_flags(ac_ctx* c, int dim, int64_t first, int64_t m, double alpha2
     return AC_OK;
 }
 
+// OrthoSize (and the initial Size, source and coface key) of list d, on the
+// side stream as soon as the list's rows are final, overlapping the
+// canonicalisation of the lower dimensions; compute_filtration joins it.
+static int fork_orthosize(ac_ctx* c, int d, cudaStream_t s) {
+    SimplexList& L = c->K[d];
+    const int64_t m = L.count;
+    if (m == 0) return AC_OK;
+    AC_TRY(c->fkey[d].reserve((size_t)m * sizeof(unsigned long long), s));
+    AC_CUDA(cudaEventRecord(c->ev_fork, s));
+    AC_CUDA(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
+    k_orthosize<<<(unsigned)((m + 127) / 128), 128, 0, c->side>>>(
+        c->P.as<int4>(), c->Gbuf[d].as<int4>(), m, d + 1, L.attached.as<uint8_t>(), L.orthosize.as<double>(),
+        L.f.as<double>(), L.src_dim.as<int8_t>(), L.src_idx.as<int64_t>(), c->fkey[d].as<unsigned long long>());
+    AC_LAUNCHED();
+    c->os_forked = true;
+    return AC_OK;
+}
+
 int compute_filtration(ac_ctx* c, cudaStream_t s) {
-    const int4* P = c->P.as<int4>();
-    DevBuf& keyb = c->scratch[2];
+    if (c->os_forked) {
+        AC_CUDA(cudaEventRecord(c->ev_join, c->side));
+        AC_CUDA(cudaStreamWaitEvent(s, c->ev_join, 0));
+        c->os_forked = false;
+    }
     DevBuf& argb = c->scratch[3];
-    for (int d = 3; d >= 0; d--) {
+    for (int d = 2; d >= 0; d--) {
         SimplexList& L = c->K[d];
         const int64_t m = L.count;
         if (m == 0) continue;
-        AC_TRY(keyb.reserve((size_t)m * sizeof(unsigned long long), s));
+        unsigned long long* keyb = c->fkey[d].as<unsigned long long>();
         AC_TRY(argb.reserve((size_t)m * sizeof(unsigned long long), s));
-        k_orthosize<<<(unsigned)((m + 127) / 128), 128, 0, s>>>(
-            P, c->Gbuf[d].as<int4>(), m, d + 1, L.attached.as<uint8_t>(), L.orthosize.as<double>(), L.f.as<double>(),
-            L.src_dim.as<int8_t>(), L.src_idx.as<int64_t>(), keyb.as<unsigned long long>());
-        AC_LAUNCHED();
-        if (d == 3) continue;
         SimplexList& U = c->K[d + 1];
         AC_CUDA(cudaMemsetAsync(argb.p, 0xff, (size_t)m * sizeof(unsigned long long), s));
         if (U.count > 0) {
@@ -827,16 +849,16 @@ int compute_filtration(ac_ctx* c, cudaStream_t s) {
             AC_TRY(rowb.reserve((size_t)U.count * (d + 2) * sizeof(int64_t), s));
             k_coface_min<<<nbk, 128, 0, s>>>(c->Gbuf[d + 1].as<int4>(), U.f.as<double>(), U.count, d + 2,
                                              c->Gbuf[d].as<int4>(), L.v0_off.as<int64_t>(), L.attached.as<uint8_t>(),
-                                             keyb.as<unsigned long long>(), rowb.as<int64_t>());
+                                             keyb, rowb.as<int64_t>());
             AC_LAUNCHED();
-            k_coface_arg<<<nbk, 128, 0, s>>>(U.f.as<double>(), U.count, d + 2, rowb.as<int64_t>(),
-                                             keyb.as<unsigned long long>(), argb.as<unsigned long long>());
+            k_coface_arg<<<nbk, 128, 0, s>>>(U.f.as<double>(), U.count, d + 2, rowb.as<int64_t>(), keyb,
+                                             argb.as<unsigned long long>());
             AC_LAUNCHED();
         }
         k_coface_apply<<<(unsigned)((m + 127) / 128), 128, 0, s>>>(
-            m, L.attached.as<uint8_t>(), keyb.as<unsigned long long>(), argb.as<unsigned long long>(),
-            U.src_dim.as<int8_t>(), U.src_idx.as<int64_t>(), L.f.as<double>(), L.src_dim.as<int8_t>(),
-            L.src_idx.as<int64_t>(), &c->counters.as<DevCounters>()->err);
+            m, L.attached.as<uint8_t>(), keyb, argb.as<unsigned long long>(), U.src_dim.as<int8_t>(),
+            U.src_idx.as<int64_t>(), L.f.as<double>(), L.src_dim.as<int8_t>(), L.src_idx.as<int64_t>(),
+            &c->counters.as<DevCounters>()->err);
         AC_LAUNCHED();
     }
     return AC_OK;

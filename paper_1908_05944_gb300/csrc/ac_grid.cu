@@ -210,16 +210,18 @@ __global__ void k_deg_hist(const int64_t* __restrict__ cnt, int64_t n, unsigned*
         if (h[t]) atomicAdd(&hist[t], h[t]);
 }
 
-// one thread: start of each bin in decreasing order, and the head size
+// start of each bin in decreasing order, and the head size: one thread per bin
 __global__ void k_deg_starts(const unsigned* __restrict__ hist, unsigned* __restrict__ cursor,
                              long long* __restrict__ n_wide) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    __shared__ unsigned h[DEG_BINS];
+    const int b = threadIdx.x;
+    if (b < DEG_BINS) h[b] = hist[b];
+    __syncthreads();
+    if (b >= DEG_BINS) return;
     unsigned run = 0;
-    for (int b = DEG_BINS - 1; b >= 0; b--) {
-        cursor[b] = run;
-        run += hist[b];
-        if (b == 65) *n_wide = run;
-    }
+    for (int q = DEG_BINS - 1; q > b; q--) run += h[q];
+    cursor[b] = run;
+    if (b == 65) *n_wide = run + h[65];
 }
 
 __global__ void k_deg_scatter(const int64_t* __restrict__ cnt, int64_t n, unsigned* __restrict__ cursor,
@@ -277,7 +279,7 @@ int build_neighbours(ac_ctx* c, cudaStream_t s) {
     AC_CUDA(cudaMemsetAsync(hist, 0, DEG_BINS * sizeof(unsigned), s));
     k_deg_hist<<<nb, 128, 0, s>>>(cntp, n, hist);
     AC_LAUNCHED();
-    k_deg_starts<<<1, 32, 0, s>>>(hist, cursor, n_wide);
+    k_deg_starts<<<1, (DEG_BINS + 31) / 32 * 32, 0, s>>>(hist, cursor, n_wide);
     AC_LAUNCHED();
     k_deg_scatter<<<nb, 128, 0, s>>>(cntp, n, cursor, c->work.as<int32_t>());
     AC_LAUNCHED();

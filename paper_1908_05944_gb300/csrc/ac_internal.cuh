@@ -241,6 +241,8 @@ struct ac_ctx {
     // scratch
     ac::DevBuf counters;  // DevCounters
     ac::DevBuf scratch[7];
+    ac::DevBuf fkey[4];      // per-dimension coface-minimum keys (k_orthosize, k_coface_*)
+    bool os_forked = false;  // k_orthosize launches on the side stream await their join
     ac::DevBuf scan_tmp;
 
     ac::DevCounters hc{};             // host copy of the counters from the last readback
