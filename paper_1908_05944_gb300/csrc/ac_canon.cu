@@ -462,6 +462,217 @@ static int canon_dim(ac_ctx* c, int d, const int4* a4, const int2* a2, int64_t n
     }
 }
 
+// ---------------------------------------------------------------------------
+// K^1 by marks (Step 4 for edges). An edge of K^1 joins two atoms whose grown
+// balls meet (its OrthoSize is at most alpha), so its second vertex is an
+// entry of the neighbour row of its first vertex (smallest input index); the
+// rows list grid-sorted positions in ascending order. The free edges and the
+// three edges of every K^2 triangle set bits over those rows (bit OR: a
+// duplicate changes nothing, so nothing is sorted or removed), a second mask
+// keeps the free edges, and each atom writes its marked entries as rows in
+// ascending input order.
+
+struct EdgeMarkArgs {
+    const int2* free_e;  // free edges (sorted positions), nA of them
+    int64_t nA;
+    const int4* tri;     // K^2 rows (global input indices), nB of them
+    int64_t nB;
+    const int32_t* order;  // sorted position -> input index
+    const int32_t* rank;   // input index -> sorted position
+    const int64_t* nb_off; // offsets (stride 0) or counts (stride > 0)
+    const int32_t* nb;
+    int stride;
+    int words;             // mask words per atom
+    unsigned* m_in;        // per sorted position: entry of the row is an edge of K^1
+    unsigned* m_free;      // ... and a free edge
+    unsigned* err;
+};
+
+__device__ __forceinline__ void edge_row(const EdgeMarkArgs& a, int s, int64_t& off, int& m) {
+    if (a.stride) {
+        off = (int64_t)s * a.stride;
+        m = min((int)a.nb_off[s], a.stride);
+    } else {
+        off = a.nb_off[s];
+        m = (int)(a.nb_off[s + 1] - off);
+    }
+}
+
+// position of sorted position x in the ascending row [off, off + m), or -1
+__device__ __forceinline__ int row_find(const int32_t* __restrict__ nb, int64_t off, int m, int x) {
+    int lo = 0, hi = m;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (nb[off + mid] < x) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo < m && nb[off + lo] == x ? lo : -1;
+}
+
+__device__ __forceinline__ void mark_bit(const EdgeMarkArgs& a, int su, int e, bool fr) {
+    if (e < 0) {
+        atomicOr(a.err, DERR_INTERNAL);  // an edge of K^1 between atoms whose balls do not meet: impossible
+        return;
+    }
+    const int64_t w = (int64_t)su * a.words + (e >> 5);
+    const unsigned bit = 1u << (e & 31);
+    atomicOr(&a.m_in[w], bit);
+    if (fr) atomicOr(&a.m_free[w], bit);
+}
+
+// threads [0, nA): one free edge each; then one K^2 triangle (a < b < c) each:
+// (a, b) and (a, c) in a's row, (b, c) in b's row
+__global__ void k_edge_mark(EdgeMarkArgs a) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= a.nA + a.nB) return;
+    int64_t off;
+    int m;
+    if (j < a.nA) {
+        const int2 e = a.free_e[j];
+        int gu = a.order[e.x], gv = a.order[e.y];
+        int su = e.x, sv = e.y;
+        if (gu > gv) {
+            su = e.y;
+            sv = e.x;
+        }
+        edge_row(a, su, off, m);
+        mark_bit(a, su, row_find(a.nb, off, m, sv), true);
+        return;
+    }
+    const int4 t = a.tri[j - a.nA];
+    const int sa = a.rank[t.x], sb = a.rank[t.y], sc = a.rank[t.z];
+    edge_row(a, sa, off, m);
+    const int eb = row_find(a.nb, off, m, sb), ec = row_find(a.nb, off, m, sc);
+    int64_t offb;
+    int mb;
+    edge_row(a, sb, offb, mb);
+    const int ebc = row_find(a.nb, offb, mb, sc);
+    mark_bit(a, sa, eb, false);
+    mark_bit(a, sa, ec, false);
+    mark_bit(a, sb, ebc, false);
+}
+
+// rows per first vertex (input index g)
+__global__ void k_edge_count(EdgeMarkArgs a, int64_t n, int64_t* __restrict__ cnt) {
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= n) return;
+    const unsigned* mw = a.m_in + (int64_t)a.rank[g] * a.words;
+    int c = 0;
+    for (int w = 0; w < a.words; w++) c += __popc(mw[w]);
+    cnt[g] = c;
+}
+
+// the marked entries of g's row, ranked by input index: one warp per atom;
+// the marked entries' input indices are compacted into shared memory, then
+// each marked lane counts the smaller ones
+constexpr int EW_WARPS = 4;
+
+__global__ void __launch_bounds__(EW_WARPS * 32) k_edge_write(EdgeMarkArgs a, int64_t n, const int64_t* __restrict__ uoff,
+                                                              const int32_t* __restrict__ mol_of,
+                                                              const int64_t* __restrict__ mol_off, int4* __restrict__ G,
+                                                              int32_t* __restrict__ out, uint8_t* __restrict__ attached) {
+    __shared__ int hs_all[EW_WARPS][256];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    int* hs = hs_all[wib];
+    const int64_t g = (int64_t)blockIdx.x * EW_WARPS + wib;
+    if (g >= n) return;
+    const int s = a.rank[g];
+    const unsigned* mw = a.m_in + (int64_t)s * a.words;
+    const unsigned* fw = a.m_free + (int64_t)s * a.words;
+    int64_t off;
+    int m;
+    edge_row(a, s, off, m);
+    const int64_t row0 = uoff[g];
+    const int base = (int)mol_off[mol_of[g]];
+    // pass 1: compact the marked entries (input index, free bit) in entry order
+    int c = 0;
+    for (int w = 0; w < a.words; w++) {
+        const unsigned bits = mw[w];  // the same word for the whole warp
+        if (!bits) continue;
+        const bool mine = (bits >> lane) & 1u;
+        if (mine) {
+            const int h = a.order[a.nb[off + 32 * w + lane]];
+            hs[c + __popc(bits & ((1u << lane) - 1u))] = h;
+        }
+        c += __popc(bits);
+    }
+    __syncwarp();
+    // pass 2: rank each compacted entry among the others
+    for (int k = lane; k < c; k += 32) {
+        const int h = hs[k];
+        int r = 0;
+        for (int q = 0; q < c; q++) r += hs[q] < h;
+        // the free bit of the k-th marked entry
+        int rem = k, w = 0;
+        unsigned bits = mw[0];
+        while (rem >= __popc(bits)) {
+            rem -= __popc(bits);
+            bits = mw[++w];
+        }
+        for (int t = 0; t < rem; t++) bits &= bits - 1;
+        const int e = __ffs(bits) - 1;
+        const int64_t row = row0 + r;
+        G[row] = make_int4((int)g, h, -1, -1);
+        out[row * 2 + 0] = (int)g - base;
+        out[row * 2 + 1] = h - base;
+        attached[row] = (fw[w] >> e) & 1u ? 0 : 1;
+    }
+}
+
+static int canon_edges_by_marks(ac_ctx* c, cudaStream_t s) {
+    const DevCounters& h = c->hc;
+    const int64_t n = c->n;
+    SimplexList& L = c->K[1];
+    Work& w = c->cw;
+    const int words = (h.max_degree + 31) / 32 > 0 ? (h.max_degree + 31) / 32 : 1;
+    const size_t nn = (size_t)(n > 0 ? n : 1);
+    DevBuf& masks = c->scratch[2];
+    AC_TRY(masks.reserve(2 * nn * words * sizeof(unsigned), s));
+    AC_TRY(w.cnt.reserve((nn + 1) * sizeof(int64_t), s));
+    AC_TRY(L.v0_off.reserve((nn + 1) * sizeof(int64_t), s));
+    AC_CUDA(cudaMemsetAsync(masks.p, 0, 2 * nn * words * sizeof(unsigned), s));
+    EdgeMarkArgs a{c->edge_pass.as<int2>(), (int64_t)h.n_edge_pass, c->Gbuf[2].as<int4>(), c->K[2].count,
+                   c->order.as<int32_t>(), c->rank.as<int32_t>(), c->nb_cnt.as<int64_t>(), c->nb.as<int32_t>(),
+                   c->nb_stride, words, masks.as<unsigned>(), masks.as<unsigned>() + nn * words,
+                   &c->counters.as<DevCounters>()->err};
+    const int64_t items = a.nA + a.nB;
+    if (items > 0) {
+        k_edge_mark<<<(unsigned)((items + 255) / 256), 256, 0, s>>>(a);
+        AC_LAUNCHED();
+    }
+    int64_t* cnt = w.cnt.as<int64_t>();
+    if (n > 0) {
+        k_edge_count<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(a, n, cnt);
+        AC_LAUNCHED();
+    }
+    int64_t* uoff = L.v0_off.as<int64_t>();
+    AC_TRY(scan_exclusive_i64(c, cnt, uoff, n, s));
+    int64_t count = L.count;
+    if (c->replaying) {
+        AC_TRY(expect_i64(c, uoff + n, count, s));
+    } else {
+        AC_CUDA(cudaMemcpyAsync(c->h_stage, uoff + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        AC_TRY(sync_host(c, s));
+        count = c->h_stage[0];
+    }
+    L.count = count;
+    const size_t rows = (size_t)(count > 0 ? count : 1);
+    AC_TRY(L.tuples.reserve(rows * 2 * sizeof(int32_t), s));
+    AC_TRY(L.attached.reserve(rows, s));
+    AC_TRY(L.f.reserve(rows * sizeof(double), s));
+    AC_TRY(L.orthosize.reserve(rows * sizeof(double), s));
+    AC_TRY(L.src_dim.reserve(rows, s));
+    AC_TRY(L.src_idx.reserve(rows * sizeof(int64_t), s));
+    AC_TRY(c->Gbuf[1].reserve(rows * sizeof(int4), s));
+    if (n > 0) {
+        k_edge_write<<<(unsigned)((n + EW_WARPS - 1) / EW_WARPS), EW_WARPS * 32, 0, s>>>(a, n, uoff, c->mol_of.as<int32_t>(),
+                                                                  c->d_moloff.as<int64_t>(), c->Gbuf[1].as<int4>(),
+                                                                  L.tuples.as<int32_t>(), L.attached.as<uint8_t>());
+        AC_LAUNCHED();
+    }
+    return AC_OK;
+}
+
 // Vertices (Step 5): K^0 = endpoints of K^1 + atoms whose centre passes AC2.
 __global__ void k_mark_endpoints(const int4* __restrict__ E, int64_t m, uint8_t* __restrict__ endpoint) {
     int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -524,9 +735,8 @@ int canonicalise(ac_ctx* c, cudaStream_t s) {
                      c->K[2], c->Gbuf[2], w, s));
     AC_TRY(fork_orthosize(c, 2, s));
     AC_TRY(stage_mark(c, 5, s));
-    // K^1 = unattached edges + edges of K^2
-    AC_TRY(canon_dim(c, 1, nullptr, c->edge_pass.as<int2>(), (int64_t)h.n_edge_pass, c->Gbuf[2].as<int4>(),
-                     c->K[2].count, c->K[1], c->Gbuf[1], w, s));
+    // K^1 = unattached edges + edges of K^2, by marks over the neighbour rows
+    AC_TRY(canon_edges_by_marks(c, s));
     AC_TRY(fork_orthosize(c, 1, s));
     // K^0
     {
