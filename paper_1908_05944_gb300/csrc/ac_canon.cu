@@ -673,6 +673,273 @@ static int canon_edges_by_marks(ac_ctx* c, cudaStream_t s) {
     return AC_OK;
 }
 
+// ---------------------------------------------------------------------------
+// K^2 by marks (Step 3 for triangles), as for edges one dimension up: a
+// triangle of K^2 has pairwise-meeting vertices, so its second and third
+// vertices are entries p < q of the neighbour row of its first vertex. Each
+// atom has a pair mask over its row (bit q (q - 1) / 2 + p), sized by its own
+// row length m (m (m - 1) / 2 bits); the free triangles and the four facets of
+// every tetrahedron of K^3 set bits, a second mask keeps the free ones, and
+// each atom writes its marked pairs in lexicographic input order.
+
+struct TriMarkArgs {
+    const int4* free_t;  // free triangles (sorted positions in x, y, z), nA of them
+    int64_t nA;
+    const int4* tet;     // K^3 rows (global input indices), nB of them
+    int64_t nB;
+    const int32_t* order;
+    const int32_t* rank;
+    const int64_t* nb_off;
+    const int32_t* nb;
+    int stride;
+    const int64_t* moff;  // first mask word of each sorted position (n + 1)
+    unsigned* m_in;
+    unsigned* m_free;
+    unsigned* err;
+};
+
+__device__ __forceinline__ void nb_row_of(const int64_t* __restrict__ nb_off, int stride, int s, int64_t& off, int& m) {
+    if (stride) {
+        off = (int64_t)s * stride;
+        m = min((int)nb_off[s], stride);
+    } else {
+        off = nb_off[s];
+        m = (int)(nb_off[s + 1] - off);
+    }
+}
+
+__device__ __forceinline__ int64_t pair_words(int m) { return ((int64_t)m * (m - 1) / 2 + 31) / 32; }
+
+// mask words of every sorted position
+__global__ void k_pair_words(const int64_t* __restrict__ nb_off, int stride, int64_t n, int64_t* __restrict__ pw) {
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    int64_t off;
+    int m;
+    nb_row_of(nb_off, stride, (int)s, off, m);
+    pw[s] = pair_words(m);
+}
+
+__device__ __forceinline__ void mark_pair(const TriMarkArgs& a, int sa, int e1, int e2, bool fr) {
+    if (e1 < 0 || e2 < 0) {
+        atomicOr(a.err, DERR_INTERNAL);  // a triangle of K^2 whose vertices' balls do not meet: impossible
+        return;
+    }
+    const int p = min(e1, e2), q = max(e1, e2);
+    const int64_t bit = (int64_t)q * (q - 1) / 2 + p;
+    const int64_t w = a.moff[sa] + (bit >> 5);
+    const unsigned b = 1u << (bit & 31);
+    atomicOr(&a.m_in[w], b);
+    if (fr) atomicOr(&a.m_free[w], b);
+}
+
+// threads [0, nA): one free triangle each; then one K^3 tetrahedron (a < b < c < d)
+// each: (a,b,c), (a,b,d), (a,c,d) in a's row, (b,c,d) in b's row
+__global__ void k_tri_mark(TriMarkArgs a) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= a.nA + a.nB) return;
+    int64_t off;
+    int m;
+    if (j < a.nA) {
+        const int4 t = a.free_t[j];
+        int sv[3] = {t.x, t.y, t.z};
+        int gv[3] = {a.order[t.x], a.order[t.y], a.order[t.z]};
+        int f = 0;  // the vertex with the smallest input index
+        if (gv[1] < gv[f]) f = 1;
+        if (gv[2] < gv[f]) f = 2;
+        const int sa = sv[f], s1 = sv[f == 0 ? 1 : 0], s2 = sv[f == 2 ? 1 : 2];
+        nb_row_of(a.nb_off, a.stride, sa, off, m);
+        mark_pair(a, sa, row_find(a.nb, off, m, s1), row_find(a.nb, off, m, s2), true);
+        return;
+    }
+    const int4 t = a.tet[j - a.nA];
+    const int sa = a.rank[t.x], sb = a.rank[t.y], sc = a.rank[t.z], sd = a.rank[t.w];
+    nb_row_of(a.nb_off, a.stride, sa, off, m);
+    const int pb = row_find(a.nb, off, m, sb), pc = row_find(a.nb, off, m, sc), pd = row_find(a.nb, off, m, sd);
+    mark_pair(a, sa, pb, pc, false);
+    mark_pair(a, sa, pb, pd, false);
+    mark_pair(a, sa, pc, pd, false);
+    nb_row_of(a.nb_off, a.stride, sb, off, m);
+    mark_pair(a, sb, row_find(a.nb, off, m, sc), row_find(a.nb, off, m, sd), false);
+}
+
+constexpr int TW_WARPS = 4;
+constexpr int TW_CAP = 256;  // marked pairs ranked in shared memory; more take the slow path
+
+// rows per first vertex (input index g): one warp per atom
+__global__ void __launch_bounds__(TW_WARPS * 32) k_tri_count(TriMarkArgs a, int64_t n, int64_t* __restrict__ cnt) {
+    const int lane = threadIdx.x & 31;
+    const int64_t g = (int64_t)blockIdx.x * TW_WARPS + (threadIdx.x >> 5);
+    if (g >= n) return;
+    const int s = a.rank[g];
+    const int64_t w0 = a.moff[s], w1 = a.moff[s + 1];
+    int c = 0;
+    for (int64_t w = w0 + lane; w < w1; w += 32) c += __popc(a.m_in[w]);
+    c = __reduce_add_sync(0xffffffffu, c);
+    if (lane == 0) cnt[g] = c;
+}
+
+__device__ __forceinline__ void pair_of(int64_t bit, int& p, int& q) {
+    int x = (int)((1.0f + sqrtf(1.0f + 8.0f * (float)bit)) * 0.5f);
+    while ((int64_t)x * (x - 1) / 2 > bit) x--;
+    while ((int64_t)(x + 1) * x / 2 <= bit) x++;
+    q = x;
+    p = (int)(bit - (int64_t)q * (q - 1) / 2);
+}
+
+__global__ void __launch_bounds__(TW_WARPS * 32) k_tri_write(TriMarkArgs a, int64_t n, const int64_t* __restrict__ uoff,
+                                                             const int32_t* __restrict__ mol_of,
+                                                             const int64_t* __restrict__ mol_off, int4* __restrict__ G,
+                                                             int32_t* __restrict__ out, uint8_t* __restrict__ attached) {
+    __shared__ unsigned long long key_all[TW_WARPS][TW_CAP];
+    __shared__ uint8_t fr_all[TW_WARPS][TW_CAP];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int64_t g = (int64_t)blockIdx.x * TW_WARPS + wib;
+    if (g >= n) return;
+    unsigned long long* key = key_all[wib];
+    uint8_t* frs = fr_all[wib];
+    const int s = a.rank[g];
+    int64_t off;
+    int m;
+    nb_row_of(a.nb_off, a.stride, s, off, m);
+    const int64_t w0 = a.moff[s], w1 = a.moff[s + 1];
+    const int64_t row0 = uoff[g];
+    const int64_t total = uoff[g + 1] - row0;
+    const int base = (int)mol_off[mol_of[g]];
+    auto key_of = [&](int64_t bit) {
+        int p, q;
+        pair_of(bit, p, q);
+        const unsigned hb = (unsigned)a.order[a.nb[off + p]], hc = (unsigned)a.order[a.nb[off + q]];
+        return hb < hc ? ((unsigned long long)hb << 32) | hc : ((unsigned long long)hc << 32) | hb;
+    };
+    auto emit = [&](unsigned long long k, int64_t r, bool fr) {
+        const int y = (int)(k >> 32), z = (int)(k & 0xffffffffu);
+        const int64_t row = row0 + r;
+        G[row] = make_int4((int)g, y, z, -1);
+        out[row * 3 + 0] = (int)g - base;
+        out[row * 3 + 1] = y - base;
+        out[row * 3 + 2] = z - base;
+        attached[row] = fr ? 0 : 1;
+    };
+    if (total <= TW_CAP) {
+        // compact the marked pairs in bit order, then rank them
+        int c = 0;
+        for (int64_t wb = w0; wb < w1; wb += 32) {
+            const int64_t w = wb + lane;
+            const unsigned bits = w < w1 ? a.m_in[w] : 0u;
+            const int k = __popc(bits);
+            int incl = k;
+            for (int d = 1; d < 32; d <<= 1) {
+                const int v = __shfl_up_sync(0xffffffffu, incl, d);
+                if (lane >= d) incl += v;
+            }
+            int slot = c + incl - k;
+            const unsigned frw = bits ? a.m_free[w] : 0u;
+            for (unsigned b = bits; b; b &= b - 1) {
+                const int t = __ffs(b) - 1;
+                key[slot] = key_of((w - w0) * 32 + t);
+                frs[slot] = (uint8_t)((frw >> t) & 1u);
+                slot++;
+            }
+            c += __shfl_sync(0xffffffffu, incl, 31);
+        }
+        __syncwarp();
+        for (int k = lane; k < c; k += 32) {
+            const unsigned long long kk = key[k];
+            int r = 0;
+            for (int q = 0; q < c; q++) r += key[q] < kk;
+            emit(kk, r, frs[k] != 0);
+        }
+    } else {
+        // many pairs (a very wide row): rank each against all, from the masks
+        for (int64_t w = w0; w < w1; w++) {
+            const unsigned bits = a.m_in[w];
+            const unsigned frw = a.m_free[w];
+            for (int t = lane; t < 32; t += 32) {
+                if (!((bits >> t) & 1u)) continue;
+                const unsigned long long kk = key_of((w - w0) * 32 + t);
+                int64_t r = 0;
+                for (int64_t w2 = w0; w2 < w1; w2++)
+                    for (unsigned b2 = a.m_in[w2]; b2; b2 &= b2 - 1)
+                        r += key_of((w2 - w0) * 32 + __ffs(b2) - 1) < kk;
+                emit(kk, r, (frw >> t) & 1u);
+            }
+        }
+    }
+}
+
+static int canon_tris_by_marks(ac_ctx* c, cudaStream_t s) {
+    const DevCounters& h = c->hc;
+    const int64_t n = c->n;
+    SimplexList& L = c->K[2];
+    Work& w = c->cw;
+    const size_t nn = (size_t)(n > 0 ? n : 1);
+    DevBuf& moffb = c->pair_moff;
+    DevBuf& masks = c->scratch[2];
+    AC_TRY(moffb.reserve((nn + 1) * sizeof(int64_t), s));
+    AC_TRY(w.cnt.reserve((nn + 1) * sizeof(int64_t), s));
+    AC_TRY(L.v0_off.reserve((nn + 1) * sizeof(int64_t), s));
+    int64_t* moff = moffb.as<int64_t>();
+    int64_t* cnt = w.cnt.as<int64_t>();
+    if (n > 0) {
+        k_pair_words<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(c->nb_cnt.as<int64_t>(), c->nb_stride, n, cnt);
+        AC_LAUNCHED();
+    }
+    AC_TRY(scan_exclusive_i64(c, cnt, moff, n, s));
+    int64_t words = c->pair_words;
+    if (c->replaying) {
+        AC_TRY(expect_i64(c, moff + n, words, s));
+    } else {
+        AC_CUDA(cudaMemcpyAsync(c->h_stage, moff + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        AC_TRY(sync_host(c, s));
+        words = c->h_stage[0];
+    }
+    c->pair_words = words;
+    const size_t mw = (size_t)(words > 0 ? words : 1);
+    AC_TRY(masks.reserve(2 * mw * sizeof(unsigned), s));
+    AC_CUDA(cudaMemsetAsync(masks.p, 0, 2 * mw * sizeof(unsigned), s));
+    TriMarkArgs a{c->tri_pass.as<int4>(), (int64_t)h.n_tri_pass, c->Gbuf[3].as<int4>(), c->K[3].count,
+                  c->order.as<int32_t>(), c->rank.as<int32_t>(), c->nb_cnt.as<int64_t>(), c->nb.as<int32_t>(),
+                  c->nb_stride, moff, masks.as<unsigned>(), masks.as<unsigned>() + mw,
+                  &c->counters.as<DevCounters>()->err};
+    const int64_t items = a.nA + a.nB;
+    if (items > 0) {
+        k_tri_mark<<<(unsigned)((items + 255) / 256), 256, 0, s>>>(a);
+        AC_LAUNCHED();
+    }
+    const unsigned wb = (unsigned)((n + TW_WARPS - 1) / TW_WARPS);
+    if (n > 0) {
+        k_tri_count<<<wb, TW_WARPS * 32, 0, s>>>(a, n, cnt);
+        AC_LAUNCHED();
+    }
+    int64_t* uoff = L.v0_off.as<int64_t>();
+    AC_TRY(scan_exclusive_i64(c, cnt, uoff, n, s));
+    int64_t count = L.count;
+    if (c->replaying) {
+        AC_TRY(expect_i64(c, uoff + n, count, s));
+    } else {
+        AC_CUDA(cudaMemcpyAsync(c->h_stage, uoff + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        AC_TRY(sync_host(c, s));
+        count = c->h_stage[0];
+    }
+    L.count = count;
+    const size_t rows = (size_t)(count > 0 ? count : 1);
+    AC_TRY(L.tuples.reserve(rows * 3 * sizeof(int32_t), s));
+    AC_TRY(L.attached.reserve(rows, s));
+    AC_TRY(L.f.reserve(rows * sizeof(double), s));
+    AC_TRY(L.orthosize.reserve(rows * sizeof(double), s));
+    AC_TRY(L.src_dim.reserve(rows, s));
+    AC_TRY(L.src_idx.reserve(rows * sizeof(int64_t), s));
+    AC_TRY(c->Gbuf[2].reserve(rows * sizeof(int4), s));
+    if (n > 0) {
+        k_tri_write<<<wb, TW_WARPS * 32, 0, s>>>(a, n, uoff, c->mol_of.as<int32_t>(), c->d_moloff.as<int64_t>(),
+                                                 c->Gbuf[2].as<int4>(), L.tuples.as<int32_t>(),
+                                                 L.attached.as<uint8_t>());
+        AC_LAUNCHED();
+    }
+    return AC_OK;
+}
+
 // Vertices (Step 5): K^0 = endpoints of K^1 + atoms whose centre passes AC2.
 __global__ void k_mark_endpoints(const int4* __restrict__ E, int64_t m, uint8_t* __restrict__ endpoint) {
     int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -731,8 +998,7 @@ int canonicalise(ac_ctx* c, cudaStream_t s) {
     AC_TRY(fork_orthosize(c, 3, s));
     AC_TRY(stage_mark(c, 4, s));
     // K^2 = unattached triangles + facets of K^3
-    AC_TRY(canon_dim(c, 2, c->tri_pass.as<int4>(), nullptr, (int64_t)h.n_tri_pass, c->Gbuf[3].as<int4>(), c->K[3].count,
-                     c->K[2], c->Gbuf[2], w, s));
+    AC_TRY(canon_tris_by_marks(c, s));
     AC_TRY(fork_orthosize(c, 2, s));
     AC_TRY(stage_mark(c, 5, s));
     // K^1 = unattached edges + edges of K^2, by marks over the neighbour rows

@@ -243,6 +243,8 @@ struct ac_ctx {
     ac::DevBuf scratch[7];
     ac::DevBuf fkey[4];      // per-dimension coface-minimum keys (k_orthosize, k_coface_*)
     bool os_forked = false;  // k_orthosize launches on the side stream await their join
+    int64_t pair_words = 0;  // words of the triangle pair masks (recorded for replays)
+    ac::DevBuf pair_moff;    // first pair-mask word of each sorted position (n + 1)
     ac::DevBuf scan_tmp;
 
     ac::DevCounters hc{};             // host copy of the counters from the last readback
