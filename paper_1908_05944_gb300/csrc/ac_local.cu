@@ -1036,9 +1036,99 @@ __device__ __forceinline__ bool meet(long long D, long long s1, long long s2) {
     return t <= 0 || t * t <= 4 * s1 * s2;
 }
 
-__global__ void k_resolve(LocalArgs A, int64_t n_pending) {
-    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= n_pending) return;
+constexpr int RESOLVE_LANES = 8;
+
+// AC2 test of one candidate (entry e of L(i)) against an escalated simplex:
+// the FP32 test with y rounded from y64 (filtered mode), then FP64, then exact
+// integers with the symbolic perturbation. True if the candidate violates AC2.
+__device__ __forceinline__ bool resolve_one(const LocalArgs& A, int e, int64_t off, const int4& Pi, long long Wi,
+                                            int gi, int nv, const int* v, const long long (*q)[3], const long long* a,
+                                            const long long* sv, const int* gv, long long det, long long g11,
+                                            long long g22, long long g12, long long n1, long long n2,
+                                            const long long (*C)[3], const long long* N, bool f32, const float* yf,
+                                            float E32, const double* y, double E, unsigned& n32, unsigned& n64,
+                                            unsigned& nx) {
+    const long long Aq = A.pc.A;
+    const int x = A.nb[off + e];
+    if (x == v[0] || (nv >= 2 && x == v[1]) || (nv == 3 && x == v[2])) return false;
+    const int4 Px = A.Ps[x];
+    const long long sx = (long long)Px.w + Aq;
+    const long long qx[3] = {(long long)Px.x - Pi.x, (long long)Px.y - Pi.y, (long long)Px.z - Pi.z};
+    bool adj = true;
+    for (int t = 0; t < nv && adj; t++) {
+        // both points lie within 2h <= 2^13 quanta of p_i: differences below 2^14, squares in 32 bits
+        const int dx = (int)(qx[0] - q[t][0]), dy = (int)(qx[1] - q[t][1]), dz = (int)(qx[2] - q[t][2]);
+        adj = meet((long long)(dx * dx + dy * dy + dz * dz), sv[t], sx);
+    }
+    if (!adj) return false;
+    const long long ax = qx[0] * qx[0] + qx[1] * qx[1] + qx[2] * qx[2] - Px.w + Wi;
+    int dec = 0;
+    if (f32) {
+        // the per-atom kernel's FP32 test (same operands and operations)
+        const float t = __fmaf_rn((float)qx[2], yf[2], __fmaf_rn((float)qx[1], yf[1], __fmul_rn((float)qx[0], yf[0])));
+        const float d = __fmaf_rn(-2.0f, t, (float)ax);
+        if (d > E32) dec = 1;
+        else if (d < -E32) dec = -1;
+        if (dec) n32++;
+    }
+    if (nv >= 2 && !dec) {
+        const double t = fma((double)qx[2], y[2], fma((double)qx[1], y[1], (double)qx[0] * y[0]));
+        const double d = fma(-2.0, t, (double)ax);
+        if (d > E) dec = 1;
+        else if (d < -E) dec = -1;
+        if (dec) n64++;
+    }
+    if (!dec) {
+        nx++;
+        const int gx = A.order[x];
+        if (nv == 1) {
+            const long long qq = q[0][0] * qx[0] + q[0][1] * qx[1] + q[0][2] * qx[2];
+            const long long vv = ax * det - a[0] * qq;  // |.| < 2^55
+            if (vv != 0) {
+                dec = vv > 0 ? 1 : -1;
+            } else {
+                const long long coef[2] = {det - qq, qq};
+                const int g[2] = {gi, gv[0]};
+                dec = sos_violates(2, g, coef, gx) ? -1 : 1;
+            }
+        } else if (nv == 2) {
+            const long long gx1 = q[0][0] * qx[0] + q[0][1] * qx[1] + q[0][2] * qx[2];
+            const long long gx2 = q[1][0] * qx[0] + q[1][1] * qx[1] + q[1][2] * qx[2];
+            const i128 vv = mul64x64(ax, det) - (mul64x64(n1, gx1) + mul64x64(n2, gx2));
+            if (vv != 0) {
+                dec = vv > 0 ? 1 : -1;
+            } else {
+                const long long c1 = g22 * gx1 - g12 * gx2, c2 = g11 * gx2 - g12 * gx1;
+                const long long coef[3] = {det - c1 - c2, c1, c2};
+                const int g[3] = {gi, gv[0], gv[1]};
+                dec = sos_violates(3, g, coef, gx) ? -1 : 1;
+            }
+        } else {
+            const int sD = det > 0 ? 1 : -1;
+            i128 vv = mul64x64(ax, det) - (mul64x64(qx[0], N[0]) + mul64x64(qx[1], N[1]) + mul64x64(qx[2], N[2]));
+            if (sD < 0) vv = -vv;
+            if (vv != 0) {
+                dec = vv > 0 ? 1 : -1;
+            } else {
+                const long long D1 = qx[0] * C[0][0] + qx[1] * C[0][1] + qx[2] * C[0][2];
+                const long long D2 = qx[0] * C[1][0] + qx[1] * C[1][1] + qx[2] * C[1][2];
+                const long long D3 = qx[0] * C[2][0] + qx[1] * C[2][1] + qx[2] * C[2][2];
+                const long long coef[4] = {sD * (det - D1 - D2 - D3), sD * D1, sD * D2, sD * D3};
+                const int g[4] = {gi, gv[0], gv[1], gv[2]};
+                dec = sos_violates(4, g, coef, gx) ? -1 : 1;
+            }
+        }
+    }
+    return dec < 0;
+}
+
+__global__ void __launch_bounds__(128) k_resolve(LocalArgs A, int64_t n_pending) {
+    // RESOLVE_LANES lanes per escalated simplex: each works out the exact minors
+    // (the same values), then they share the candidates
+    const int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / RESOLVE_LANES;
+    const int sub = threadIdx.x % RESOLVE_LANES;
+    const unsigned gmask = ((1u << RESOLVE_LANES) - 1u) << ((threadIdx.x & 31) & ~(RESOLVE_LANES - 1));
+    if (j >= n_pending) return;  // the whole group
     DevCounters* cnt = A.cnt;
     const long long Aq = A.pc.A;
     const int4 rec = A.pending[j];
@@ -1083,24 +1173,25 @@ __global__ void k_resolve(LocalArgs A, int64_t n_pending) {
         for (int c = 0; c < 3; c++) N[c] = a[0] * C[0][c] + a[1] * C[1][c] + a[2] * C[2][c];
     }
     if (ac3_open) {
-        atomicAdd(&cnt->ac3_exact, 1ull);
+        if (sub == 0) atomicAdd(&cnt->ac3_exact, 1ull);
         bool ok;
         if (nv == 2)
             ok = det > 0 && mul64x64(n1, a[0]) + mul64x64(n2, a[1]) <= (i128)(4 * det) * (i128)si;
         else
             ok = det != 0 && mul64x64(N[0], N[0]) + mul64x64(N[1], N[1]) + mul64x64(N[2], N[2]) <=
                                  mul64x64(det, det) * (i128)(4 * si);
-        if (!ok) return;
-        atomicAdd(&cnt->n_cand[nv], 1ull);
-        if (A.pc.keep_candidates) {
+        if (!ok) return;  // the whole group
+        if (sub == 0) atomicAdd(&cnt->n_cand[nv], 1ull);
+        if (A.pc.keep_candidates && sub == 0) {
             const int4 item = make_int4(i, v[0], v[1], nv == 3 ? v[2] : 0);
             const unsigned long long slot = atomicAdd(&cnt->n_cand_out[nv], 1ull);
             if ((int64_t)slot < A.cap_cand[nv]) (nv == 3 ? A.cand3 : A.cand2)[slot] = item;
             else atomicOr(&cnt->err, DERR_OVF_CAND);
         }
     }
-    // FP64 orthocentre from the exact minors and its decision threshold
-    double y[3] = {0, 0, 0}, E = 0.0;
+    // FP64 orthocentre from the exact minors and its decision threshold; ey64
+    // bounds |y64_c - y_c| for every c
+    double y[3] = {0, 0, 0}, E = 0.0, ey64 = 0.0;
     if (nv == 2) {
         const double rd = 1.0 / (2.0 * (double)det);
         const double m1 = (double)n1 * rd, m2 = (double)n2 * rd;
@@ -1110,95 +1201,55 @@ __global__ void k_resolve(LocalArgs A, int64_t n_pending) {
             e += fabs(m1) * fabs((double)q[0][c]) + fabs(m2) * fabs((double)q[1][c]);
         }
         e *= 6.05 * 1.1102230246251565e-16 * (1.0 + 1e-10);
+        ey64 = e;
         E = (A.tri_k0_64 + A.tri_k1_64 * e) * (1.0 + 1e-10);
     } else if (nv == 3) {
         const double rd = 1.0 / (2.0 * (double)det);
         for (int c = 0; c < 3; c++) y[c] = (double)N[c] * rd;
+        ey64 = 4.0002 * 1.1102230246251565e-16 * fmax(fabs(y[0]), fmax(fabs(y[1]), fabs(y[2])));
         E = A.tet_eps64;
+    }
+    // filtered mode: an FP32 test first, with y rounded to FP32 from y64 and the
+    // per-atom kernel's FP32 threshold for |y~_c - y_c| <= ey32, where
+    // |y32_c - y_c| <= u32 |y64_c| + ey64 <= 1.0001 u32 |y32_c| + ey64
+    const bool f32 = A.pc.precision == AC_PRECISION_FILTERED && nv >= 2;
+    float yf[3] = {0.f, 0.f, 0.f}, E32 = 0.f;
+    if (f32) {
+        double ymax = 0.0;
+        for (int c = 0; c < 3; c++) {
+            yf[c] = __double2float_rn(y[c]);
+            ymax = fmax(ymax, fabs((double)yf[c]));
+        }
+        const double ey32 = 1.0001 * 5.9604644775390625e-08 * ymax + ey64;
+        const double e32 = ((double)A.b32.K1 * ey32 + (double)A.b32.K0) * (double)A.b32.up1 * (1.0 + 1e-6);
+        E32 = __double2float_ru(e32);
     }
     // candidates: neighbours of i adjacent to every vertex
     const int64_t off = A.nb_stride ? (int64_t)i * A.nb_stride : A.nb_off[i];
     const int m = A.nb_stride ? min((int)A.nb_off[i], A.nb_stride) : (int)(A.nb_off[i + 1] - off);
-    unsigned n64 = 0, nx = 0;
+    unsigned n32 = 0, n64 = 0, nx = 0;
     bool violated = false;
-    // the next candidate's record is fetched while this one is tested
-    int x_next = m > 0 ? A.nb[off] : 0;
-    int4 P_next = m > 0 ? A.Ps[x_next] : make_int4(0, 0, 0, 0);
-    for (int e = 0; e < m && !violated; e++) {
-        const int x = x_next;
-        const int4 Px = P_next;
-        if (e + 1 < m) {
-            x_next = A.nb[off + e + 1];
-            P_next = A.Ps[x_next];
+    for (int e0 = 0; e0 < m; e0 += RESOLVE_LANES) {
+        const int e = e0 + sub;
+        bool viol = false;
+        if (e < m) viol = resolve_one(A, e, off, Pi, Wi, gi, nv, v, q, a, sv, gv, det, g11, g22, g12, n1, n2, C, N, f32, yf,
+                                      E32, y, E, n32, n64, nx);
+        if (__any_sync(gmask, viol)) {
+            violated = true;
+            break;
         }
-        if (x == v[0] || (nv >= 2 && x == v[1]) || (nv == 3 && x == v[2])) continue;
-        const long long sx = (long long)Px.w + Aq;
-        const long long qx[3] = {(long long)Px.x - Pi.x, (long long)Px.y - Pi.y, (long long)Px.z - Pi.z};
-        bool adj = true;
-        for (int t = 0; t < nv && adj; t++) {
-            const long long dx = qx[0] - q[t][0], dy = qx[1] - q[t][1], dz = qx[2] - q[t][2];
-            adj = meet(dx * dx + dy * dy + dz * dz, sv[t], sx);
-        }
-        if (!adj) continue;
-        const long long ax = qx[0] * qx[0] + qx[1] * qx[1] + qx[2] * qx[2] - Px.w + Wi;
-        int dec = 0;
-        if (nv >= 2) {
-            const double t = fma((double)qx[2], y[2], fma((double)qx[1], y[1], (double)qx[0] * y[0]));
-            const double d = fma(-2.0, t, (double)ax);
-            if (d > E) dec = 1;
-            else if (d < -E) dec = -1;
-        }
-        if (dec) {
-            n64++;
-        } else {
-            nx++;
-            const int gx = A.order[x];
-            if (nv == 1) {
-                const long long qq = q[0][0] * qx[0] + q[0][1] * qx[1] + q[0][2] * qx[2];
-                const long long vv = ax * det - a[0] * qq;  // |.| < 2^55
-                if (vv != 0) {
-                    dec = vv > 0 ? 1 : -1;
-                } else {
-                    const long long coef[2] = {det - qq, qq};
-                    const int g[2] = {gi, gv[0]};
-                    dec = sos_violates(2, g, coef, gx) ? -1 : 1;
-                }
-            } else if (nv == 2) {
-                const long long gx1 = q[0][0] * qx[0] + q[0][1] * qx[1] + q[0][2] * qx[2];
-                const long long gx2 = q[1][0] * qx[0] + q[1][1] * qx[1] + q[1][2] * qx[2];
-                const i128 vv = mul64x64(ax, det) - (mul64x64(n1, gx1) + mul64x64(n2, gx2));
-                if (vv != 0) {
-                    dec = vv > 0 ? 1 : -1;
-                } else {
-                    const long long c1 = g22 * gx1 - g12 * gx2, c2 = g11 * gx2 - g12 * gx1;
-                    const long long coef[3] = {det - c1 - c2, c1, c2};
-                    const int g[3] = {gi, gv[0], gv[1]};
-                    dec = sos_violates(3, g, coef, gx) ? -1 : 1;
-                }
-            } else {
-                const int sD = det > 0 ? 1 : -1;
-                i128 vv = mul64x64(ax, det) - (mul64x64(qx[0], N[0]) + mul64x64(qx[1], N[1]) + mul64x64(qx[2], N[2]));
-                if (sD < 0) vv = -vv;
-                if (vv != 0) {
-                    dec = vv > 0 ? 1 : -1;
-                } else {
-                    const long long D1 = qx[0] * C[0][0] + qx[1] * C[0][1] + qx[2] * C[0][2];
-                    const long long D2 = qx[0] * C[1][0] + qx[1] * C[1][1] + qx[2] * C[1][2];
-                    const long long D3 = qx[0] * C[2][0] + qx[1] * C[2][1] + qx[2] * C[2][2];
-                    const long long coef[4] = {sD * (det - D1 - D2 - D3), sD * D1, sD * D2, sD * D3};
-                    const int g[4] = {gi, gv[0], gv[1], gv[2]};
-                    dec = sos_violates(4, g, coef, gx) ? -1 : 1;
-                }
-            }
-        }
-        violated = dec < 0;
-    }
+    }    n32 = __reduce_add_sync(gmask, n32);
+    n64 = __reduce_add_sync(gmask, n64);
+    nx = __reduce_add_sync(gmask, nx);
+    if (sub != 0) return;
     if (nv == 3) {
-        atomicAdd(&cnt->ac2_tet[1], (unsigned long long)n64);
-        atomicAdd(&cnt->ac2_tet[2], (unsigned long long)nx);
+        if (n32) atomicAdd(&cnt->ac2_tet[0], (unsigned long long)n32);
+        if (n64) atomicAdd(&cnt->ac2_tet[1], (unsigned long long)n64);
+        if (nx) atomicAdd(&cnt->ac2_tet[2], (unsigned long long)nx);
     } else if (nv == 2) {
-        atomicAdd(&cnt->ac2_tri[1], (unsigned long long)n64);
-        atomicAdd(&cnt->ac2_tri[2], (unsigned long long)nx);
+        if (n32) atomicAdd(&cnt->ac2_tri[0], (unsigned long long)n32);
+        if (n64) atomicAdd(&cnt->ac2_tri[1], (unsigned long long)n64);
+        if (nx) atomicAdd(&cnt->ac2_tri[2], (unsigned long long)nx);
     } else {
         atomicAdd(&cnt->ac2_edge, (unsigned long long)(n64 + nx));
     }
@@ -1398,7 +1449,7 @@ int run_local(ac_ctx* c, cudaStream_t s) {
             const BuildRecord& r = c->rec;
             AC_TRY(expect_u64(c, &dc->n_pending, (unsigned long long)r.n_pending, s));
             if (r.n_pending > 0) {
-                k_resolve<<<(unsigned)((r.n_pending + 127) / 128), 128, 0, s>>>(a, r.n_pending);
+                k_resolve<<<(unsigned)((r.n_pending * RESOLVE_LANES + 127) / 128), 128, 0, s>>>(a, r.n_pending);
                 AC_LAUNCHED();
             }
             AC_TRY(expect_u64(c, &dc->n_tet_out, r.post.n_tet_out, s));
@@ -1415,7 +1466,7 @@ int run_local(ac_ctx* c, cudaStream_t s) {
             c->cap_pending = (int64_t)(h.n_pending * 5 / 4) + 4096;
             again = true;
         } else if (h.n_pending > 0) {
-            k_resolve<<<(unsigned)((h.n_pending + 127) / 128), 128, 0, s>>>(a, (int64_t)h.n_pending);
+            k_resolve<<<(unsigned)((h.n_pending * RESOLVE_LANES + 127) / 128), 128, 0, s>>>(a, (int64_t)h.n_pending);
             AC_LAUNCHED();
             AC_TRY(read_counters(c, &h, s));
         }
