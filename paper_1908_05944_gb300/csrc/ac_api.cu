@@ -483,6 +483,80 @@ using namespace ac;
 // ---------------------------------------------------------------------------
 // public API
 
+// The CUDA objects of a context (timing events, fork/join events, the side and
+// capture streams, the page-locked readback block) come from a small
+// process-wide cache: creating and destroying them costs more than a small
+// build, and applications create contexts one after another. A destroyed
+// context's objects are idle (ac_destroy synchronises the device first).
+struct CtxRes {
+    int device = -1;
+    cudaEvent_t ev[10] = {};
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaStream_t side = nullptr, cap_stream = nullptr;
+    void* pinned = nullptr;
+    size_t pinned_bytes = 0;
+};
+
+static std::mutex g_res_mu;
+static std::vector<CtxRes> g_res;  // at most RES_CACHE entries
+constexpr size_t RES_CACHE = 8;
+
+static void res_free(CtxRes& r) {
+    for (int k = 0; k < 10; k++)
+        if (r.ev[k]) cudaEventDestroy(r.ev[k]);
+    if (r.ev_fork) cudaEventDestroy(r.ev_fork);
+    if (r.ev_join) cudaEventDestroy(r.ev_join);
+    if (r.side) cudaStreamDestroy(r.side);
+    if (r.cap_stream) cudaStreamDestroy(r.cap_stream);
+    if (r.pinned) cudaFreeHost(r.pinned);
+    r = CtxRes{};
+}
+
+// a cached set for this device with at least pinned_bytes of readback block, or a new one
+static int res_take(size_t pinned_bytes, CtxRes& out) {
+    int dev = 0;
+    AC_CUDA(cudaGetDevice(&dev));
+    {
+        std::lock_guard<std::mutex> lk(g_res_mu);
+        for (size_t k = 0; k < g_res.size(); k++)
+            if (g_res[k].device == dev && g_res[k].pinned_bytes >= pinned_bytes) {
+                out = g_res[k];
+                g_res.erase(g_res.begin() + (long)k);
+                return AC_OK;
+            }
+    }
+    CtxRes r;
+    r.device = dev;
+    bool ok = true;
+    for (int k = 0; k < 10 && ok; k++) ok = cudaEventCreate(&r.ev[k]) == cudaSuccess;
+    ok = ok && cudaEventCreateWithFlags(&r.ev_fork, cudaEventDisableTiming) == cudaSuccess &&
+         cudaEventCreateWithFlags(&r.ev_join, cudaEventDisableTiming) == cudaSuccess &&
+         cudaStreamCreateWithFlags(&r.side, cudaStreamNonBlocking) == cudaSuccess &&
+         cudaStreamCreateWithFlags(&r.cap_stream, cudaStreamNonBlocking) == cudaSuccess &&
+         cudaMallocHost(&r.pinned, pinned_bytes) == cudaSuccess;
+    if (!ok) {
+        const cudaError_t e = cudaGetLastError();
+        res_free(r);
+        return cuda_fail(e, "context events, streams or page-locked block", __FILE__, __LINE__);
+    }
+    r.pinned_bytes = pinned_bytes;
+    out = r;
+    return AC_OK;
+}
+
+static void res_give(CtxRes& r) {
+    if (r.device < 0) return;
+    {
+        std::lock_guard<std::mutex> lk(g_res_mu);
+        if (g_res.size() < RES_CACHE) {
+            g_res.push_back(r);
+            r = CtxRes{};
+            return;
+        }
+    }
+    res_free(r);
+}
+
 static int create_impl(const double* centres, const double* radii, const int64_t* offsets, int64_t n_mol,
                        double alpha, const ac_options* opt, ac_ctx** out) {
     if (!out) return fail(AC_ERR_INVALID_ARG, "out is NULL");
@@ -516,19 +590,22 @@ static int create_impl(const double* centres, const double* radii, const int64_t
         ac_destroy(c);
         return code;
     };
-    for (int k = 0; k < 10; k++)
-        if (cudaEventCreate(&c->ev[k]) != cudaSuccess) return bail(cuda_fail(cudaGetLastError(), "cudaEventCreate", __FILE__, __LINE__));
-    if (cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess ||
-        cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
-        return bail(cuda_fail(cudaGetLastError(), "side stream", __FILE__, __LINE__));
     {
         const size_t a0 = 64 * sizeof(int64_t), a1 = (sizeof(DevCounters) + 255) & ~(size_t)255;
         const size_t a2 = ((size_t)6 * n_mol * sizeof(int32_t) + 255) & ~(size_t)255;
         const size_t a3 = (size_t)7 * (n_mol + 1) * sizeof(int64_t);
-        if (cudaMallocHost(&c->h_pinned, a0 + a1 + a2 + a3) != cudaSuccess)
-            return bail(cuda_fail(cudaGetLastError(), "cudaMallocHost", __FILE__, __LINE__));
+        // small blocks share one size class, so cached sets fit most contexts
+        const size_t need = std::max<size_t>(a0 + a1 + a2 + a3, 64 * 1024);
+        CtxRes r;
+        if ((rc = res_take(need, r))) return bail(rc);
+        for (int k = 0; k < 10; k++) c->ev[k] = r.ev[k];
+        c->ev_fork = r.ev_fork;
+        c->ev_join = r.ev_join;
+        c->side = r.side;
+        c->cap_stream = r.cap_stream;
+        c->h_pinned = r.pinned;
+        c->h_pinned_bytes = r.pinned_bytes;
+        c->res_device = r.device;
         char* b = static_cast<char*>(c->h_pinned);
         c->h_stage = reinterpret_cast<int64_t*>(b);
         c->h_cnt = reinterpret_cast<DevCounters*>(b + a0);
@@ -887,13 +964,20 @@ extern "C" void ac_destroy(ac_ctx* c) {
     cudaDeviceSynchronize();
     StreamScope scope(nullptr);
     drop_graph(c);
-    for (int k = 0; k < 10; k++)
-        if (c->ev[k]) cudaEventDestroy(c->ev[k]);
-    if (c->h_pinned) cudaFreeHost(c->h_pinned);
-    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
-    if (c->ev_join) cudaEventDestroy(c->ev_join);
-    if (c->side) cudaStreamDestroy(c->side);
-    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    CtxRes r;
+    r.device = c->res_device;
+    for (int k = 0; k < 10; k++) r.ev[k] = c->ev[k];
+    r.ev_fork = c->ev_fork;
+    r.ev_join = c->ev_join;
+    r.side = c->side;
+    r.cap_stream = c->cap_stream;
+    r.pinned = c->h_pinned;
+    r.pinned_bytes = c->h_pinned_bytes;
+    // a set from a failed creation is incomplete: free it rather than cache it
+    bool whole = r.device >= 0 && r.pinned && r.side && r.cap_stream && r.ev_fork && r.ev_join;
+    for (int k = 0; k < 10; k++) whole = whole && r.ev[k];
+    if (whole && cudaGetLastError() == cudaSuccess) res_give(r);
+    else res_free(r);
     delete c;
 }
 

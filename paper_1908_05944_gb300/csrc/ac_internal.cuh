@@ -268,6 +268,8 @@ struct ac_ctx {
     ac::CanonWork cw;
 
     ac_stats stats{};
+    int res_device = -1;        // device of the cached CUDA objects below
+    size_t h_pinned_bytes = 0;
     cudaEvent_t ev[10] = {};  // stage boundaries; ev[8], ev[9] bracket the per-atom kernel
     cudaStream_t side = nullptr;                    // wide-row launch, concurrent with the narrow one
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
