@@ -387,9 +387,14 @@ __global__ void k_canon_write(CanonWriteArgs a) {
 
 using Work = CanonWork;
 
+// the items were unique: the de-duplicated total must equal their number
+__global__ void k_check_total(const int64_t* __restrict__ total, int64_t want, unsigned* __restrict__ err) {
+    if (*total != want) atomicOr(err, DERR_INTERNAL);
+}
+
 template <int K>
 static int canon_dim_k(ac_ctx* c, const int4* a4, const int2* a2, int64_t nA, const int4* cof, int64_t nB,
-                       SimplexList& L, DevBuf& Gout, Work& w, cudaStream_t s) {
+                       SimplexList& L, DevBuf& Gout, Work& w, cudaStream_t s, bool unique) {
     const int64_t n = c->n;
     const int64_t total = nA + nB * (K + 1);
     AC_TRY(w.T.reserve((size_t)(total + 1) * sizeof(int4), s));
@@ -430,6 +435,11 @@ static int canon_dim_k(ac_ctx* c, const int4* a4, const int2* a2, int64_t nA, co
     int64_t count = L.count;  // a replay keeps the recorded build's count and checks it
     if (c->replaying) {
         AC_TRY(expect_i64(c, uoff + n, count, s));
+    } else if (unique) {
+        // items emitted once each (by their owner): their number is the count, checked on the device
+        count = total;
+        k_check_total<<<1, 1, 0, s>>>(uoff + n, total, &c->counters.as<DevCounters>()->err);
+        AC_LAUNCHED();
     } else {
         AC_CUDA(cudaMemcpyAsync(c->h_stage, uoff + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
         AC_TRY(sync_host(c, s));
@@ -454,11 +464,11 @@ static int canon_dim_k(ac_ctx* c, const int4* a4, const int2* a2, int64_t nA, co
 }
 
 static int canon_dim(ac_ctx* c, int d, const int4* a4, const int2* a2, int64_t nA, const int4* cof, int64_t nB,
-                     SimplexList& L, DevBuf& Gout, Work& w, cudaStream_t s) {
+                     SimplexList& L, DevBuf& Gout, Work& w, cudaStream_t s, bool unique = false) {
     switch (d) {
-        case 1: return canon_dim_k<2>(c, a4, a2, nA, cof, nB, L, Gout, w, s);
-        case 2: return canon_dim_k<3>(c, a4, a2, nA, cof, nB, L, Gout, w, s);
-        default: return canon_dim_k<4>(c, a4, a2, nA, cof, nB, L, Gout, w, s);
+        case 1: return canon_dim_k<2>(c, a4, a2, nA, cof, nB, L, Gout, w, s, unique);
+        case 2: return canon_dim_k<3>(c, a4, a2, nA, cof, nB, L, Gout, w, s, unique);
+        default: return canon_dim_k<4>(c, a4, a2, nA, cof, nB, L, Gout, w, s, unique);
     }
 }
 
@@ -710,14 +720,27 @@ __device__ __forceinline__ void nb_row_of(const int64_t* __restrict__ nb_off, in
 
 __device__ __forceinline__ int64_t pair_words(int m) { return ((int64_t)m * (m - 1) / 2 + 31) / 32; }
 
-// mask words of every sorted position
-__global__ void k_pair_words(const int64_t* __restrict__ nb_off, int stride, int64_t n, int64_t* __restrict__ pw) {
+// mask words of every sorted position, from the neighbour counts
+__global__ void k_pair_words(const int64_t* __restrict__ nb_cnt, int64_t n, int64_t* __restrict__ pw) {
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
-    int64_t off;
-    int m;
-    nb_row_of(nb_off, stride, (int)s, off, m);
-    pw[s] = pair_words(m);
+    pw[s] = pair_words((int)nb_cnt[s]);
+}
+
+// The pair-mask layout of the K^2 marks (first word of each sorted position,
+// n + 1, into c->pair_moff) from the neighbour counts, before those become
+// offsets; the caller reads the total (pair_moff[n]) with its other sizes.
+int plan_pair_masks(ac_ctx* c, const int64_t* nb_cnt, cudaStream_t s) {
+    const int64_t n = c->n;
+    const size_t nn = (size_t)(n > 0 ? n : 1);
+    AC_TRY(c->pair_moff.reserve((nn + 1) * sizeof(int64_t), s));
+    AC_TRY(c->cw.cnt.reserve((nn + 1) * sizeof(int64_t), s));
+    int64_t* pw = c->cw.cnt.as<int64_t>();
+    if (n > 0) {
+        k_pair_words<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(nb_cnt, n, pw);
+        AC_LAUNCHED();
+    }
+    return scan_exclusive_i64(c, pw, c->pair_moff.as<int64_t>(), n, s);
 }
 
 __device__ __forceinline__ void mark_pair(const TriMarkArgs& a, int sa, int e1, int e2, bool fr) {
@@ -874,27 +897,13 @@ static int canon_tris_by_marks(ac_ctx* c, cudaStream_t s) {
     SimplexList& L = c->K[2];
     Work& w = c->cw;
     const size_t nn = (size_t)(n > 0 ? n : 1);
-    DevBuf& moffb = c->pair_moff;
     DevBuf& masks = c->scratch[2];
-    AC_TRY(moffb.reserve((nn + 1) * sizeof(int64_t), s));
     AC_TRY(w.cnt.reserve((nn + 1) * sizeof(int64_t), s));
     AC_TRY(L.v0_off.reserve((nn + 1) * sizeof(int64_t), s));
-    int64_t* moff = moffb.as<int64_t>();
+    // first mask word of each sorted position and their total: from the neighbour pass
+    const int64_t* moff = c->pair_moff.as<int64_t>();
     int64_t* cnt = w.cnt.as<int64_t>();
-    if (n > 0) {
-        k_pair_words<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(c->nb_cnt.as<int64_t>(), c->nb_stride, n, cnt);
-        AC_LAUNCHED();
-    }
-    AC_TRY(scan_exclusive_i64(c, cnt, moff, n, s));
-    int64_t words = c->pair_words;
-    if (c->replaying) {
-        AC_TRY(expect_i64(c, moff + n, words, s));
-    } else {
-        AC_CUDA(cudaMemcpyAsync(c->h_stage, moff + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-        AC_TRY(sync_host(c, s));
-        words = c->h_stage[0];
-    }
-    c->pair_words = words;
+    const int64_t words = c->pair_words;
     const size_t mw = (size_t)(words > 0 ? words : 1);
     AC_TRY(masks.reserve(2 * mw * sizeof(unsigned), s));
     AC_CUDA(cudaMemsetAsync(masks.p, 0, 2 * mw * sizeof(unsigned), s));
@@ -994,7 +1003,8 @@ int canonicalise(ac_ctx* c, cudaStream_t s) {
     Work& w = c->cw;
     const int64_t n = c->n;
     // K^3
-    AC_TRY(canon_dim(c, 3, c->tet_out.as<int4>(), nullptr, (int64_t)h.n_tet_out, nullptr, 0, c->K[3], c->Gbuf[3], w, s));
+    AC_TRY(canon_dim(c, 3, c->tet_out.as<int4>(), nullptr, (int64_t)h.n_tet_out, nullptr, 0, c->K[3], c->Gbuf[3], w, s,
+                     true));
     AC_TRY(fork_orthosize(c, 3, s));
     AC_TRY(stage_mark(c, 4, s));
     // K^2 = unattached triangles + facets of K^3

@@ -251,6 +251,7 @@ int build_neighbours(ac_ctx* c, cudaStream_t s) {
         c->nb_total = 0;
         c->n_wide = 0;
         c->nb_stride = 0;
+        c->pair_words = 0;
         AC_CUDA(cudaMemsetAsync(cntp, 0, sizeof(int64_t), s));
         AC_TRY(c->nb.reserve(4, s));
         return AC_OK;
@@ -270,6 +271,8 @@ int build_neighbours(ac_ctx* c, cudaStream_t s) {
         k<<<nb, 128, 0, s>>>(g.Ps, g.mol_s, g.grids, g.cell_start, c->pc, n, cntp, nullptr, nullptr, dc);
     }
     AC_LAUNCHED();
+    // layout of the K^2 pair masks, from the counts
+    AC_TRY(plan_pair_masks(c, cntp, s));
     // work order from the counts (before a scan turns them into offsets)
     AC_TRY(c->work.reserve((size_t)n * sizeof(int32_t), s));
     AC_TRY(c->deg.reserve(2 * DEG_BINS * sizeof(unsigned) + 64, s));
@@ -291,12 +294,16 @@ int build_neighbours(ac_ctx* c, cudaStream_t s) {
         c->n_wide = c->rec.n_wide;
         AC_TRY(expect_u64(c, &dc->nb_sum, (unsigned long long)total, s));
         AC_TRY(expect_i64(c, reinterpret_cast<const int64_t*>(n_wide), c->n_wide, s));
+        AC_TRY(expect_i64(c, c->pair_moff.as<int64_t>() + n, c->pair_words, s));
     } else {
         AC_CUDA(cudaMemcpyAsync(c->h_stage + 1, n_wide, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        AC_CUDA(cudaMemcpyAsync(c->h_stage + 2, c->pair_moff.as<int64_t>() + n, sizeof(int64_t),
+                                cudaMemcpyDeviceToHost, s));
         DevCounters h;
-        AC_TRY(read_counters(c, &h, s));  // also completes the copy above
+        AC_TRY(read_counters(c, &h, s));  // also completes the copies above
         total = (int64_t)h.nb_sum;
         c->n_wide = c->h_stage[1];
+        c->pair_words = c->h_stage[2];
         if (h.err & DERR_COINCIDENT)
             return fail(AC_ERR_DEGENERATE, "two centres coincide after quantisation to 1/1024 A");
         if (h.max_degree > NB_STRIDE) compact = true;  // rows too short: redo as compact lists

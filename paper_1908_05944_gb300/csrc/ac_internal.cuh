@@ -284,6 +284,7 @@ int scan_exclusive_i64(ac_ctx* c, const int64_t* in, int64_t* out, int64_t n, cu
 int scan_exclusive_u32_to_u32(ac_ctx* c, const uint32_t* in, uint32_t* out, int64_t n, cudaStream_t s);
 
 int quantise_and_plan(ac_ctx* c, cudaStream_t s);
+int plan_pair_masks(ac_ctx* c, const int64_t* nb_cnt, cudaStream_t s);
 int build_grid(ac_ctx* c, cudaStream_t s);
 int build_neighbours(ac_ctx* c, cudaStream_t s);
 int run_local(ac_ctx* c, cudaStream_t s);

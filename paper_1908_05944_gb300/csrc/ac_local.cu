@@ -1122,13 +1122,10 @@ __device__ __forceinline__ bool resolve_one(const LocalArgs& A, int e, int64_t o
     return dec < 0;
 }
 
-__global__ void __launch_bounds__(128) k_resolve(LocalArgs A, int64_t n_pending) {
-    // RESOLVE_LANES lanes per escalated simplex: each works out the exact minors
-    // (the same values), then they share the candidates
-    const int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / RESOLVE_LANES;
-    const int sub = threadIdx.x % RESOLVE_LANES;
-    const unsigned gmask = ((1u << RESOLVE_LANES) - 1u) << ((threadIdx.x & 31) & ~(RESOLVE_LANES - 1));
-    if (j >= n_pending) return;  // the whole group
+// Escalated simplex j, settled by the RESOLVE_LANES lanes of gmask (sub is this
+// lane's place among them): each works out the exact minors (the same values),
+// then they share the candidates. Every return is taken by the whole group.
+__device__ __forceinline__ void resolve_item(const LocalArgs& A, int64_t j, int sub, unsigned gmask) {
     DevCounters* cnt = A.cnt;
     const long long Aq = A.pc.A;
     const int4 rec = A.pending[j];
@@ -1269,6 +1266,19 @@ __global__ void __launch_bounds__(128) k_resolve(LocalArgs A, int64_t n_pending)
     }
 }
 
+// One group of RESOLVE_LANES lanes per escalated simplex, grid-stride over the
+// list. n_pending < 0: the count the per-atom pass left on the device (at most
+// the list's capacity), so a synchronised build need not read it first.
+__global__ void __launch_bounds__(128) k_resolve(LocalArgs A, int64_t n_pending) {
+    const int sub = threadIdx.x % RESOLVE_LANES;
+    const unsigned gmask = ((1u << RESOLVE_LANES) - 1u) << ((threadIdx.x & 31) & ~(RESOLVE_LANES - 1));
+    const int64_t np = n_pending >= 0 ? n_pending
+                                      : (int64_t)min(A.cnt->n_pending, (unsigned long long)A.cap_pending);
+    const int64_t groups = (int64_t)gridDim.x * blockDim.x / RESOLVE_LANES;
+    for (int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / RESOLVE_LANES; j < np; j += groups)
+        resolve_item(A, j, sub, gmask);
+}
+
 // ---------------------------------------------------------------------------
 
 template <int WORDS, class R>
@@ -1375,6 +1385,13 @@ static void set_constants(const PredConst& pc, int64_t wmax, LocalArgs& a) {
     a.tri_k1_64 = nextafter((2 * g3d * H + 2 * H) * s3 * sf * (1 + 1e-12), INFINITY);
 }
 
+// blocks of k_resolve for up to `items` escalated simplices: one group per
+// simplex, at most a few resident waves (the kernel strides over the rest)
+static unsigned resolve_blocks(int64_t items) {
+    const int64_t want = (items * RESOLVE_LANES + 127) / 128;
+    return (unsigned)std::max<int64_t>(1, std::min<int64_t>(want, 152 * 16 * 4));
+}
+
 int run_local(ac_ctx* c, cudaStream_t s) {
     const int64_t n = c->n;
     DevCounters h = c->replaying ? c->rec.post : c->hc;  // read after the neighbour count pass
@@ -1449,7 +1466,7 @@ int run_local(ac_ctx* c, cudaStream_t s) {
             const BuildRecord& r = c->rec;
             AC_TRY(expect_u64(c, &dc->n_pending, (unsigned long long)r.n_pending, s));
             if (r.n_pending > 0) {
-                k_resolve<<<(unsigned)((r.n_pending * RESOLVE_LANES + 127) / 128), 128, 0, s>>>(a, r.n_pending);
+                k_resolve<<<resolve_blocks(r.n_pending), 128, 0, s>>>(a, r.n_pending);
                 AC_LAUNCHED();
             }
             AC_TRY(expect_u64(c, &dc->n_tet_out, r.post.n_tet_out, s));
@@ -1459,16 +1476,17 @@ int run_local(ac_ctx* c, cudaStream_t s) {
             c->hc = r.post;
             return AC_OK;
         }
+        // the resolve kernel sized by the list's capacity, reading the count on the device: one host wait
+        if (c->cap_pending > 0) {
+            k_resolve<<<resolve_blocks(c->cap_pending), 128, 0, s>>>(a, -1);
+            AC_LAUNCHED();
+        }
         AC_TRY(read_counters(c, &h, s));
         if (h.err & DERR_DEGREE) return fail(AC_ERR_CAPACITY, "neighbour list wider than the kernel's masks");
         bool again = false;
         if ((int64_t)h.n_pending > c->cap_pending) {
             c->cap_pending = (int64_t)(h.n_pending * 5 / 4) + 4096;
             again = true;
-        } else if (h.n_pending > 0) {
-            k_resolve<<<(unsigned)((h.n_pending * RESOLVE_LANES + 127) / 128), 128, 0, s>>>(a, (int64_t)h.n_pending);
-            AC_LAUNCHED();
-            AC_TRY(read_counters(c, &h, s));
         }
         if ((int64_t)h.n_tet_out > c->cap_tet) {
             c->cap_tet = (int64_t)(h.n_tet_out * 5 / 4) + 1024;
