@@ -753,13 +753,18 @@ static int record_build(ac_ctx* c, const DevCounters& post, cudaStream_t s) {
     r.n_pending = (int64_t)post.n_pending;
     for (int d = 0; d < 4; d++) r.count[d] = c->K[d].count;
     for (int d = 1; d < 4; d++) r.count[3 + d] = c->C[d].count;
+    r.valid = true;
+    return AC_OK;
+}
+
+// The plan bounds a replay checks against, copied before the build's last host
+// wait (which then also completes them, before a replay on another stream reads them).
+static int record_copies(ac_ctx* c, cudaStream_t s) {
     const size_t nb = (size_t)c->n_mol * 6;
     AC_TRY(c->rec_bbox.reserve((nb + 1) * sizeof(int32_t), s));
     AC_CUDA(cudaMemcpyAsync(c->rec_bbox.p, c->scratch[0].p, nb * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
     AC_CUDA(cudaMemcpyAsync(c->rec_bbox.as<int32_t>() + nb, c->scratch[1].p, sizeof(int32_t), cudaMemcpyDeviceToDevice,
                             s));
-    AC_TRY(sync_host(c, s));  // the copies finish before a replay on another stream reads them
-    r.valid = true;
     return AC_OK;
 }
 
@@ -794,6 +799,7 @@ extern "C" int ac_build(ac_ctx* c, void* stream) {
     if (!replayed) {
         drop_graph(c);
         AC_TRY(build_body(c, s));
+        if (!c->opt.no_graph) AC_TRY(record_copies(c, s));
         AC_TRY(read_counters(c, &h, s));
     }
     if (h.err & DERR_INTERNAL) return fail(AC_ERR_CUDA, "internal: attached simplex without a coface in the complex");

@@ -280,7 +280,7 @@ __device__ void sort_big_bucket(int4* __restrict__ T, int64_t a, int64_t b, int6
 
 template <int K>
 __global__ void __launch_bounds__(CSORT_WARPS * 32) k_canon_sort(int4* __restrict__ T, const int64_t* __restrict__ off,
-                                                                  int64_t n, int64_t* __restrict__ uniq) {
+                                                                  int64_t n, int64_t* __restrict__ uniq, bool unique) {
     __shared__ SortSmem sm[CSORT_WARPS];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     SortSmem& S = sm[w];
@@ -289,6 +289,27 @@ __global__ void __launch_bounds__(CSORT_WARPS * 32) k_canon_sort(int4* __restric
         const int64_t a = off[g];
         const int64_t kb = off[g + 1] - a;
         const int k = kb > CSORT_MAX ? CSORT_MAX + 1 : (int)kb;
+        if (unique && k <= 32) {
+            // distinct items (nothing to merge), one per lane: each takes its rank among the others
+            int4 t = make_int4(0, 0, 0, 0);
+            unsigned long long hi = ~0ull;
+            unsigned lo = ~0u;
+            if (lane < k) {
+                t = T[a + lane];
+                make_key<K>(t, hi, lo);
+            }
+            int r = 0;
+            for (int u = 0; u < k; u++) {
+                const unsigned long long hu = __shfl_sync(0xffffffffu, hi, u);
+                const unsigned lu = __shfl_sync(0xffffffffu, lo, u);
+                r += key_less<K, unsigned long long>(hu, lu, hi, lo) ? 1 : 0;
+            }
+            __syncwarp();
+            if (lane < k) T[a + r] = t;
+            if (lane == 0) uniq[g] = k;
+            __syncwarp();
+            continue;
+        }
         if (k > CSORT_MAX) {
             if (lane == 0) sort_big_bucket<K>(T, a, a + kb, &uniq[g]);
             __syncwarp();
@@ -427,11 +448,14 @@ static int canon_dim_k(ac_ctx* c, const int4* a4, const int2* a2, int64_t nA, co
         // one resident wave, buckets taken grid-stride
         int64_t blocks = (n + CSORT_WARPS - 1) / CSORT_WARPS;
         if (blocks > (int64_t)sms * (per_sm > 0 ? per_sm : 1)) blocks = (int64_t)sms * (per_sm > 0 ? per_sm : 1);
-        k_canon_sort<K><<<(unsigned)blocks, CSORT_WARPS * 32, 0, s>>>(w.T.as<int4>(), cnt, n, uniq);
+        k_canon_sort<K><<<(unsigned)blocks, CSORT_WARPS * 32, 0, s>>>(w.T.as<int4>(), cnt, n, uniq, unique);
         AC_LAUNCHED();
     }
     int64_t* uoff = L.v0_off.as<int64_t>();
-    AC_TRY(scan_exclusive_i64(c, uniq, uoff, n, s));
+    if (unique)  // every item is a row: the rows start where the buckets do
+        AC_CUDA(cudaMemcpyAsync(uoff, cnt, (size_t)(n + 1) * sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
+    else
+        AC_TRY(scan_exclusive_i64(c, uniq, uoff, n, s));
     int64_t count = L.count;  // a replay keeps the recorded build's count and checks it
     if (c->replaying) {
         AC_TRY(expect_i64(c, uoff + n, count, s));
@@ -1066,8 +1090,9 @@ int canonicalise(ac_ctx* c, cudaStream_t s) {
     if (c->pc.keep_candidates) {
         for (int d = 1; d <= 3; d++) {
             int64_t m = (int64_t)h.n_cand_out[d];
+            // each candidate is emitted once, by its owner
             AC_TRY(canon_dim(c, d, d >= 2 ? c->cand[d].as<int4>() : nullptr, d == 1 ? c->cand[1].as<int2>() : nullptr, m,
-                             nullptr, 0, c->C[d], c->CGbuf[d], w, s));
+                             nullptr, 0, c->C[d], c->CGbuf[d], w, s, true));
         }
     }
     // per-molecule row ranges, copied to the host with the build's last transfer
