@@ -604,7 +604,8 @@ constexpr int EW_WARPS = 4;
 __global__ void __launch_bounds__(EW_WARPS * 32) k_edge_write(EdgeMarkArgs a, int64_t n, const int64_t* __restrict__ uoff,
                                                               const int32_t* __restrict__ mol_of,
                                                               const int64_t* __restrict__ mol_off, int4* __restrict__ G,
-                                                              int32_t* __restrict__ out, uint8_t* __restrict__ attached) {
+                                                              int32_t* __restrict__ out, uint8_t* __restrict__ attached,
+                                                              uint8_t* __restrict__ endpoint) {
     __shared__ int hs_all[EW_WARPS][256];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     int* hs = hs_all[wib];
@@ -631,6 +632,8 @@ __global__ void __launch_bounds__(EW_WARPS * 32) k_edge_write(EdgeMarkArgs a, in
         c += __popc(bits);
     }
     __syncwarp();
+    // the vertices of K^1 (Step 5: endpoints are in K^0); only ones are written
+    if (lane == 0 && c > 0) endpoint[g] = 1;
     // pass 2: rank each compacted entry among the others
     for (int k = lane; k < c; k += 32) {
         const int h = hs[k];
@@ -650,6 +653,7 @@ __global__ void __launch_bounds__(EW_WARPS * 32) k_edge_write(EdgeMarkArgs a, in
         out[row * 2 + 0] = (int)g - base;
         out[row * 2 + 1] = h - base;
         attached[row] = (fw[w] >> e) & 1u ? 0 : 1;
+        endpoint[h] = 1;
     }
 }
 
@@ -698,10 +702,13 @@ static int canon_edges_by_marks(ac_ctx* c, cudaStream_t s) {
     AC_TRY(L.src_dim.reserve(rows, s));
     AC_TRY(L.src_idx.reserve(rows * sizeof(int64_t), s));
     AC_TRY(c->Gbuf[1].reserve(rows * sizeof(int4), s));
+    AC_TRY(w.big.reserve(nn, s));  // endpoint flags of K^1, for K^0
+    AC_CUDA(cudaMemsetAsync(w.big.p, 0, nn, s));
     if (n > 0) {
         k_edge_write<<<(unsigned)((n + EW_WARPS - 1) / EW_WARPS), EW_WARPS * 32, 0, s>>>(a, n, uoff, c->mol_of.as<int32_t>(),
                                                                   c->d_moloff.as<int64_t>(), c->Gbuf[1].as<int4>(),
-                                                                  L.tuples.as<int32_t>(), L.attached.as<uint8_t>());
+                                                                  L.tuples.as<int32_t>(), L.attached.as<uint8_t>(),
+                                                                  w.big.as<uint8_t>());
         AC_LAUNCHED();
     }
     return AC_OK;
@@ -742,28 +749,14 @@ __device__ __forceinline__ void nb_row_of(const int64_t* __restrict__ nb_off, in
     }
 }
 
-__device__ __forceinline__ int64_t pair_words(int m) { return ((int64_t)m * (m - 1) / 2 + 31) / 32; }
-
-// mask words of every sorted position, from the neighbour counts
-__global__ void k_pair_words(const int64_t* __restrict__ nb_cnt, int64_t n, int64_t* __restrict__ pw) {
-    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= n) return;
-    pw[s] = pair_words((int)nb_cnt[s]);
-}
 
 // The pair-mask layout of the K^2 marks (first word of each sorted position,
-// n + 1, into c->pair_moff) from the neighbour counts, before those become
-// offsets; the caller reads the total (pair_moff[n]) with its other sizes.
-int plan_pair_masks(ac_ctx* c, const int64_t* nb_cnt, cudaStream_t s) {
+// n + 1, into c->pair_moff) from the words per atom the neighbour pass wrote;
+// the caller reads the total (pair_moff[n]) with its other sizes.
+int plan_pair_masks(ac_ctx* c, const int64_t* pw, cudaStream_t s) {
     const int64_t n = c->n;
     const size_t nn = (size_t)(n > 0 ? n : 1);
     AC_TRY(c->pair_moff.reserve((nn + 1) * sizeof(int64_t), s));
-    AC_TRY(c->cw.cnt.reserve((nn + 1) * sizeof(int64_t), s));
-    int64_t* pw = c->cw.cnt.as<int64_t>();
-    if (n > 0) {
-        k_pair_words<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(nb_cnt, n, pw);
-        AC_LAUNCHED();
-    }
     return scan_exclusive_i64(c, pw, c->pair_moff.as<int64_t>(), n, s);
 }
 
@@ -973,15 +966,8 @@ static int canon_tris_by_marks(ac_ctx* c, cudaStream_t s) {
     return AC_OK;
 }
 
-// Vertices (Step 5): K^0 = endpoints of K^1 + atoms whose centre passes AC2.
-__global__ void k_mark_endpoints(const int4* __restrict__ E, int64_t m, uint8_t* __restrict__ endpoint) {
-    int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= m) return;
-    int4 e = E[j];
-    endpoint[e.x] = 1;
-    endpoint[e.y] = 1;
-}
-
+// Vertices (Step 5): K^0 = endpoints of K^1 (flagged by k_edge_write) + atoms
+// whose centre passes AC2.
 __global__ void k_vertex_flags(const uint8_t* __restrict__ endpoint, const uint8_t* __restrict__ vert_pass,
                                const int32_t* __restrict__ rank, int64_t n, int64_t* __restrict__ inK) {
     int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -1045,13 +1031,7 @@ int canonicalise(ac_ctx* c, cudaStream_t s) {
         AC_TRY(w.big.reserve(nn, s));
         AC_TRY(w.cnt.reserve((nn + 1) * sizeof(int64_t), s));
         AC_TRY(L.v0_off.reserve((nn + 1) * sizeof(int64_t), s));
-        uint8_t* endpoint = w.big.as<uint8_t>();
-        AC_CUDA(cudaMemsetAsync(endpoint, 0, nn, s));
-        if (c->K[1].count > 0) {
-            k_mark_endpoints<<<(unsigned)((c->K[1].count + 255) / 256), 256, 0, s>>>(c->Gbuf[1].as<int4>(), c->K[1].count,
-                                                                                    endpoint);
-            AC_LAUNCHED();
-        }
+        uint8_t* endpoint = w.big.as<uint8_t>();  // set by k_edge_write
         int64_t* inK = w.cnt.as<int64_t>();
         if (n > 0) {
             k_vertex_flags<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(endpoint, c->vert_pass.as<uint8_t>(),

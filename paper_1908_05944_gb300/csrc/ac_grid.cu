@@ -125,7 +125,7 @@ template <int MODE, bool GUARD>
 __global__ void k_neighbours(const int4* __restrict__ Ps, const int32_t* __restrict__ mol_s,
                              const MolGrid* __restrict__ grids, const uint32_t* __restrict__ cell_start,
                              PredConst pc, int64_t n, int64_t* __restrict__ nb_cnt, const int64_t* __restrict__ nb_off,
-                             int32_t* __restrict__ nb, DevCounters* __restrict__ cnt) {
+                             int32_t* __restrict__ nb, DevCounters* __restrict__ cnt, int64_t* __restrict__ pw) {
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int64_t count = 0;
     if (s < n) {
@@ -182,6 +182,7 @@ __global__ void k_neighbours(const int4* __restrict__ Ps, const int32_t* __restr
         }
         if (MODE != NB_CSR) {
             nb_cnt[s] = count;
+            pw[s] = pair_mask_words((int)count);  // the K^2 pair mask of this atom
             atomicMax(&cnt->max_degree, (int)count);
         }
     }
@@ -262,17 +263,19 @@ int build_neighbours(ac_ctx* c, cudaStream_t s) {
     // a replay keeps the recorded layout; a synchronised build tries the padded one
     const bool padded = c->replaying ? c->rec.nb_stride == NB_STRIDE : true;
     const GridView g{c->Ps.as<int4>(), c->mol_s.as<int32_t>(), c->grids.as<MolGrid>(), c->cell_start.as<uint32_t>()};
+    AC_TRY(c->cw.cnt.reserve((size_t)(n + 1) * sizeof(int64_t), s));
+    int64_t* pw = c->cw.cnt.as<int64_t>();
     if (padded) {
         AC_TRY(c->nb.reserve((size_t)n * NB_STRIDE * sizeof(int32_t), s));
         auto k = guard ? k_neighbours<NB_PADDED, true> : k_neighbours<NB_PADDED, false>;
-        k<<<nb, 128, 0, s>>>(g.Ps, g.mol_s, g.grids, g.cell_start, c->pc, n, cntp, nullptr, c->nb.as<int32_t>(), dc);
+        k<<<nb, 128, 0, s>>>(g.Ps, g.mol_s, g.grids, g.cell_start, c->pc, n, cntp, nullptr, c->nb.as<int32_t>(), dc, pw);
     } else {
         auto k = guard ? k_neighbours<NB_COUNT, true> : k_neighbours<NB_COUNT, false>;
-        k<<<nb, 128, 0, s>>>(g.Ps, g.mol_s, g.grids, g.cell_start, c->pc, n, cntp, nullptr, nullptr, dc);
+        k<<<nb, 128, 0, s>>>(g.Ps, g.mol_s, g.grids, g.cell_start, c->pc, n, cntp, nullptr, nullptr, dc, pw);
     }
     AC_LAUNCHED();
-    // layout of the K^2 pair masks, from the counts
-    AC_TRY(plan_pair_masks(c, cntp, s));
+    // layout of the K^2 pair masks, from the words per atom
+    AC_TRY(plan_pair_masks(c, pw, s));
     // work order from the counts (before a scan turns them into offsets)
     AC_TRY(c->work.reserve((size_t)n * sizeof(int32_t), s));
     AC_TRY(c->deg.reserve(2 * DEG_BINS * sizeof(unsigned) + 64, s));
@@ -315,7 +318,8 @@ int build_neighbours(ac_ctx* c, cudaStream_t s) {
     if (c->replaying) AC_TRY(expect_i64(c, cntp + n, total, s));
     AC_TRY(c->nb.reserve((size_t)(total > 0 ? total : 1) * sizeof(int32_t), s));
     auto k_fill = guard ? k_neighbours<NB_CSR, true> : k_neighbours<NB_CSR, false>;
-    k_fill<<<nb, 128, 0, s>>>(g.Ps, g.mol_s, g.grids, g.cell_start, c->pc, n, nullptr, cntp, c->nb.as<int32_t>(), dc);
+    k_fill<<<nb, 128, 0, s>>>(g.Ps, g.mol_s, g.grids, g.cell_start, c->pc, n, nullptr, cntp, c->nb.as<int32_t>(), dc,
+                              nullptr);
     AC_LAUNCHED();
     return AC_OK;
 }

@@ -284,7 +284,10 @@ int scan_exclusive_i64(ac_ctx* c, const int64_t* in, int64_t* out, int64_t n, cu
 int scan_exclusive_u32_to_u32(ac_ctx* c, const uint32_t* in, uint32_t* out, int64_t n, cudaStream_t s);
 
 int quantise_and_plan(ac_ctx* c, cudaStream_t s);
-int plan_pair_masks(ac_ctx* c, const int64_t* nb_cnt, cudaStream_t s);
+int plan_pair_masks(ac_ctx* c, const int64_t* pw, cudaStream_t s);
+
+// 32-bit words of an atom's triangle pair mask: one bit per pair of its m neighbours
+__device__ __forceinline__ int64_t pair_mask_words(int m) { return ((int64_t)m * (m - 1) / 2 + 31) / 32; }
 int build_grid(ac_ctx* c, cudaStream_t s);
 int build_neighbours(ac_ctx* c, cudaStream_t s);
 int run_local(ac_ctx* c, cudaStream_t s);
