@@ -1301,56 +1301,59 @@ int subcomplex_flags(ac_ctx* c, int dim, int64_t first, int64_t m, double alpha2
     return AC_OK;
 }
 
-// OrthoSize (and the initial Size, source and coface key) of list d, on the
-// side stream as soon as the list's rows are final, overlapping the
-// canonicalisation of the lower dimensions; compute_filtration joins it.
+// The filtration of list d on the side stream, as soon as the list's rows are
+// final, overlapping the canonicalisation of the lower dimensions: OrthoSize
+// (with the initial Size, source and coface key), then for d < 3 the two
+// coface passes over K^(d+1), whose values are final by then (the side stream
+// ran its passes first). compute_filtration joins the side stream. Each pass
+// has its own buffers, reserved here on the build's stream before the fork.
 static int fork_orthosize(ac_ctx* c, int d, cudaStream_t s) {
     SimplexList& L = c->K[d];
     const int64_t m = L.count;
     if (m == 0) return AC_OK;
+    SimplexList* U = d < 3 ? &c->K[d + 1] : nullptr;
+    const int64_t mu = U ? U->count : 0;
     AC_TRY(c->fkey[d].reserve((size_t)m * sizeof(unsigned long long), s));
+    if (U) {
+        AC_TRY(c->fargs[d].reserve((size_t)m * sizeof(unsigned long long), s));
+        if (mu > 0) AC_TRY(c->frows[d].reserve((size_t)mu * (d + 2) * sizeof(int64_t), s));
+    }
     AC_CUDA(cudaEventRecord(c->ev_fork, s));
-    AC_CUDA(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
-    k_orthosize<<<(unsigned)((m + 127) / 128), 128, 0, c->side>>>(
-        c->P.as<int4>(), c->Gbuf[d].as<int4>(), m, d + 1, L.attached.as<uint8_t>(), L.orthosize.as<double>(),
-        L.f.as<double>(), L.src_dim.as<int8_t>(), L.src_idx.as<int64_t>(), c->fkey[d].as<unsigned long long>());
+    cudaStream_t t = c->side;
+    AC_CUDA(cudaStreamWaitEvent(t, c->ev_fork, 0));
+    unsigned long long* keyb = c->fkey[d].as<unsigned long long>();
+    k_orthosize<<<(unsigned)((m + 127) / 128), 128, 0, t>>>(c->P.as<int4>(), c->Gbuf[d].as<int4>(), m, d + 1,
+                                                            L.attached.as<uint8_t>(), L.orthosize.as<double>(),
+                                                            L.f.as<double>(), L.src_dim.as<int8_t>(),
+                                                            L.src_idx.as<int64_t>(), keyb);
     AC_LAUNCHED();
     c->os_forked = true;
+    if (!U) return AC_OK;
+    unsigned long long* argb = c->fargs[d].as<unsigned long long>();
+    AC_CUDA(cudaMemsetAsync(argb, 0xff, (size_t)m * sizeof(unsigned long long), t));
+    if (mu > 0) {
+        const unsigned nbk = (unsigned)((mu + 127) / 128);
+        int64_t* rows = c->frows[d].as<int64_t>();
+        k_coface_min<<<nbk, 128, 0, t>>>(c->Gbuf[d + 1].as<int4>(), U->f.as<double>(), mu, d + 2, c->Gbuf[d].as<int4>(),
+                                         L.v0_off.as<int64_t>(), L.attached.as<uint8_t>(), keyb, rows);
+        AC_LAUNCHED();
+        k_coface_arg<<<nbk, 128, 0, t>>>(U->f.as<double>(), mu, d + 2, rows, keyb, argb);
+        AC_LAUNCHED();
+    }
+    k_coface_apply<<<(unsigned)((m + 127) / 128), 128, 0, t>>>(
+        m, L.attached.as<uint8_t>(), keyb, argb, U->src_dim.as<int8_t>(), U->src_idx.as<int64_t>(), L.f.as<double>(),
+        L.src_dim.as<int8_t>(), L.src_idx.as<int64_t>(), &c->counters.as<DevCounters>()->err);
+    AC_LAUNCHED();
     return AC_OK;
 }
 
+// Size of every list (Section 2.3): computed on the side stream as the lists
+// were finished (fork_orthosize); the build's stream waits for it here.
 int compute_filtration(ac_ctx* c, cudaStream_t s) {
     if (c->os_forked) {
         AC_CUDA(cudaEventRecord(c->ev_join, c->side));
         AC_CUDA(cudaStreamWaitEvent(s, c->ev_join, 0));
         c->os_forked = false;
-    }
-    DevBuf& argb = c->scratch[3];
-    for (int d = 2; d >= 0; d--) {
-        SimplexList& L = c->K[d];
-        const int64_t m = L.count;
-        if (m == 0) continue;
-        unsigned long long* keyb = c->fkey[d].as<unsigned long long>();
-        AC_TRY(argb.reserve((size_t)m * sizeof(unsigned long long), s));
-        SimplexList& U = c->K[d + 1];
-        AC_CUDA(cudaMemsetAsync(argb.p, 0xff, (size_t)m * sizeof(unsigned long long), s));
-        if (U.count > 0) {
-            const unsigned nbk = (unsigned)((U.count + 127) / 128);
-            DevBuf& rowb = c->scratch[4];
-            AC_TRY(rowb.reserve((size_t)U.count * (d + 2) * sizeof(int64_t), s));
-            k_coface_min<<<nbk, 128, 0, s>>>(c->Gbuf[d + 1].as<int4>(), U.f.as<double>(), U.count, d + 2,
-                                             c->Gbuf[d].as<int4>(), L.v0_off.as<int64_t>(), L.attached.as<uint8_t>(),
-                                             keyb, rowb.as<int64_t>());
-            AC_LAUNCHED();
-            k_coface_arg<<<nbk, 128, 0, s>>>(U.f.as<double>(), U.count, d + 2, rowb.as<int64_t>(), keyb,
-                                             argb.as<unsigned long long>());
-            AC_LAUNCHED();
-        }
-        k_coface_apply<<<(unsigned)((m + 127) / 128), 128, 0, s>>>(
-            m, L.attached.as<uint8_t>(), keyb, argb.as<unsigned long long>(), U.src_dim.as<int8_t>(),
-            U.src_idx.as<int64_t>(), L.f.as<double>(), L.src_dim.as<int8_t>(), L.src_idx.as<int64_t>(),
-            &c->counters.as<DevCounters>()->err);
-        AC_LAUNCHED();
     }
     return AC_OK;
 }

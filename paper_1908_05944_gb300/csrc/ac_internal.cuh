@@ -242,6 +242,8 @@ struct ac_ctx {
     ac::DevBuf counters;  // DevCounters
     ac::DevBuf scratch[7];
     ac::DevBuf fkey[4];      // per-dimension coface-minimum keys (k_orthosize, k_coface_*)
+    ac::DevBuf fargs[4];     // per-dimension lexicographic argmin of the coface minimum
+    ac::DevBuf frows[4];     // per-dimension facet rows of the cofaces (k_coface_min -> k_coface_arg)
     bool os_forked = false;  // k_orthosize launches on the side stream await their join
     int64_t pair_words = 0;  // words of the triangle pair masks (recorded for replays)
     ac::DevBuf pair_moff;    // first pair-mask word of each sorted position (n + 1)
