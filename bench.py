@@ -7,8 +7,9 @@ Size filtration values. Inputs are resident in device memory when the timed
 region starts; L2 is flushed (a 256 MB write) between timed steps.
 
 `e2e` repeats the step through the public C ABI with host buffers: create from
-pinned host arrays (host->device copy), build, copy every simplex list and
-filtration value back to pinned host memory, destroy.
+pinned host arrays (host->device copy), build with every simplex list, its
+filtration values and attached flags delivered to page-locked host memory
+(opt.host_results), destroy.
 
 With --impl reference the exact CPU oracle (oracle/) is timed instead, on a
 bounded sub-ball of the same workload per step, on the host cores.
@@ -392,7 +393,10 @@ def run_forms(args):
 
 
 def run_e2e(args, rank, world, steps):
-    """Whole public-API round trip with host buffers (pinned)."""
+    """Whole public-API round trip with host buffers: a fresh context from page-locked host arrays
+    (H2D inside), one build that also delivers every list (rows, filtration values, attached flags)
+    to host memory (opt.host_results: each list is copied as soon as it is final, overlapping the
+    rest of the build), and the context's destruction."""
     import torch
 
     import paper_1908_05944_gb300 as ac
@@ -403,36 +407,19 @@ def run_e2e(args, rank, world, steps):
     r_h = torch.from_numpy(r_np).pin_memory()
     prec = ac.AC_PRECISION_FILTERED if args.precision == "filtered" else ac.AC_PRECISION_PLAIN_FP64
     h2d = c_np.nbytes + r_np.nbytes
-    outs_host = None
     times = []
     d2h = 0
     for it in range(steps + 1):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        cx = ac.AlphaComplex(c_h, r_h, 0.0, ac.options(precision=prec))
+        cx = ac.AlphaComplex(c_h, r_h, 0.0, ac.options(precision=prec, host_results=True))
         cx.build()
         d2h = 0
-        if outs_host is None:
-            outs_host = []
-            for d in range(4):
-                m = cx.count(d)
-                outs_host.append((torch.empty((max(m, 1) * 2, d + 1), dtype=torch.int32).pin_memory(),
-                                  torch.empty(max(m, 1) * 2, dtype=torch.float64).pin_memory()))
         for d in range(4):
-            tv = cx.simplices(d, copy=False)
-            fv = cx.filtration_values(d, copy=False)
-            cnt = tv.shape[0]
-            if cnt:
-                if outs_host[d][0].shape[0] < cnt:
-                    outs_host[d] = (torch.empty((cnt * 2, d + 1), dtype=torch.int32).pin_memory(),
-                                    torch.empty(cnt * 2, dtype=torch.float64).pin_memory())
-                outs_host[d][0][:cnt].copy_(tv, non_blocking=True)
-                outs_host[d][1][:cnt].copy_(fv, non_blocking=True)
-            d2h += cnt * (d + 1) * 4 + cnt * 8
-        torch.cuda.synchronize()
+            t, f, a = cx.host_lists(d, copy=False)  # page-locked host memory, filled by the build
+            d2h += t.nbytes + f.nbytes + a.nbytes
         cx.close()
-        torch.cuda.synchronize()
-        if it > 0:  # first round trip warms the allocator
+        if it > 0:  # the first round trip warms the allocators
             times.append(time.perf_counter() - t0)
     t = max_over_ranks(float(sum(times)), world)
     return {"value": n * world * steps / t, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}

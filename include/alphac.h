@@ -76,7 +76,11 @@ typedef struct {
     int32_t no_graph;        /* 1: every ac_build synchronises with the host at each list size
                                 (default 0: later builds of a context replay its first build's
                                 launch sequence as one CUDA graph, see ac_build) */
-    int32_t reserved[7];
+    int32_t host_results;    /* 1: ac_build also copies every list (rows, filtration values,
+                                attached flags) to page-locked host memory owned by the context,
+                                each list as soon as it is final, overlapping the rest of the
+                                build; read them with ac_get_simplices_host */
+    int32_t reserved[6];
 } ac_options;
 
 typedef struct {
@@ -303,6 +307,20 @@ AC_API int ac_chunked_info(const ac_chunked* res, ac_chunked_stats* out);
 
 /* Free a chunked result. NULL is a no-op. */
 AC_API void ac_chunked_free(ac_chunked* res);
+
+/*
+ * Host copies of dimension dim (0..3) of molecule mol (-1 for a single-molecule
+ * context), made by the last ac_build of a context created with
+ * opt.host_results = 1: *count rows of dim+1 int32 indices (as
+ * ac_get_simplices), their filtration values (as ac_filtration_values) and
+ * attached flags (as ac_attached_flags). Page-locked host memory owned by the
+ * context, valid until the next ac_build or ac_destroy. Any output pointer
+ * but count may be NULL.
+ * Errors: AC_ERR_INVALID_ARG (bad dim/mol), AC_ERR_STATE (no build, or the
+ * context does not keep host results).
+ */
+AC_API int ac_get_simplices_host(ac_ctx* ctx, int dim, int64_t mol, const int32_t** h_tuples, const double** h_f,
+                                 const uint8_t** h_attached, int64_t* count);
 
 /* Counters and stage times of the last ac_build. */
 AC_API int ac_get_stats(ac_ctx* ctx, ac_stats* out);

@@ -37,14 +37,14 @@ AC_FILTRATION_ORTHOSIZE = 1
 # every symbol include/alphac.h declares
 EXPORTS = ["ac_create", "ac_create_batch", "ac_build", "ac_get_simplices", "ac_filtration_values", "ac_attached_flags",
            "ac_get_candidates", "ac_eval_filtration", "ac_backward", "ac_backward_noalloc", "ac_autotune",
-           "ac_subcomplex", "ac_chunk_plan", "ac_build_chunked", "ac_chunked_simplices", "ac_chunked_info",
+           "ac_subcomplex", "ac_get_simplices_host", "ac_chunk_plan", "ac_build_chunked", "ac_chunked_simplices", "ac_chunked_info",
            "ac_chunked_free", "ac_get_stats", "ac_get_sizes", "ac_destroy", "ac_error_string", "ac_last_error_detail"]
 
 
 class ac_options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("filtration", ctypes.c_int32), ("cell_factor", ctypes.c_double),
                 ("block_warps", ctypes.c_int32), ("keep_candidates", ctypes.c_int32),
-                ("no_graph", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
+                ("no_graph", ctypes.c_int32), ("host_results", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
 
 
 class ac_stats(ctypes.Structure):
@@ -98,6 +98,7 @@ def _declare(lib):
     lib.ac_backward_noalloc.argtypes = [vp, vp, vp, vp, vp]
     lib.ac_autotune.argtypes = [vp, vp, P(ac_options)]
     lib.ac_subcomplex.argtypes = [vp, i32, i64, dbl, vp, P(i64), vp]
+    lib.ac_get_simplices_host.argtypes = [vp, i32, i64, P(vp), P(vp), P(vp), P(i64)]
     lib.ac_chunk_plan.argtypes = [vp, vp, i64, dbl, i64, vp, i64, P(i64), P(i64)]
     lib.ac_build_chunked.argtypes = [vp, vp, i64, dbl, P(ac_options), i64, vp, P(vp)]
     lib.ac_chunked_simplices.argtypes = [vp, i32, P(vp), P(vp), P(vp), P(i64)]
@@ -176,8 +177,9 @@ class _DeviceArray:
 
 
 def options(precision=AC_PRECISION_FILTERED, filtration=AC_FILTRATION_SIZE, cell_factor=0.0, block_warps=0,
-            keep_candidates=False, no_graph=False) -> ac_options:
+            keep_candidates=False, no_graph=False, host_results=False) -> ac_options:
     o = ac_options()
+    o.host_results = 1 if host_results else 0
     o.precision = precision
     o.filtration = filtration
     o.cell_factor = cell_factor
@@ -243,6 +245,22 @@ class AlphaComplex:
 
     def attached(self, dim: int, mol: int = -1, copy: bool = True):
         return self._view(lib().ac_attached_flags, dim, mol, 0, "|u1", copy)
+
+    def host_lists(self, dim: int, mol: int = -1, copy: bool = True):
+        """(rows, filtration values, attached flags) of list dim as numpy arrays, from the host copies the
+        last build made (the context needs options(host_results=True)); copy=False gives views into the
+        context's page-locked memory, valid until its next build."""
+        t, f, a = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p()
+        cnt = ctypes.c_int64()
+        _check(lib().ac_get_simplices_host(self._h, dim, mol, ctypes.byref(t), ctypes.byref(f), ctypes.byref(a),
+                                           ctypes.byref(cnt)), "ac_get_simplices_host")
+        n = cnt.value
+        if n == 0:
+            return (np.zeros((0, dim + 1), np.int32), np.zeros(0, np.float64), np.zeros(0, np.uint8))
+        out = (np.ctypeslib.as_array((ctypes.c_int32 * (n * (dim + 1))).from_address(t.value)).reshape(n, dim + 1),
+               np.ctypeslib.as_array((ctypes.c_double * n).from_address(f.value)),
+               np.ctypeslib.as_array((ctypes.c_uint8 * n).from_address(a.value)))
+        return tuple(x.copy() for x in out) if copy else out
 
     def candidates(self, dim: int, copy: bool = True):
         import torch

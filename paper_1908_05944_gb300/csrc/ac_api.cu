@@ -557,6 +557,57 @@ static void res_give(CtxRes& r) {
     res_free(r);
 }
 
+// Page-locked host blocks for the host copies of the lists: pinning memory costs
+// far more than a build, so blocks return to a process-wide cache (up to 8 GB)
+// when a context is destroyed or needs a larger one, and are taken best-fit.
+static std::mutex g_hb_mu;
+static std::vector<std::pair<void*, size_t>> g_hb;
+static size_t g_hb_total = 0;
+constexpr size_t HB_CACHE_BYTES = (size_t)8 << 30;
+
+static void host_block_give(void* p, size_t bytes) {
+    if (!p) return;
+    {
+        std::lock_guard<std::mutex> lk(g_hb_mu);
+        if (g_hb_total + bytes <= HB_CACHE_BYTES) {
+            g_hb.emplace_back(p, bytes);
+            g_hb_total += bytes;
+            return;
+        }
+    }
+    cudaFreeHost(p);
+}
+
+int ac::host_block_for(ac_ctx* c, int d, size_t bytes) {
+    if (c->hres_bytes[d] >= bytes && c->hres[d]) return AC_OK;
+    host_block_give(c->hres[d], c->hres_bytes[d]);
+    c->hres[d] = nullptr;
+    c->hres_bytes[d] = 0;
+    {
+        std::lock_guard<std::mutex> lk(g_hb_mu);
+        size_t best = g_hb.size();
+        for (size_t k = 0; k < g_hb.size(); k++)
+            if (g_hb[k].second >= bytes && g_hb[k].second <= 4 * bytes + (1 << 20) &&
+                (best == g_hb.size() || g_hb[k].second < g_hb[best].second))
+                best = k;
+        if (best < g_hb.size()) {
+            c->hres[d] = g_hb[best].first;
+            c->hres_bytes[d] = g_hb[best].second;
+            g_hb_total -= g_hb[best].second;
+            g_hb.erase(g_hb.begin() + (long)best);
+            return AC_OK;
+        }
+    }
+    // a new block, with room to grow (a quarter more, at least 1 MB)
+    const size_t want = std::max(bytes + bytes / 4, (size_t)1 << 20);
+    if (cudaMallocHost(&c->hres[d], want) != cudaSuccess) {
+        c->hres[d] = nullptr;
+        return cuda_fail(cudaGetLastError(), "cudaMallocHost of a host result block", __FILE__, __LINE__);
+    }
+    c->hres_bytes[d] = want;
+    return AC_OK;
+}
+
 static int create_impl(const double* centres, const double* radii, const int64_t* offsets, int64_t n_mol,
                        double alpha, const ac_options* opt, ac_ctx** out) {
     if (!out) return fail(AC_ERR_INVALID_ARG, "out is NULL");
@@ -878,6 +929,21 @@ extern "C" int ac_attached_flags(ac_ctx* c, int dim, int64_t mol, const uint8_t*
     return AC_OK;
 }
 
+extern "C" int ac_get_simplices_host(ac_ctx* c, int dim, int64_t mol, const int32_t** h_tuples, const double** h_f,
+                                     const uint8_t** h_attached, int64_t* count) {
+    int64_t first = 0;
+    AC_TRY(get_list(c, c ? c->K : nullptr, dim, mol, &first, count));
+    if (!c->opt.host_results) return fail(AC_ERR_STATE, "context does not keep host results (opt.host_results)");
+    const int64_t total = c->K[dim].count;
+    const int k = dim + 1;
+    char* b = static_cast<char*>(c->hres[dim]);
+    if (total > 0 && !b) return fail(AC_ERR_STATE, "no host copy of this list");
+    if (h_tuples) *h_tuples = total > 0 ? reinterpret_cast<const int32_t*>(b) + first * k : nullptr;
+    if (h_f) *h_f = total > 0 ? reinterpret_cast<const double*>(b + hres_f_off(total, k)) + first : nullptr;
+    if (h_attached) *h_attached = total > 0 ? reinterpret_cast<const uint8_t*>(b + hres_a_off(total, k)) + first : nullptr;
+    return AC_OK;
+}
+
 extern "C" int ac_get_candidates(ac_ctx* c, int dim, const int32_t** d_tuples, int64_t* count) {
     if (!c || dim < 1 || dim > 3 || !d_tuples || !count) return fail(AC_ERR_INVALID_ARG, "bad argument");
     if (!c->built) return fail(AC_ERR_STATE, "no successful ac_build on this context");
@@ -970,6 +1036,7 @@ extern "C" void ac_destroy(ac_ctx* c) {
     cudaDeviceSynchronize();
     StreamScope scope(nullptr);
     drop_graph(c);
+    for (int d = 0; d < 4; d++) host_block_give(c->hres[d], c->hres_bytes[d]);
     CtxRes r;
     r.device = c->res_device;
     for (int k = 0; k < 10; k++) r.ev[k] = c->ev[k];

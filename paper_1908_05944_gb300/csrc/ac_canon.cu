@@ -1301,6 +1301,22 @@ int subcomplex_flags(ac_ctx* c, int dim, int64_t first, int64_t m, double alpha2
     return AC_OK;
 }
 
+// opt.host_results: list d (rows, the selected filtration values, attached
+// flags) to its page-locked host block, on stream t once its values are final
+static int copy_to_host(ac_ctx* c, int d, cudaStream_t t) {
+    if (!c->opt.host_results) return AC_OK;
+    const SimplexList& L = c->K[d];
+    const int64_t m = L.count;
+    const int k = d + 1;
+    AC_TRY(host_block_for(c, d, hres_bytes_for(m, k)));
+    char* b = static_cast<char*>(c->hres[d]);
+    const DevBuf& f = c->opt.filtration == AC_FILTRATION_ORTHOSIZE ? L.orthosize : L.f;
+    AC_CUDA(cudaMemcpyAsync(b, L.tuples.p, (size_t)m * k * sizeof(int32_t), cudaMemcpyDeviceToHost, t));
+    AC_CUDA(cudaMemcpyAsync(b + hres_f_off(m, k), f.p, (size_t)m * sizeof(double), cudaMemcpyDeviceToHost, t));
+    AC_CUDA(cudaMemcpyAsync(b + hres_a_off(m, k), L.attached.p, (size_t)m, cudaMemcpyDeviceToHost, t));
+    return AC_OK;
+}
+
 // The filtration of list d on the side stream, as soon as the list's rows are
 // final, overlapping the canonicalisation of the lower dimensions: OrthoSize
 // (with the initial Size, source and coface key), then for d < 3 the two
@@ -1328,7 +1344,7 @@ static int fork_orthosize(ac_ctx* c, int d, cudaStream_t s) {
                                                             L.src_idx.as<int64_t>(), keyb);
     AC_LAUNCHED();
     c->os_forked = true;
-    if (!U) return AC_OK;
+    if (!U) return copy_to_host(c, d, t);
     unsigned long long* argb = c->fargs[d].as<unsigned long long>();
     AC_CUDA(cudaMemsetAsync(argb, 0xff, (size_t)m * sizeof(unsigned long long), t));
     if (mu > 0) {
@@ -1344,7 +1360,7 @@ static int fork_orthosize(ac_ctx* c, int d, cudaStream_t s) {
         m, L.attached.as<uint8_t>(), keyb, argb, U->src_dim.as<int8_t>(), U->src_idx.as<int64_t>(), L.f.as<double>(),
         L.src_dim.as<int8_t>(), L.src_idx.as<int64_t>(), &c->counters.as<DevCounters>()->err);
     AC_LAUNCHED();
-    return AC_OK;
+    return copy_to_host(c, d, t);
 }
 
 // Size of every list (Section 2.3): computed on the side stream as the lists

@@ -241,6 +241,10 @@ struct ac_ctx {
     // scratch
     ac::DevBuf counters;  // DevCounters
     ac::DevBuf scratch[7];
+    // host copies of the lists (opt.host_results): per dimension one page-locked
+    // block [rows int32 | values f64 | attached u8], from a process-wide cache
+    void* hres[4] = {nullptr, nullptr, nullptr, nullptr};
+    size_t hres_bytes[4] = {0, 0, 0, 0};
     ac::DevBuf fkey[4];      // per-dimension coface-minimum keys (k_orthosize, k_coface_*)
     ac::DevBuf fargs[4];     // per-dimension lexicographic argmin of the coface minimum
     ac::DevBuf frows[4];     // per-dimension facet rows of the cofaces (k_coface_min -> k_coface_arg)
@@ -287,6 +291,12 @@ int scan_exclusive_u32_to_u32(ac_ctx* c, const uint32_t* in, uint32_t* out, int6
 
 int quantise_and_plan(ac_ctx* c, cudaStream_t s);
 int plan_pair_masks(ac_ctx* c, const int64_t* pw, cudaStream_t s);
+// page-locked host block of at least `bytes` for list d's host copy (process-wide cache)
+int host_block_for(ac_ctx* c, int d, size_t bytes);
+// byte offsets of the three parts of a host block holding `count` rows of k entries
+inline size_t hres_f_off(int64_t count, int k) { return ((size_t)count * k * sizeof(int32_t) + 15) & ~(size_t)15; }
+inline size_t hres_a_off(int64_t count, int k) { return hres_f_off(count, k) + (size_t)count * sizeof(double); }
+inline size_t hres_bytes_for(int64_t count, int k) { return hres_a_off(count, k) + (size_t)count; }
 
 // 32-bit words of an atom's triangle pair mask: one bit per pair of its m neighbours
 __device__ __forceinline__ int64_t pair_mask_words(int m) { return ((int64_t)m * (m - 1) / 2 + 31) / 32; }

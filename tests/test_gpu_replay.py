@@ -113,3 +113,41 @@ def test_batch_and_candidate_lists_replay():
     assert kx.stats()["replayed"] == 1
     for d, want in zip((1, 2, 3), cand):
         assert np.array_equal(kx.candidates(d).cpu().numpy(), want)
+
+
+def test_host_results_equal_device_lists():
+    """opt.host_results: the build copies each list to page-locked host memory as soon as it is
+    final; the copies equal the device lists, after the first build and after replays, per molecule."""
+    import torch
+
+    import paper_1908_05944_gb300 as ac
+
+    c, r = synth.workload("globule2k_vdw")
+    for filtration in (ac.AC_FILTRATION_SIZE, ac.AC_FILTRATION_ORTHOSIZE):
+        cx = ac.AlphaComplex(torch.from_numpy(c).cuda(), torch.from_numpy(r).cuda(), 0.0,
+                             ac.options(host_results=True, filtration=filtration))
+        for _ in range(3):
+            cx.build()
+            for d in range(4):
+                t, f, a = cx.host_lists(d)
+                assert np.array_equal(t, cx.simplices(d).cpu().numpy())
+                assert np.array_equal(f, cx.filtration_values(d).cpu().numpy())
+                assert np.array_equal(a, cx.attached(d).cpu().numpy())
+        assert cx.stats()["replayed"] == 1
+    sizes = [300, 0, 800]
+    mols = [synth.globule(2100 + m, n, probe=True) if n else (np.zeros((0, 3)), np.zeros(0))
+            for m, n in enumerate(sizes)]
+    offsets = np.concatenate([[0], np.cumsum(sizes)])
+    bx = ac.AlphaComplex(torch.from_numpy(np.concatenate([m[0] for m in mols])).cuda(),
+                         torch.from_numpy(np.concatenate([m[1] for m in mols])).cuda(), 0.0, ac.options(host_results=True),
+                         offsets=offsets)
+    bx.build()
+    for m in range(len(sizes)):
+        for d in range(4):
+            t, f, a = bx.host_lists(d, m)
+            assert np.array_equal(t, bx.simplices(d, m).cpu().numpy())
+            assert np.array_equal(f, bx.filtration_values(d, m).cpu().numpy())
+    plain = ac.AlphaComplex(torch.from_numpy(c).cuda(), torch.from_numpy(r).cuda(), 0.0).build()
+    with pytest.raises(ac.AlphacError) as e:
+        plain.host_lists(1)
+    assert e.value.code == ac.AC_ERR_STATE
