@@ -519,6 +519,7 @@ struct EdgeMarkArgs {
     int words;             // mask words per atom
     unsigned* m_in;        // per sorted position: entry of the row is an edge of K^1
     unsigned* m_free;      // ... and a free edge
+    unsigned long long* rows;  // per input index: distinct marked edges (the atom's row count)
     unsigned* err;
 };
 
@@ -543,14 +544,16 @@ __device__ __forceinline__ int row_find(const int32_t* __restrict__ nb, int64_t 
     return lo < m && nb[off + lo] == x ? lo : -1;
 }
 
-__device__ __forceinline__ void mark_bit(const EdgeMarkArgs& a, int su, int e, bool fr) {
+// bit e of sorted position su's row mask; the first setting of a bit counts a
+// row for input index gu (duplicates leave the count as it is)
+__device__ __forceinline__ void mark_bit(const EdgeMarkArgs& a, int su, int gu, int e, bool fr) {
     if (e < 0) {
         atomicOr(a.err, DERR_INTERNAL);  // an edge of K^1 between atoms whose balls do not meet: impossible
         return;
     }
     const int64_t w = (int64_t)su * a.words + (e >> 5);
     const unsigned bit = 1u << (e & 31);
-    atomicOr(&a.m_in[w], bit);
+    if (!(atomicOr(&a.m_in[w], bit) & bit)) atomicAdd(&a.rows[gu], 1ull);
     if (fr) atomicOr(&a.m_free[w], bit);
 }
 
@@ -568,9 +571,10 @@ __global__ void k_edge_mark(EdgeMarkArgs a) {
         if (gu > gv) {
             su = e.y;
             sv = e.x;
+            gu = gv;
         }
         edge_row(a, su, off, m);
-        mark_bit(a, su, row_find(a.nb, off, m, sv), true);
+        mark_bit(a, su, gu, row_find(a.nb, off, m, sv), true);
         return;
     }
     const int4 t = a.tri[j - a.nA];
@@ -581,19 +585,9 @@ __global__ void k_edge_mark(EdgeMarkArgs a) {
     int mb;
     edge_row(a, sb, offb, mb);
     const int ebc = row_find(a.nb, offb, mb, sc);
-    mark_bit(a, sa, eb, false);
-    mark_bit(a, sa, ec, false);
-    mark_bit(a, sb, ebc, false);
-}
-
-// rows per first vertex (input index g)
-__global__ void k_edge_count(EdgeMarkArgs a, int64_t n, int64_t* __restrict__ cnt) {
-    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= n) return;
-    const unsigned* mw = a.m_in + (int64_t)a.rank[g] * a.words;
-    int c = 0;
-    for (int w = 0; w < a.words; w++) c += __popc(mw[w]);
-    cnt[g] = c;
+    mark_bit(a, sa, t.x, eb, false);
+    mark_bit(a, sa, t.x, ec, false);
+    mark_bit(a, sb, t.y, ebc, false);
 }
 
 // the marked entries of g's row, ranked by input index: one warp per atom;
@@ -669,18 +663,15 @@ static int canon_edges_by_marks(ac_ctx* c, cudaStream_t s) {
     AC_TRY(w.cnt.reserve((nn + 1) * sizeof(int64_t), s));
     AC_TRY(L.v0_off.reserve((nn + 1) * sizeof(int64_t), s));
     AC_CUDA(cudaMemsetAsync(masks.p, 0, 2 * nn * words * sizeof(unsigned), s));
+    int64_t* cnt = w.cnt.as<int64_t>();
+    AC_CUDA(cudaMemsetAsync(cnt, 0, nn * sizeof(int64_t), s));
     EdgeMarkArgs a{c->edge_pass.as<int2>(), (int64_t)h.n_edge_pass, c->Gbuf[2].as<int4>(), c->K[2].count,
                    c->order.as<int32_t>(), c->rank.as<int32_t>(), c->nb_cnt.as<int64_t>(), c->nb.as<int32_t>(),
                    c->nb_stride, words, masks.as<unsigned>(), masks.as<unsigned>() + nn * words,
-                   &c->counters.as<DevCounters>()->err};
+                   reinterpret_cast<unsigned long long*>(cnt), &c->counters.as<DevCounters>()->err};
     const int64_t items = a.nA + a.nB;
     if (items > 0) {
         k_edge_mark<<<(unsigned)((items + 255) / 256), 256, 0, s>>>(a);
-        AC_LAUNCHED();
-    }
-    int64_t* cnt = w.cnt.as<int64_t>();
-    if (n > 0) {
-        k_edge_count<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(a, n, cnt);
         AC_LAUNCHED();
     }
     int64_t* uoff = L.v0_off.as<int64_t>();
@@ -736,6 +727,7 @@ struct TriMarkArgs {
     const int64_t* moff;  // first mask word of each sorted position (n + 1)
     unsigned* m_in;
     unsigned* m_free;
+    unsigned long long* rows;  // per input index: distinct marked pairs (the atom's row count)
     unsigned* err;
 };
 
@@ -760,7 +752,7 @@ int plan_pair_masks(ac_ctx* c, const int64_t* pw, cudaStream_t s) {
     return scan_exclusive_i64(c, pw, c->pair_moff.as<int64_t>(), n, s);
 }
 
-__device__ __forceinline__ void mark_pair(const TriMarkArgs& a, int sa, int e1, int e2, bool fr) {
+__device__ __forceinline__ void mark_pair(const TriMarkArgs& a, int sa, int ga, int e1, int e2, bool fr) {
     if (e1 < 0 || e2 < 0) {
         atomicOr(a.err, DERR_INTERNAL);  // a triangle of K^2 whose vertices' balls do not meet: impossible
         return;
@@ -769,7 +761,7 @@ __device__ __forceinline__ void mark_pair(const TriMarkArgs& a, int sa, int e1, 
     const int64_t bit = (int64_t)q * (q - 1) / 2 + p;
     const int64_t w = a.moff[sa] + (bit >> 5);
     const unsigned b = 1u << (bit & 31);
-    atomicOr(&a.m_in[w], b);
+    if (!(atomicOr(&a.m_in[w], b) & b)) atomicAdd(&a.rows[ga], 1ull);
     if (fr) atomicOr(&a.m_free[w], b);
 }
 
@@ -789,35 +781,22 @@ __global__ void k_tri_mark(TriMarkArgs a) {
         if (gv[2] < gv[f]) f = 2;
         const int sa = sv[f], s1 = sv[f == 0 ? 1 : 0], s2 = sv[f == 2 ? 1 : 2];
         nb_row_of(a.nb_off, a.stride, sa, off, m);
-        mark_pair(a, sa, row_find(a.nb, off, m, s1), row_find(a.nb, off, m, s2), true);
+        mark_pair(a, sa, gv[f], row_find(a.nb, off, m, s1), row_find(a.nb, off, m, s2), true);
         return;
     }
     const int4 t = a.tet[j - a.nA];
     const int sa = a.rank[t.x], sb = a.rank[t.y], sc = a.rank[t.z], sd = a.rank[t.w];
     nb_row_of(a.nb_off, a.stride, sa, off, m);
     const int pb = row_find(a.nb, off, m, sb), pc = row_find(a.nb, off, m, sc), pd = row_find(a.nb, off, m, sd);
-    mark_pair(a, sa, pb, pc, false);
-    mark_pair(a, sa, pb, pd, false);
-    mark_pair(a, sa, pc, pd, false);
+    mark_pair(a, sa, t.x, pb, pc, false);
+    mark_pair(a, sa, t.x, pb, pd, false);
+    mark_pair(a, sa, t.x, pc, pd, false);
     nb_row_of(a.nb_off, a.stride, sb, off, m);
-    mark_pair(a, sb, row_find(a.nb, off, m, sc), row_find(a.nb, off, m, sd), false);
+    mark_pair(a, sb, t.y, row_find(a.nb, off, m, sc), row_find(a.nb, off, m, sd), false);
 }
 
 constexpr int TW_WARPS = 4;
 constexpr int TW_CAP = 256;  // marked pairs ranked in shared memory; more take the slow path
-
-// rows per first vertex (input index g): one warp per atom
-__global__ void __launch_bounds__(TW_WARPS * 32) k_tri_count(TriMarkArgs a, int64_t n, int64_t* __restrict__ cnt) {
-    const int lane = threadIdx.x & 31;
-    const int64_t g = (int64_t)blockIdx.x * TW_WARPS + (threadIdx.x >> 5);
-    if (g >= n) return;
-    const int s = a.rank[g];
-    const int64_t w0 = a.moff[s], w1 = a.moff[s + 1];
-    int c = 0;
-    for (int64_t w = w0 + lane; w < w1; w += 32) c += __popc(a.m_in[w]);
-    c = __reduce_add_sync(0xffffffffu, c);
-    if (lane == 0) cnt[g] = c;
-}
 
 __device__ __forceinline__ void pair_of(int64_t bit, int& p, int& q) {
     int x = (int)((1.0f + sqrtf(1.0f + 8.0f * (float)bit)) * 0.5f);
@@ -924,20 +903,17 @@ static int canon_tris_by_marks(ac_ctx* c, cudaStream_t s) {
     const size_t mw = (size_t)(words > 0 ? words : 1);
     AC_TRY(masks.reserve(2 * mw * sizeof(unsigned), s));
     AC_CUDA(cudaMemsetAsync(masks.p, 0, 2 * mw * sizeof(unsigned), s));
+    AC_CUDA(cudaMemsetAsync(cnt, 0, nn * sizeof(int64_t), s));
     TriMarkArgs a{c->tri_pass.as<int4>(), (int64_t)h.n_tri_pass, c->Gbuf[3].as<int4>(), c->K[3].count,
                   c->order.as<int32_t>(), c->rank.as<int32_t>(), c->nb_cnt.as<int64_t>(), c->nb.as<int32_t>(),
                   c->nb_stride, moff, masks.as<unsigned>(), masks.as<unsigned>() + mw,
-                  &c->counters.as<DevCounters>()->err};
+                  reinterpret_cast<unsigned long long*>(cnt), &c->counters.as<DevCounters>()->err};
     const int64_t items = a.nA + a.nB;
     if (items > 0) {
         k_tri_mark<<<(unsigned)((items + 255) / 256), 256, 0, s>>>(a);
         AC_LAUNCHED();
     }
     const unsigned wb = (unsigned)((n + TW_WARPS - 1) / TW_WARPS);
-    if (n > 0) {
-        k_tri_count<<<wb, TW_WARPS * 32, 0, s>>>(a, n, cnt);
-        AC_LAUNCHED();
-    }
     int64_t* uoff = L.v0_off.as<int64_t>();
     AC_TRY(scan_exclusive_i64(c, cnt, uoff, n, s));
     int64_t count = L.count;
