@@ -315,6 +315,28 @@ def run_forms(args):
             "equal_to_whole_build": bool(equal), "whole_build_host_round_trip_ms": whole_s * 1e3}
         del ch
     del host
+    # context for the paper's Table 1 row of its largest unpartitioned molecule (58,674 atoms, van der Waals
+    # radii, alpha 0 and 1; 65 ms and 160 ms with memory transfers on a GTX 660 Ti): a synthetic globule of
+    # the same size and radii, timed end to end (fresh context from host arrays, lists back in host memory)
+    # and as a device-resident graph replay
+    c58, r58 = synth.globule(7, 58674, probe=False)
+    c58h, r58h = torch.from_numpy(c58).pin_memory(), torch.from_numpy(r58).pin_memory()
+    for alpha in (0.0, 1.0):
+        e2e = []
+        for it in range(4):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ex = ac.AlphaComplex(c58h, r58h, alpha, ac.options(host_results=True)).build(stream)
+            n_s = sum(ex.count(d) for d in range(4))
+            ex.close()
+            if it:
+                e2e.append(time.perf_counter() - t0)
+        gx = ac.AlphaComplex(torch.from_numpy(c58).cuda(), torch.from_numpy(r58).cuda(), alpha)
+        ms = time_builds(gx, steps, warm, stream, flush)
+        gx.close()
+        out[f"globule58k_vdw/alpha{alpha:g}"] = {"simplices": int(n_s), "e2e_ms": 1e3 * float(np.median(e2e)),
+                                               "device_ms": sum(ms) / steps,
+                                               "paper_gtx660ti_ms_1AON": 65.2 if alpha == 0.0 else 159.9}
     # batch: one context over all molecules vs one context per molecule
     sizes = synth.batch_sizes(4, 1024)
     mols = [synth.globule(1000 + m, int(n), probe=True) for m, n in enumerate(sizes)]
