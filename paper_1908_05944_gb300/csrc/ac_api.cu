@@ -853,7 +853,10 @@ extern "C" int ac_build(ac_ctx* c, void* stream) {
         if (!c->opt.no_graph) AC_TRY(record_copies(c, s));
         AC_TRY(read_counters(c, &h, s));
     }
-    if (h.err & DERR_INTERNAL) return fail(AC_ERR_CUDA, "internal: attached simplex without a coface in the complex");
+    if (h.err & DERR_INTERNAL)
+        return fail(AC_ERR_CUDA,
+                    "internal invariant failed (an attached simplex without a coface, a simplex of K^1 or K^2 whose "
+                    "vertices are not neighbours, or a K^3 row count that differs from the emitted tetrahedra)");
     if (h.err & DERR_TIMEOUT) {
         drop_graph(c);
         c->rec.valid = false;

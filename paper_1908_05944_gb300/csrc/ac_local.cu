@@ -1386,10 +1386,17 @@ static void set_constants(const PredConst& pc, int64_t wmax, LocalArgs& a) {
 }
 
 // blocks of k_resolve for up to `items` escalated simplices: one group per
-// simplex, at most a few resident waves (the kernel strides over the rest)
+// simplex, at most four resident waves of the device (the kernel strides over
+// the rest, so the cap only bounds the blocks that start with nothing to do)
 static unsigned resolve_blocks(int64_t items) {
+    static int sms = 0;
+    if (sms == 0) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0)
+            sms = 152;
+    }
     const int64_t want = (items * RESOLVE_LANES + 127) / 128;
-    return (unsigned)std::max<int64_t>(1, std::min<int64_t>(want, 152 * 16 * 4));
+    return (unsigned)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)sms * 16 * 4));
 }
 
 int run_local(ac_ctx* c, cudaStream_t s) {
