@@ -337,6 +337,15 @@ def run_forms(args):
         out[f"globule58k_vdw/alpha{alpha:g}"] = {"simplices": int(n_s), "e2e_ms": 1e3 * float(np.median(e2e)),
                                                "device_ms": sum(ms) / steps,
                                                "paper_gtx660ti_ms_1AON": 65.2 if alpha == 0.0 else 159.9}
+    # a point set unlike proteins: 200,000 particles (jittered lattice, radii log-uniform over a factor 8)
+    cp, rp = synth.particles(13, 200000)
+    px = ac.AlphaComplex(torch.from_numpy(cp).cuda(), torch.from_numpy(rp).cuda(), 0.0)
+    ms = time_builds(px, steps, warm, stream, flush)
+    pst = px.stats()
+    out["particles200k"] = {"atoms_per_s": len(rp) * steps / (sum(ms) / 1e3), "ms_per_step": sum(ms) / steps,
+                            "simplices": pst["simplices"], "max_degree": pst["max_degree"],
+                            "neighbour_pairs_per_atom": pst["neighbour_pairs"] / len(rp)}
+    px.close()
     # batch: one context over all molecules vs one context per molecule
     sizes = synth.batch_sizes(4, 1024)
     mols = [synth.globule(1000 + m, int(n), probe=True) for m, n in enumerate(sizes)]

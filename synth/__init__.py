@@ -111,6 +111,21 @@ def raw(seed: int, k: int) -> np.ndarray:
     return out
 
 
+def particles(seed: int, n: int, spacing: float = 1.0, r_lo: float = 0.25, r_hi: float = 2.0):
+    """A particle set unlike a protein (an SPH-like cloud): n points on a jittered cubic lattice of the
+    given spacing (each coordinate moved by up to 0.4 spacing, so no two coincide), radii log-uniform in
+    [r_lo, r_hi] (a ratio of 8 by default, against about 1.2 for atoms). Centres and radii are exact
+    multiples of 1/1024 (units as for atoms)."""
+    u = (raw(seed, 4 * n) >> np.uint64(11)).astype(np.float64) * 2.0 ** -53 if n else np.zeros(0)
+    u = u.reshape(n, 4) if n else np.zeros((0, 4))
+    m = max(1, int(math.ceil(n ** (1.0 / 3.0) - 1e-9)))
+    k = np.arange(n)
+    lattice = np.stack([k % m, (k // m) % m, k // (m * m)], 1).astype(np.float64)
+    xyz = (lattice + (u[:, :3] - 0.5) * 0.8) * spacing
+    r = r_lo * (r_hi / r_lo) ** u[:, 3]
+    return np.round(xyz * 1024.0) / 1024.0, np.round(r * 1024.0) / 1024.0
+
+
 # The five workloads (sizes, regions, seeds), named by what they are.
 WORKLOADS = {
     "globule2k_vdw": dict(seed=1, n=2000, probe=False),

@@ -1,0 +1,35 @@
+"""Point sets unlike proteins: an SPH-like particle cloud with radii spread over a
+factor of 8 (against about 1.2 for atoms), so neighbour counts vary from a few
+to over a hundred and many atoms take the wide-row path of the per-atom kernel.
+The whole complex must equal the oracle's, for alpha 0 and alpha > 0, in both
+predicate modes.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from gpu_util import assert_same_complex, run_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("alpha,mode", [(0.0, 0), (0.5, 0), (0.0, 1)], ids=["a0-filtered", "a0.5-filtered", "a0-fp64"])
+def test_particles_equal_oracle(alpha, mode):
+    c, r = synth.particles(11, 3000)
+    gpu = run_gpu(c, r, alpha, precision=mode)
+    st = gpu.stats()
+    assert st["max_degree"] > 64, "the cloud should exercise the wide-row path"
+    assert_same_complex(gpu, oracle.alpha_complex(c, r, alpha))
+
+
+def test_particles_chunked_equal_whole():
+    import paper_1908_05944_gb300 as ac
+
+    c, r = synth.particles(12, 6000)
+    whole = run_gpu(c, r, 0.0)
+    ch = ac.ChunkedComplex(c, r, 0.0, 900)
+    assert ch.stats()["n_chunks"] > 3
+    for d in range(4):
+        assert np.array_equal(ch.simplices(d), whole.simplices(d).cpu().numpy())
+        assert np.array_equal(ch.filtration_values(d), whole.filtration_values(d).cpu().numpy())

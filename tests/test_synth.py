@@ -45,3 +45,15 @@ def test_shell_and_batch_sizes():
 def test_normal_draws():
     w = synth.normal(6, 100001)
     assert abs(w.mean()) < 0.02 and abs(w.std() - 1) < 0.02
+
+
+def test_particles_generator():
+    """The SPH-like cloud: seeded, exact multiples of 1/1024, distinct centres, radii in range."""
+    c, r = synth.particles(11, 5000)
+    c2, r2 = synth.particles(11, 5000)
+    assert np.array_equal(c, c2) and np.array_equal(r, r2)
+    assert not np.array_equal(c, synth.particles(12, 5000)[0])
+    q = c * 1024.0
+    assert np.array_equal(q, np.round(q)) and np.array_equal(r * 1024.0, np.round(r * 1024.0))
+    assert len(np.unique(np.round(q).astype(np.int64), axis=0)) == len(c)
+    assert r.min() >= 0.25 and r.max() <= 2.0 and r.max() / r.min() > 7.0
