@@ -68,6 +68,8 @@
 // and lambda_i = 1 - sum of the others (exact 64-bit integers).
 #include <math.h>
 
+#include <type_traits>
+
 #include "ac_internal.cuh"
 
 namespace ac {
@@ -81,6 +83,11 @@ constexpr int PL_CAP = 256;    // Sigma^2 pairs listed during the triangle phase
 template <int WORDS>
 struct WarpSmem {
     static constexpr int M = 32 * WORDS;
+    // row positions take 8 bits up to 256 neighbours, 10 bits beyond
+    static constexpr int SH = WORDS > 8 ? 10 : 8;
+    static constexpr unsigned PM = (1u << SH) - 1u;
+    using Pos = typename std::conditional<(WORDS > 8), unsigned short, unsigned char>::type;
+    using Pair = typename std::conditional<(WORDS > 8), unsigned, unsigned short>::type;
     float4 qf[M];   // (qx, qy, qz, a_x): coordinates exact, a_x rounded once
     int ai[M];      // a_x exact
     int s[M];       // W_x + A
@@ -90,15 +97,15 @@ struct WarpSmem {
     unsigned Mrow[M][WORDS];
     unsigned Trow[M][WORDS];
     unsigned up[WORDS];
-    unsigned char uplist[M];
+    Pos uplist[M];
     unsigned char upf[M];  // edge (i, x) in Sigma^1, by position
     int n_up;
     int n_tet, n_tri, n_edge;
     int rowpre[M + 1];                // prefix sums of candidate counts per row of up
     int pairpre[PAIR_CHUNK + 1];      // prefix sums of tetrahedron candidates per Sigma^2 pair
-    unsigned short plist[PL_CAP];     // Sigma^2 pairs (p | k << 8) in enumeration order
+    Pair plist[PL_CAP];               // Sigma^2 pairs (p | k << SH) in enumeration order
     int n_pl;                         // pairs found (the list holds them while n_pl <= PL_CAP)
-    unsigned cand[CAND_CAP];          // candidate codes (p | k << 8 [| l << 16]) of the current batch
+    unsigned cand[CAND_CAP];          // candidate codes (p | k << SH [| l << 2 SH]) of the current batch
     int4 st_tet[STAGE];
     int4 st_tri[STAGE];
     int2 st_edge[STAGE];
@@ -618,7 +625,7 @@ __global__ void __launch_bounds__(256, 4) k_local(LocalArgs A) {
 #pragma unroll 1
             for (int w = 0; w < nw; w++) {
                 const unsigned b = S.up[w];
-                if ((b >> lane) & 1u) S.uplist[base + __popc(b & lanemask_lt())] = (unsigned char)(32 * w + lane);
+                if ((b >> lane) & 1u) S.uplist[base + __popc(b & lanemask_lt())] = (typename SM::Pos)(32 * w + lane);
                 base += __popc(b);
             }
             if (lane == 0) {
@@ -710,7 +717,7 @@ __global__ void __launch_bounds__(256, 4) k_local(LocalArgs A) {
         // ---- phase C: triangles (i,p,k): AC3, then AC2 at the orthocentre -----
         // Candidates of row r (p = uplist[r]): k in M[p] & up, k > p. Rows are
         // taken 32 at a time, one per lane; each writes its candidates as codes
-        // p | k << 8 to cand[] in row order (CAND_CAP per batch), and windows
+        // p | k << SH to cand[] in row order (CAND_CAP per batch), and windows
         // of 32 candidates read them back.
 #pragma unroll 1
         for (int r0 = 0; r0 < n_up; r0 += 32) {
@@ -730,7 +737,7 @@ __global__ void __launch_bounds__(256, 4) k_local(LocalArgs A) {
                         while (b) {
                             const int k = 32 * w + __ffs(b) - 1;
                             b &= b - 1;
-                            if (t >= done && t < done + CAND_CAP) S.cand[t - done] = (unsigned)p | ((unsigned)k << 8);
+                            if (t >= done && t < done + CAND_CAP) S.cand[t - done] = (unsigned)p | ((unsigned)k << SM::SH);
                             t++;
                         }
                     }
@@ -748,8 +755,8 @@ __global__ void __launch_bounds__(256, 4) k_local(LocalArgs A) {
                     o.ac3 = -1;
                     if (valid) {
                         const unsigned code = S.cand[j];
-                        pp = code & 255u;
-                        kk = code >> 8;
+                        pp = code & SM::PM;
+                        kk = code >> SM::SH;
                         n_ac3t++;
                         o = ortho_tri<R>(point<R>(S, pp), point<R>(S, kk), T, B);
                         if (o.ac3 >= 0) {
@@ -776,7 +783,7 @@ __global__ void __launch_bounds__(256, 4) k_local(LocalArgs A) {
                         const bool tp = valid && (keep_it || pend_ac3);
                         const unsigned bt = __ballot_sync(FULL, tp);
                         const int slot = S.n_pl + __popc(bt & lanemask_lt());
-                        if (tp && slot < PL_CAP) S.plist[slot] = (unsigned short)(pp | (kk << 8));
+                        if (tp && slot < PL_CAP) S.plist[slot] = (typename SM::Pair)(pp | (kk << SM::SH));
                         __syncwarp();
                         if (lane == 0) S.n_pl += __popc(bt);
                         __syncwarp();
@@ -801,7 +808,7 @@ __global__ void __launch_bounds__(256, 4) k_local(LocalArgs A) {
         // them, located by a prefix and a binary search). Pairs are taken
         // PAIR_CHUNK at a time with a prefix over their candidate counts
         // popc(T[p] & T[k]); their candidates l are written as codes
-        // p | k << 8 | l << 16 to cand[] (CAND_CAP per batch) and read back by
+        // p | k << SH | l << 2 SH to cand[] (CAND_CAP per batch) and read back by
         // windows of 32.
         const bool use_list = S.n_pl <= PL_CAP;
         if (!use_list) {
@@ -827,7 +834,7 @@ __global__ void __launch_bounds__(256, 4) k_local(LocalArgs A) {
             const int r = row_of(S.rowpre, n_up, j);
             const int p = S.uplist[r];
             const int k = nth_in_words(nw, j - S.rowpre[r], [&](int w) { return S.Trow[p][w]; });
-            return (unsigned)(p | (k << 8));
+            return (unsigned)(p | (k << SM::SH));
         };
         // AC3 then AC2 for the batch of candidate codes in cand[0, nbatch), 32 per window
         auto tet_windows = [&](int nbatch) {
@@ -842,9 +849,9 @@ __global__ void __launch_bounds__(256, 4) k_local(LocalArgs A) {
                 o.ac3 = -1;
                 if (valid) {
                     const unsigned code = S.cand[j];
-                    p3 = code & 255u;
-                    k3 = (code >> 8) & 255u;
-                    ll = code >> 16;
+                    p3 = code & SM::PM;
+                    k3 = (code >> SM::SH) & SM::PM;
+                    ll = code >> (2 * SM::SH);
                     n_ac3k++;
                     o = ortho_tet<R>(point<R>(S, p3), point<R>(S, k3), point<R>(S, ll), T, B);
                     if (o.ac3 > 0) {
@@ -889,7 +896,7 @@ __global__ void __launch_bounds__(256, 4) k_local(LocalArgs A) {
                     mk0[t] = mk1[t] = 0u;
                     if (j < n_pairs) {
                         code[t] = pair_code(j);
-                        const int p = code[t] & 255u, k = code[t] >> 8;
+                        const int p = code[t] & SM::PM, k = code[t] >> SM::SH;
                         mk0[t] = S.Trow[p][0] & S.Trow[k][0];
                         if (WORDS > 1) mk1[t] = S.Trow[p][WORDS - 1] & S.Trow[k][WORDS - 1];
                         mine += __popc(mk0[t]) + __popc(mk1[t]);
@@ -910,7 +917,7 @@ __global__ void __launch_bounds__(256, 4) k_local(LocalArgs A) {
                                     const int l = 32 * w + __ffs(b) - 1;
                                     b &= b - 1;
                                     if (t >= done && t < done + CAND_CAP)
-                                        S.cand[t - done] = code[u] | ((unsigned)l << 16);
+                                        S.cand[t - done] = code[u] | ((unsigned)l << (2 * SM::SH));
                                     t++;
                                 }
                             }
@@ -930,8 +937,8 @@ __global__ void __launch_bounds__(256, 4) k_local(LocalArgs A) {
                         int c = 0;
                         if (q0 + lane < cn) {
                             const unsigned code = pair_code(c0 + q0 + lane);
-                            const int p = code & 255u, k = code >> 8;
-                            if (!use_list) S.plist[q0 + lane] = (unsigned short)code;  // chunk-local copy
+                            const int p = code & SM::PM, k = code >> SM::SH;
+                            if (!use_list) S.plist[q0 + lane] = (typename SM::Pair)code;  // chunk-local copy
                             for (int w = 0; w < nw; w++) c += __popc(S.Trow[p][w] & S.Trow[k][w]);
                         }
                         int tot;
@@ -949,14 +956,14 @@ __global__ void __launch_bounds__(256, 4) k_local(LocalArgs A) {
                         const int a0 = S.pairpre[q], a1 = S.pairpre[q + 1];
                         if (a1 <= done || a0 >= done + CAND_CAP) continue;
                         const unsigned code = S.plist[(use_list ? c0 : 0) + q];
-                        const int p = code & 255u, k = code >> 8;
+                        const int p = code & SM::PM, k = code >> SM::SH;
                         int t = a0;
                         for (int w = 0; w < nw; w++) {
                             unsigned b = S.Trow[p][w] & S.Trow[k][w];
                             while (b) {
                                 const int l = 32 * w + __ffs(b) - 1;
                                 b &= b - 1;
-                                if (t >= done && t < done + CAND_CAP) S.cand[t - done] = code | ((unsigned)l << 16);
+                                if (t >= done && t < done + CAND_CAP) S.cand[t - done] = code | ((unsigned)l << (2 * SM::SH));
                                 t++;
                             }
                         }
@@ -1308,7 +1315,8 @@ static int launch_words(ac_ctx* c, int words, const LocalArgs& a, int warps, cud
     return words == 1 ? launch_local<1, R>(c, a, a.n, warps, s)
            : words == 2 ? launch_local<2, R>(c, a, a.n, warps, s)
            : words == 4 ? launch_local<4, R>(c, a, a.n, warps, s)
-                        : launch_local<8, R>(c, a, a.n, warps, s);
+           : words == 8 ? launch_local<8, R>(c, a, a.n, warps, s)
+                        : launch_local<16, R>(c, a, a.n, warps, s);
 }
 
 // One per-atom pass over the work order (decreasing neighbour count). When
@@ -1403,10 +1411,10 @@ int run_local(ac_ctx* c, cudaStream_t s) {
     const int64_t n = c->n;
     DevCounters h = c->replaying ? c->rec.post : c->hc;  // read after the neighbour count pass
     const int maxdeg = h.max_degree;
-    int words = maxdeg <= 32 ? 1 : maxdeg <= 64 ? 2 : maxdeg <= 128 ? 4 : maxdeg <= 256 ? 8 : 0;
+    int words = maxdeg <= 32 ? 1 : maxdeg <= 64 ? 2 : maxdeg <= 128 ? 4 : maxdeg <= 256 ? 8 : maxdeg <= 512 ? 16 : 0;
     if (words == 0) {
         char b[128];
-        snprintf(b, sizeof(b), "an atom has %d neighbours; the per-atom kernel handles at most 256", maxdeg);
+        snprintf(b, sizeof(b), "an atom has %d neighbours; the per-atom kernel handles at most 512", maxdeg);
         return fail(AC_ERR_CAPACITY, b);
     }
     size_t nn = (size_t)(n > 0 ? n : 1);

@@ -196,10 +196,11 @@ def test_rebuild_is_deterministic():
         assert np.array_equal(fv[d], gpu.filtration_values(d).cpu().numpy())
 
 
-def test_star_with_oversized_buckets():
-    """Atom 0 at the centre of 250 atoms on a sphere: 496 tetrahedra, 744 triangles and 250 edges share
-    their first vertex, beyond one warp's sort (256 items), and atom 0 has 250 neighbours (widest rows)."""
-    k = 250
+@pytest.mark.parametrize("k", [250, 400])
+def test_star_with_oversized_buckets(k):
+    """Atom 0 at the centre of k atoms on a sphere: 2k - 4 tetrahedra, 3k - 6 triangles and k edges share
+    their first vertex, beyond one warp's sort (256 items), and atom 0 has k neighbours (wide rows: 256
+    entries for k = 250, 512 for k = 400)."""
     i = np.arange(k) + 0.5
     phi = np.arccos(1 - 2 * i / k)
     th = np.pi * (1 + 5 ** 0.5) * i

@@ -33,3 +33,21 @@ def test_particles_chunked_equal_whole():
     for d in range(4):
         assert np.array_equal(ch.simplices(d), whole.simplices(d).cpu().numpy())
         assert np.array_equal(ch.filtration_values(d), whole.filtration_values(d).cpu().numpy())
+
+
+def test_particles_beyond_256_neighbours():
+    """Radii over a factor of 12: some particles have 257..512 grown-ball neighbours (the per-atom
+    kernel's 512-entry rows, 10-bit row positions); the complex still equals the oracle's."""
+    c, r = synth.particles(14, 3000, r_hi=3.0)
+    gpu = run_gpu(c, r, 0.0)
+    assert 256 < gpu.stats()["max_degree"] <= 512
+    assert_same_complex(gpu, oracle.alpha_complex(c, r, 0.0))
+
+
+def test_particles_beyond_512_neighbours_refused():
+    import paper_1908_05944_gb300 as ac
+
+    c, r = synth.particles(14, 3000, r_hi=4.0)
+    with pytest.raises(ac.AlphacError) as e:
+        run_gpu(c, r, 0.0)
+    assert e.value.code == ac.AC_ERR_CAPACITY and "at most 512" in str(e.value)
