@@ -210,6 +210,50 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_lookback(const T* in, T* 
     }
 }
 
+// Two-pass scan for up to SCAN_SMALL_TILES tiles (4 M elements): the tile
+// sums, then every tile adds up the sums before it (at most a few thousand
+// values) and scans itself. No tile waits on another.
+constexpr int64_t SCAN_SMALL_TILES = 1024;
+
+template <class T>
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_sums(const T* in, int64_t n, T* agg) {
+    __shared__ T total_s;
+    const int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
+    T sum = 0;
+#pragma unroll
+    for (int k = 0; k < SCAN_ITEMS; k++) {
+        const int64_t i = base + k;
+        if (i < n) sum += in[i];
+    }
+    block_excl_scan<T>(sum, &total_s);
+    if (threadIdx.x == 0) agg[blockIdx.x] = total_s;
+}
+
+template <class T>
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_tiles(const T* in, T* out, int64_t n, const T* agg) {
+    __shared__ T before_s;
+    __shared__ T total_s;
+    T p = 0;
+    for (int t = threadIdx.x; t < (int)blockIdx.x; t += SCAN_THREADS) p += agg[t];
+    block_excl_scan<T>(p, &before_s);  // before_s: the sum of the tiles before this one
+    const int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
+    T v[SCAN_ITEMS];
+    T sum = 0;
+#pragma unroll
+    for (int k = 0; k < SCAN_ITEMS; k++) {
+        const int64_t i = base + k;
+        v[k] = i < n ? in[i] : T(0);
+        sum += v[k];
+    }
+    T pre = block_excl_scan<T>(sum, &total_s) + before_s;
+#pragma unroll
+    for (int k = 0; k < SCAN_ITEMS; k++) {
+        const int64_t i = base + k;
+        if (i <= n) out[i] = pre;
+        pre += v[k];
+    }
+}
+
 template <class T>
 static int scan_entry(const T* in, T* out, int64_t n, DevBuf& tmp, DevCounters* dc, cudaStream_t s) {
     if (n <= 0) {
@@ -217,6 +261,14 @@ static int scan_entry(const T* in, T* out, int64_t n, DevBuf& tmp, DevCounters* 
         return AC_OK;
     }
     const int64_t tiles = n / SCAN_TILE + 1;  // n + 1 outputs
+    if (tiles <= SCAN_SMALL_TILES) {
+        AC_TRY(tmp.reserve((size_t)tiles * sizeof(T), s));
+        k_scan_sums<T><<<(unsigned)tiles, SCAN_THREADS, 0, s>>>(in, n, tmp.as<T>());
+        AC_LAUNCHED();
+        k_scan_tiles<T><<<(unsigned)tiles, SCAN_THREADS, 0, s>>>(in, out, n, tmp.as<T>());
+        AC_LAUNCHED();
+        return AC_OK;
+    }
     // state: counter, flags (int per tile), aggregates and inclusive prefixes (T per tile)
     const size_t flags_off = 64, agg_off = (flags_off + (size_t)tiles * sizeof(int) + 63) & ~(size_t)63;
     const size_t inc_off = (agg_off + (size_t)tiles * sizeof(T) + 63) & ~(size_t)63;
