@@ -386,26 +386,63 @@ __global__ void k_quantise(const double* __restrict__ centres, const double* __r
             m = mol_of[i];
         }
     }
-    // one atomic per warp and bound when the warp's atoms share a molecule (the usual case)
+    // bounds reduced per warp when its atoms share a molecule (the usual case), then per block
+    // when all of its warps do: one set of atomics per block instead of one per atom
+    __shared__ int red[8][8];  // per warp: molecule (-1: none, -2: mixed), min x y z, max x y z, max W
+    const int wid = threadIdx.x >> 5;
     const int m0 = __shfl_sync(full, m, 0);
     const bool uniform = __all_sync(full, !ok || m == m0) && __any_sync(full, ok);
+    const int big = 0x7fffffff, small = (int)0x80000000;
+    int v[8];
     if (uniform) {
-        const int big = 0x7fffffff, small = (int)0x80000000;
-        const int mnx = __reduce_min_sync(full, ok ? X : big), mny = __reduce_min_sync(full, ok ? Y : big),
-                  mnz = __reduce_min_sync(full, ok ? Z : big);
-        const int mxx = __reduce_max_sync(full, ok ? X : small), mxy = __reduce_max_sync(full, ok ? Y : small),
-                  mxz = __reduce_max_sync(full, ok ? Z : small);
-        const int mw = __reduce_max_sync(full, ok ? W : 0);
-        const int mm = __reduce_max_sync(full, m);
+        v[0] = __reduce_max_sync(full, m);
+        v[1] = __reduce_min_sync(full, ok ? X : big);
+        v[2] = __reduce_min_sync(full, ok ? Y : big);
+        v[3] = __reduce_min_sync(full, ok ? Z : big);
+        v[4] = __reduce_max_sync(full, ok ? X : small);
+        v[5] = __reduce_max_sync(full, ok ? Y : small);
+        v[6] = __reduce_max_sync(full, ok ? Z : small);
+        v[7] = __reduce_max_sync(full, ok ? W : 0);
+    } else {
+        v[0] = __any_sync(full, ok) ? -2 : -1;
+    }
+    if (lane == 0)
+        for (int k = 0; k < 8; k++) red[wid][k] = v[k];
+    __syncthreads();
+    const int nw = blockDim.x >> 5;  // 256-thread blocks: 8 warps
+    int bm = -1;                      // the block's molecule, or -2 if its warps differ
+    for (int w = 0; w < nw; w++) {
+        const int mw = red[w][0];
+        if (mw == -1) continue;
+        bm = (bm == -1 && mw >= 0) ? mw : (bm == mw ? bm : -2);
+    }
+    if (bm >= 0) {
+        if (threadIdx.x == 0) {
+            int r[8] = {bm, big, big, big, small, small, small, 0};
+            for (int w = 0; w < nw; w++) {
+                if (red[w][0] < 0) continue;
+                for (int k = 1; k <= 3; k++) r[k] = min(r[k], red[w][k]);
+                for (int k = 4; k <= 7; k++) r[k] = max(r[k], red[w][k]);
+            }
+            int32_t* b = bbox + 6 * bm;
+            atomicMin(&b[0], r[1]);
+            atomicMin(&b[1], r[2]);
+            atomicMin(&b[2], r[3]);
+            atomicMax(&b[3], r[4]);
+            atomicMax(&b[4], r[5]);
+            atomicMax(&b[5], r[6]);
+            atomicMax(wmax, r[7]);
+        }
+    } else if (uniform) {
         if (lane == 0) {
-            int32_t* b = bbox + 6 * mm;
-            atomicMin(&b[0], mnx);
-            atomicMin(&b[1], mny);
-            atomicMin(&b[2], mnz);
-            atomicMax(&b[3], mxx);
-            atomicMax(&b[4], mxy);
-            atomicMax(&b[5], mxz);
-            atomicMax(wmax, mw);
+            int32_t* b = bbox + 6 * v[0];
+            atomicMin(&b[0], v[1]);
+            atomicMin(&b[1], v[2]);
+            atomicMin(&b[2], v[3]);
+            atomicMax(&b[3], v[4]);
+            atomicMax(&b[4], v[5]);
+            atomicMax(&b[5], v[6]);
+            atomicMax(wmax, v[7]);
         }
     } else if (ok) {
         int32_t* b = bbox + 6 * m;
