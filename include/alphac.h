@@ -79,7 +79,9 @@ typedef struct {
     int32_t host_results;    /* 1: ac_build also copies every list (rows, filtration values,
                                 attached flags) to page-locked host memory owned by the context,
                                 each list as soon as it is final, overlapping the rest of the
-                                build; read them with ac_get_simplices_host */
+                                build; read them with ac_get_simplices_host. The blocks go back
+                                to a process-wide cache (at most 8 GB) at ac_destroy, for the
+                                next context */
     int32_t reserved[6];
 } ac_options;
 
