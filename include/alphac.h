@@ -213,7 +213,8 @@ AC_API int ac_backward_noalloc(ac_ctx* ctx, const double* const d_dLdf[4], doubl
 /*
  * Choose the grid cell side (cell_factor in units of sqrt(r_max^2 + alpha))
  * and the warps per block of the per-atom kernel by timing builds of this
- * context over a small grid of both (about two dozen builds); the fastest is
+ * context over a small grid of both (cell factors 0.5 to 2, 4 to 8 warps: 36
+ * builds); the fastest is
  * kept in the context, a final ac_build leaves valid results, and the choice
  * is copied to *chosen (may be NULL). Results do not depend on the choice.
  * Same errors as ac_build.

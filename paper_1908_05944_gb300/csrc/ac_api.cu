@@ -1083,7 +1083,8 @@ extern "C" int ac_autotune(ac_ctx* c, void* stream, ac_options* chosen) {
     if (!c) return fail(AC_ERR_INVALID_ARG, "ctx is NULL");
     c->plan_fresh = false;  // every trial plans its own grid
     // grid cell side (in units of h) and warps per block of the per-atom kernel
-    const double factors[4] = {1.0, 1.25, 1.5, 2.0};
+    // (cells below h pay off for inputs with widely spread radii, above h for sparse ones)
+    const double factors[6] = {0.5, 0.75, 1.0, 1.25, 1.5, 2.0};
     const int warps[3] = {4, 6, 8};
     const ac_options base = c->opt;
     ac_options best = base;
