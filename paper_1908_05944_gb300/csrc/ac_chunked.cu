@@ -438,7 +438,9 @@ extern "C" int ac_build_chunked(const double* centres, const double* radii, int6
                 r0 = r1;
             }
         }
-        std::fill(off.begin(), off.end(), 0);
+        parallel_ranges(n + 1, threads, [&](int, int64_t v0, int64_t v1) {
+            std::fill(off.begin() + v0, off.begin() + v1, 0);
+        });
         auto runs = [&](const Piece& q, const std::function<void(int32_t, int64_t, int64_t)>& fn) {
             const Share& S = shares[(size_t)q.c][d];
             for (int64_t r = q.r0; r < q.r1;) {
@@ -452,7 +454,23 @@ extern "C" int ac_build_chunked(const double* centres, const double* radii, int6
         parallel_for((int64_t)pieces.size(), threads, [&](int64_t pi) {
             runs(pieces[(size_t)pi], [&](int32_t v, int64_t r, int64_t e) { off[(size_t)v + 1] = e - r; });
         });
-        for (int64_t v = 0; v < n; v++) off[(size_t)v + 1] += off[(size_t)v];
+        {
+            // inclusive prefix over off[1..n] in ranges: range sums, their prefix, then each range
+            std::vector<int64_t> part((size_t)threads + 1, 0);
+            parallel_ranges(n, threads, [&](int t, int64_t v0, int64_t v1) {
+                int64_t acc = 0;
+                for (int64_t v = v0; v < v1; v++) acc += off[(size_t)v + 1];
+                part[(size_t)t + 1] = acc;
+            });
+            for (int t = 0; t < threads; t++) part[(size_t)t + 1] += part[(size_t)t];
+            parallel_ranges(n, threads, [&](int t, int64_t v0, int64_t v1) {
+                int64_t acc = part[(size_t)t];
+                for (int64_t v = v0; v < v1; v++) {
+                    acc += off[(size_t)v + 1];
+                    off[(size_t)v + 1] = acc;
+                }
+            });
+        }
         const int64_t total = off[(size_t)n];
         if (!res->t[d].reset(total * k) || !res->f[d].reset(total) || !res->a[d].reset(total))
             return fail(AC_ERR_OOM, "host allocation of the result failed");
