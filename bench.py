@@ -511,7 +511,10 @@ def run_reference(args, rank, world):
     import oracle
 
     c, r = workload(args.workload)
-    sc, sr = sub_ball(c, r, 20000)
+    # about 0.7 s of oracle work per 20,000-atom step on 16 cores: smaller samples when many steps
+    # are asked for, so that the whole run stays within a few minutes
+    sample_atoms = int(min(20000, max(2000, 20000 * 100 // max(1, args.steps + args.warmup))))
+    sc, sr = sub_ball(c, r, sample_atoms)
     threads = os.cpu_count() or 1
     for _ in range(args.warmup):
         oracle.alpha_complex(sc, sr, 0.0, threads=threads)
