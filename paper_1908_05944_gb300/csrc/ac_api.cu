@@ -759,12 +759,15 @@ static int create_impl(const double* centres, const double* radii, const int64_t
         (rc = c->d_moloff.reserve((size_t)(n_mol + 1) * sizeof(int64_t), s)) ||
         (rc = c->counters.reserve(sizeof(DevCounters), s)))
         return bail(rc);
+    // stream-ordered copies: the quantisation below waits for its bounds before ac_create
+    // returns, so the caller's buffers are free again by then
     if (n > 0) {
-        if (cudaMemcpy(c->centres.p, centres, (size_t)n * 3 * sizeof(double), cudaMemcpyDefault) != cudaSuccess ||
-            cudaMemcpy(c->radii.p, radii, (size_t)n * sizeof(double), cudaMemcpyDefault) != cudaSuccess)
+        if (cudaMemcpyAsync(c->centres.p, centres, (size_t)n * 3 * sizeof(double), cudaMemcpyDefault, s) != cudaSuccess ||
+            cudaMemcpyAsync(c->radii.p, radii, (size_t)n * sizeof(double), cudaMemcpyDefault, s) != cudaSuccess)
             return bail(cuda_fail(cudaGetLastError(), "copy of centres/radii", __FILE__, __LINE__));
     }
-    if (cudaMemcpy(c->d_moloff.p, offsets, (size_t)(n_mol + 1) * sizeof(int64_t), cudaMemcpyHostToDevice) != cudaSuccess)
+    if (cudaMemcpyAsync(c->d_moloff.p, offsets, (size_t)(n_mol + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s) !=
+        cudaSuccess)
         return bail(cuda_fail(cudaGetLastError(), "copy of offsets", __FILE__, __LINE__));
 
     k_fill_mol<<<(unsigned)n_mol, 256, 0, s>>>(c->d_moloff.as<int64_t>(), n_mol, c->mol_of.as<int32_t>());
