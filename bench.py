@@ -289,6 +289,19 @@ def run_forms(args):
         out[f"{wl}/{prec}"] = {"atoms_per_s": n * steps / (sum(ms) / 1e3), "ms_per_step": sum(ms) / steps,
                                "simplices": st["simplices"], "local_kernel_ms": loc, "local_tflops": tf,
                                "local_frac_fp32_peak_2070mhz": tf / (SMS * FP32_LANES_PER_SM * 2 * 2070e6 / 1e12)}
+        if prec == "plain_fp64":
+            # the filtered FP32 cascade against plain FP64 on the same input: lists and values
+            fx = ac.AlphaComplex(torch.from_numpy(c_np).cuda(), torch.from_numpy(r_np).cuda(), 0.0).build(stream)
+            same, worst = True, 0.0
+            for d in range(4):
+                same = same and torch.equal(fx.simplices(d), cx.simplices(d))
+                same = same and torch.equal(fx.attached(d), cx.attached(d))
+                f32, f64 = fx.filtration_values(d), cx.filtration_values(d)
+                if f32.shape == f64.shape and f32.numel():
+                    den = f64.abs().clamp_min(1e-300)
+                    worst = max(worst, float(((f32 - f64).abs() / den).max()))
+            out[f"{wl}/{prec}"]["filtered_vs_plain_fp64"] = {"lists_equal": bool(same), "f_max_rel_diff": worst}
+            fx.close()
         cx.close()
         del cx
     # out-of-core build (Section 4.6): host arrays in, host lists out, z-slabs of at most max_core atoms
