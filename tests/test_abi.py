@@ -67,3 +67,33 @@ def test_stats_struct_layout_matches_header():
     body = body[: body.index("} ac_stats;")]
     fields = re.findall(r"^\s+\w+\s+(\w+)(?:\[\d\])?;", body, flags=re.M)
     assert fields == [f for f, _ in ac.ac_stats._fields_]
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """The ctypes mirrors of ac_options, ac_stats and ac_chunked_stats have the C layout: sizes and
+    field offsets printed by a program compiled from the header with the system C compiler."""
+    import shutil
+    import subprocess
+
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = {"ac_options": ac.ac_options, "ac_stats": ac.ac_stats, "ac_chunked_stats": ac.ac_chunked_stats}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "alphac.h"', "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append(f'  printf("{name} size %zu\\n", sizeof({name}));')
+        for field, _ in cls._fields_:
+            lines.append(f'  printf("{name} {field} %zu\\n", offsetof({name}, {field}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.dirname(HEADER), str(src), "-o", str(exe)], check=True)
+    got = {}
+    for ln in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.splitlines():
+        name, key, val = ln.split()
+        got[(name, key)] = int(val)
+    for name, cls in structs.items():
+        assert got[(name, "size")] == ctypes.sizeof(cls), name
+        for field, _ in cls._fields_:
+            assert got[(name, field)] == getattr(cls, field).offset, (name, field)
