@@ -308,10 +308,11 @@ def run_forms(args):
     # plus halo on the device at a time; against one whole-molecule build with the same host round trip
     c3, r3 = workload("shell3m_probe")
     t0 = time.perf_counter()
-    whole = ac.AlphaComplex(c3, r3, 0.0).build(stream)
-    host = [(whole.simplices(d).cpu().numpy(), whole.attached(d).cpu().numpy(),
-             whole.filtration_values(d).cpu().numpy()) for d in range(4)]
+    whole = ac.AlphaComplex(c3, r3, 0.0, ac.options(host_results=True)).build(stream)
+    views = [whole.host_lists(d, copy=False) for d in range(4)]  # host lists made during the build
     whole_s = time.perf_counter() - t0
+    host = [(t_.copy(), a_.copy(), f_.copy()) for t_, f_, a_ in views]  # kept past the context, untimed
+    del views
     whole.close()
     del whole
     for max_core in (1_000_000, 250_000):
