@@ -307,18 +307,25 @@ def run_forms(args):
     # out-of-core build (Section 4.6): host arrays in, host lists out, z-slabs of at most max_core atoms
     # plus halo on the device at a time; against one whole-molecule build with the same host round trip
     c3, r3 = workload("shell3m_probe")
-    t0 = time.perf_counter()
-    whole = ac.AlphaComplex(c3, r3, 0.0, ac.options(host_results=True)).build(stream)
-    views = [whole.host_lists(d, copy=False) for d in range(4)]  # host lists made during the build
-    whole_s = time.perf_counter() - t0
+    for rep in range(2):  # the second round trip is timed (the first also takes the page-locked blocks)
+        if rep:
+            whole.close()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        whole = ac.AlphaComplex(c3, r3, 0.0, ac.options(host_results=True)).build(stream)
+        views = [whole.host_lists(d, copy=False) for d in range(4)]  # host lists made during the build
+        whole_s = time.perf_counter() - t0
     host = [(t_.copy(), a_.copy(), f_.copy()) for t_, f_, a_ in views]  # kept past the context, untimed
     del views
     whole.close()
     del whole
     for max_core in (1_000_000, 250_000):
-        t0 = time.perf_counter()
-        ch = ac.ChunkedComplex(c3, r3, 0.0, max_core, stream=stream)
-        chunk_s = time.perf_counter() - t0
+        for rep in range(2):  # the second run is timed: the first also pays the host allocator's first touches
+            if rep:
+                ch.close()
+            t0 = time.perf_counter()
+            ch = ac.ChunkedComplex(c3, r3, 0.0, max_core, stream=stream)
+            chunk_s = time.perf_counter() - t0
         st = ch.stats()
         equal = all(np.array_equal(ch.simplices(d), host[d][0]) and np.array_equal(ch.attached(d), host[d][1])
                     and np.array_equal(ch.filtration_values(d), host[d][2]) for d in range(4))
