@@ -307,33 +307,43 @@ def run_forms(args):
     # out-of-core build (Section 4.6): host arrays in, host lists out, z-slabs of at most max_core atoms
     # plus halo on the device at a time; against one whole-molecule build with the same host round trip
     c3, r3 = workload("shell3m_probe")
-    for rep in range(2):  # the second round trip is timed (the first also takes the page-locked blocks)
-        if rep:
-            whole.close()
+    reps = 3  # timed round trips of each kind after one untimed one (which also takes the page-locked blocks)
+    whole_ms = []
+    for rep in range(reps + 1):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         whole = ac.AlphaComplex(c3, r3, 0.0, ac.options(host_results=True)).build(stream)
         views = [whole.host_lists(d, copy=False) for d in range(4)]  # host lists made during the build
-        whole_s = time.perf_counter() - t0
+        if rep:
+            whole_ms.append(1e3 * (time.perf_counter() - t0))
+        if rep < reps:
+            del views
+            whole.close()
     host = [(t_.copy(), a_.copy(), f_.copy()) for t_, f_, a_ in views]  # kept past the context, untimed
     del views
     whole.close()
     del whole
     for max_core in (1_000_000, 250_000):
-        for rep in range(2):  # the second run is timed: the first also pays the host allocator's first touches
-            if rep:
-                ch.close()
+        runs = []
+        for rep in range(reps + 1):
             t0 = time.perf_counter()
             ch = ac.ChunkedComplex(c3, r3, 0.0, max_core, stream=stream)
-            chunk_s = time.perf_counter() - t0
-        st = ch.stats()
+            wall = 1e3 * (time.perf_counter() - t0)
+            if rep:
+                runs.append((wall, ch.stats()))
+            if rep < reps:
+                ch.close()
+        wall, st = sorted(runs, key=lambda x: x[0])[reps // 2]  # the median run
         equal = all(np.array_equal(ch.simplices(d), host[d][0]) and np.array_equal(ch.attached(d), host[d][1])
                     and np.array_equal(ch.filtration_values(d), host[d][2]) for d in range(4))
         out[f"shell3m_probe/chunked_{max_core}"] = {
-            "atoms_per_s": len(r3) / chunk_s, "wall_ms": chunk_s * 1e3, "n_chunks": st["n_chunks"],
-            "subset_max": st["subset_max"], "halo_overhead": st["subset_total"] / len(r3) - 1.0,
+            "atoms_per_s": len(r3) / (wall * 1e-3), "wall_ms": wall, "wall_ms_runs": [w for w, _ in runs],
+            "n_chunks": st["n_chunks"], "subset_max": st["subset_max"],
+            "halo_overhead": st["subset_total"] / len(r3) - 1.0,
             "ms_plan": st["ms_plan"], "ms_device": st["ms_device"], "ms_assemble": st["ms_assemble"],
-            "equal_to_whole_build": bool(equal), "whole_build_host_round_trip_ms": whole_s * 1e3}
+            "equal_to_whole_build": bool(equal), "whole_build_host_round_trip_ms": float(np.median(whole_ms)),
+            "whole_build_host_round_trip_ms_runs": whole_ms}
+        ch.close()
         del ch
     del host
     # context for the paper's Table 1 row of its largest unpartitioned molecule (58,674 atoms, van der Waals

@@ -222,16 +222,18 @@ void parallel_for(int64_t n, int threads, const std::function<void(int64_t)>& fn
 int build_slab(const double* centres, const double* radii, const int32_t* members, int64_t m, int64_t lo, int64_t hi,
                const SlabPlan& P, double alpha, const ac_options& opt, cudaStream_t s, double* h_xyz, double* h_r,
                int32_t* h_g, uint8_t* h_core, int64_t* h_cnt, SlabBufs& B, Share* out) {
-    for (int64_t j = 0; j < m; j++) {
-        const int64_t i = members[j];
-        h_xyz[3 * j] = centres[3 * i];
-        h_xyz[3 * j + 1] = centres[3 * i + 1];
-        h_xyz[3 * j + 2] = centres[3 * i + 2];
-        h_r[j] = radii[i];
-        h_g[j] = (int32_t)i;
-        const int64_t Z = P.Z[(size_t)i];
-        h_core[j] = (uint8_t)(Z >= lo && Z < hi);
-    }
+    parallel_ranges(m, host_threads(), [&](int, int64_t j0, int64_t j1) {
+        for (int64_t j = j0; j < j1; j++) {
+            const int64_t i = members[j];
+            h_xyz[3 * j] = centres[3 * i];
+            h_xyz[3 * j + 1] = centres[3 * i + 1];
+            h_xyz[3 * j + 2] = centres[3 * i + 2];
+            h_r[j] = radii[i];
+            h_g[j] = (int32_t)i;
+            const int64_t Z = P.Z[(size_t)i];
+            h_core[j] = (uint8_t)(Z >= lo && Z < hi);
+        }
+    });
     ac_ctx* c = nullptr;
     AC_TRY(ac_create(h_xyz, h_r, m, alpha, &opt, &c));
     struct Guard {
