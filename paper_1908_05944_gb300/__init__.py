@@ -249,7 +249,7 @@ class AlphaComplex:
     def host_lists(self, dim: int, mol: int = -1, copy: bool = True):
         """(rows, filtration values, attached flags) of list dim as numpy arrays, from the host copies the
         last build made (the context needs options(host_results=True)); copy=False gives views into the
-        context's page-locked memory, valid until its next build."""
+        context's page-locked memory, valid until its next build or close()."""
         t, f, a = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p()
         cnt = ctypes.c_int64()
         _check(lib().ac_get_simplices_host(self._h, dim, mol, ctypes.byref(t), ctypes.byref(f), ctypes.byref(a),
