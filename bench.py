@@ -43,6 +43,10 @@ FLOPS_AC3 = {1: 20.0, 2: 60.0, 3: 120.0}
 FLOPS_AC2 = 12.0
 FP32_LANES_PER_SM = 128
 SMS = 152
+# GB300's FP64 rate is far below its FP32 rate: 1.25 TFLOP/s nominal at the
+# 2,070 MHz maximum SM clock. The plain FP64 path is measured against it.
+FP64_NOMINAL_TFLOPS = 1.25
+MAX_SM_MHZ = 2070.0
 
 
 def parse():
@@ -289,6 +293,8 @@ def run_forms(args):
         out[f"{wl}/{prec}"] = {"atoms_per_s": n * steps / (sum(ms) / 1e3), "ms_per_step": sum(ms) / steps,
                                "simplices": st["simplices"], "local_kernel_ms": loc, "local_tflops": tf,
                                "local_frac_fp32_peak_2070mhz": tf / (SMS * FP32_LANES_PER_SM * 2 * 2070e6 / 1e12)}
+        if prec == "plain_fp64":  # its bounding roofline: the FP64 pipe
+            out[f"{wl}/{prec}"]["local_frac_fp64_nominal_2070mhz"] = tf / FP64_NOMINAL_TFLOPS
         if prec == "plain_fp64":
             # the filtered FP32 cascade against plain FP64 on the same input: lists and values
             fx = ac.AlphaComplex(torch.from_numpy(c_np).cuda(), torch.from_numpy(r_np).cuda(), 0.0).build(stream)
@@ -585,7 +591,13 @@ def main():
     peaks = measured_peaks()
     clocks = res["clocks"]
     sm_mhz = clocks.get("sm_mhz") or peaks.get("clocks_under_load", {}).get("sm_mhz_median") or 2070.0
-    peak_tflops = SMS * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+    if args.precision == "filtered":
+        peak_tflops = SMS * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+        basis = f"FP32 FMA: {SMS} SMs x {FP32_LANES_PER_SM} lanes x 2 x {sm_mhz:.0f} MHz (derived; sampled SM clock)"
+    else:
+        peak_tflops = FP64_NOMINAL_TFLOPS * sm_mhz / MAX_SM_MHZ
+        basis = (f"FP64: nominal {FP64_NOMINAL_TFLOPS} TFLOP/s at {MAX_SM_MHZ:.0f} MHz, scaled to the sampled "
+                 f"{sm_mhz:.0f} MHz")
     achieved = res["local_flops"] / (res["local_ms"] * 1e-3) / 1e12 if res["local_ms"] > 0 else 0.0
     line = {
         "metric": METRIC, "value": res["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -602,10 +614,9 @@ def main():
         "gpu_launches": res["launches"],
         "roofline": {"bound": "alu", "kernel": "k_local (fused estimation + pruning)", "achieved": achieved,
                      "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved / peak_tflops if peak_tflops else None,
-                     "traffic": profiled_traffic(args.workload),
+                     "traffic": profiled_traffic(args.workload) if args.precision == "filtered" else None,
                      "traffic_unit": "bytes per pass (ncu dram read + write, both launches)",
-                     "peak_basis": f"FP32 FMA: {SMS} SMs x {FP32_LANES_PER_SM} lanes x 2 x {sm_mhz:.0f} MHz "
-                                   "(derived; sampled SM clock)"},
+                     "peak_basis": basis},
         "stage_ms": res["stats"]["ms_stage"],
         "predicates": {"ac2_tet": res["stats"]["ac2_tests_tet"], "ac2_tri": res["stats"]["ac2_tests_tri"],
                        "ac2_edge": res["stats"]["ac2_tests_edge"], "ac3": res["stats"]["ac3_tests"]},
