@@ -117,6 +117,24 @@ def test_tiny_inputs(n):
     assert_same_complex(gpu, ref)
 
 
+@pytest.mark.parametrize("mode", MODES)
+def test_halfway_quantisation(mode):
+    # centres and radii halfway between two quanta round half to even on both sides:
+    # a pair of equal balls 2048.5 quanta apart is an edge of Size exactly 0 at alpha = 0,
+    # 2049.5 quanta apart it is not; radii 1000.5 and 1001.5 quanta give R = 1000 and 1002
+    q = 1024.0
+    c = np.array([[0.0, 0.0, 0.0], [2048.5 / q, 0.0, 0.0], [40.0, 0.0, 0.0], [40.0 - 2049.5 / q, 0.0, 0.0],
+                  [0.0, 40.0, 0.0], [0.0, -40.0, 0.0], [0.0, 0.0, -2048.5 / q]])
+    r = np.array([1.0, 1.0, 1.0, 1.0, 1000.5 / q, 1001.5 / q, 1.0])
+    ref = oracle.alpha_complex(c, r, 0.0)
+    gpu = run_gpu(c, r, 0.0, precision=MODES[mode])
+    assert_same_complex(gpu, ref)
+    assert gpu.simplices(1).cpu().numpy().tolist() == [[0, 1], [0, 6]]
+    assert gpu.filtration_values(1).cpu().numpy().tolist() == [0.0, 0.0]
+    f0 = gpu.filtration_values(0).cpu().numpy()
+    assert f0[4] == -(1000 * 1000) / 2.0**20 and f0[5] == -(1002 * 1002) / 2.0**20
+
+
 def test_all_atoms_in_one_cell():
     rng = np.random.default_rng(5)
     c = np.round(rng.uniform(0, 1.5, (12, 3)) * 1024) / 1024

@@ -2,8 +2,8 @@
 
 Each mutation is a plausible slip (a sign, a dropped term, a strict bound, a
 skipped step). It is applied to a temporary copy of ``oracle/alpha_oracle.c``,
-compiled with gcc, and run against the golden fixtures and the brute force; at
-least one comparison must fail. The real oracle is untouched.
+compiled with gcc, and run against the golden fixtures, the quantisation cases
+and the brute force; at least one comparison must fail. The real oracle is untouched.
 """
 import os
 import subprocess
@@ -29,6 +29,9 @@ MUTATIONS = {
                             "for (int64_t t = 0; t < 0; t++)\n        for (int k = 0; k <= d; k++) iv_push(&out, F->v[(d + 1) * t + k]);"),
     "vertices_skip_ac2": ("int ok = simplex_geom(pr, v, c->d, &s) && ac2_holds(pr, v, c->d, &s);",
                           "int ok = simplex_geom(pr, v, c->d, &s) && (c->d == 0 || ac2_holds(pr, v, c->d, &s));"),
+    "quantise_centre_half_away_from_zero": ("pr->P[3 * i + c] = (int64_t)nearbyint(x * 1024.0);",
+                                            "pr->P[3 * i + c] = (int64_t)round(x * 1024.0);"),
+    "quantise_radius_truncates": ("int64_t R = (int64_t)nearbyint(rr * 1024.0);", "int64_t R = (int64_t)(rr * 1024.0);"),
     "violation_ignores_ties": ("return sos_sign(v, s, x, qx) < 0;", "return 0;"),
 }
 
@@ -92,12 +95,30 @@ def _golden_agrees(lib_path):
     return True
 
 
+def _quantisation_agrees(lib_path):
+    """Rounding half to even at 1/1024 A (the cases of test_oracle_quantisation)."""
+    try:
+        for r, R in ((1.7, 1741), (1000.5 / 1024.0, 1000), (1001.5 / 1024.0, 1002)):
+            ac = oracle.alpha_complex(np.array([[0.25, -3.5, 7.0]]), np.array([r]), 0.0, lib_path=lib_path)
+            if len(ac.f[0]) != 1 or ac.f[0][0] != -(R * R) / 2.0**20:
+                return False
+        for x in (2048.5, -2048.5):
+            ac = oracle.alpha_complex(np.array([[0.0, 0.0, 0.0], [x / 1024.0, 0.0, 0.0]]), np.array([1.0, 1.0]), 0.0,
+                                      lib_path=lib_path)
+            if ac.simplices[1].tolist() != [[0, 1]] or ac.f[1][0] != 0.0:
+                return False
+    except oracle.OracleError:
+        return False
+    return True
+
+
 def test_unmutated_copy_passes(brute_cases, tmp_path):
     path = str(tmp_path / "orig.so")
     src = tmp_path / "orig.c"
     src.write_text(SRC)
     subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared", "-pthread", str(src), "-o", path, "-lm"])
     assert _golden_agrees(path)
+    assert _quantisation_agrees(path)
     assert all(_agrees(path, P, R, A, want) for P, R, A, want in brute_cases)
 
 
@@ -109,5 +130,6 @@ def test_mutation_is_caught(name, brute_cases, tmp_path):
     src.write_text(SRC.replace(old, new, 1))
     path = str(tmp_path / "mut.so")
     subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared", "-pthread", str(src), "-o", path, "-lm"])
-    caught = not _golden_agrees(path) or not all(_agrees(path, P, R, A, want) for P, R, A, want in brute_cases)
+    caught = (not _golden_agrees(path) or not _quantisation_agrees(path)
+              or not all(_agrees(path, P, R, A, want) for P, R, A, want in brute_cases))
     assert caught, f"planted mistake {name} passed every pin"
