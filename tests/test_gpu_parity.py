@@ -133,6 +133,15 @@ def test_halfway_quantisation(mode):
     assert gpu.filtration_values(1).cpu().numpy().tolist() == [0.0, 0.0]
     f0 = gpu.filtration_values(0).cpu().numpy()
     assert f0[4] == -(1000 * 1000) / 2.0**20 and f0[5] == -(1002 * 1002) / 2.0**20
+    # alpha halfway between two quanta: equal balls 2050 quanta apart have edge Size 2049 / 2^20;
+    # alpha 2048.5 / 2^20 rounds to 2048 (no edge), 2049.5 / 2^20 to 2050 (edge)
+    c2 = np.array([[0.0, 0.0, 0.0], [2050.0 / q, 0.0, 0.0]])
+    for a_half, edges in ((2048.5, 0), (2049.5, 1)):
+        alpha = a_half / 2.0**20
+        ref = oracle.alpha_complex(c2, np.ones(2), alpha)
+        gpu = run_gpu(c2, np.ones(2), alpha, precision=MODES[mode])
+        assert_same_complex(gpu, ref)
+        assert gpu.count(1) == edges
 
 
 def test_all_atoms_in_one_cell():

@@ -31,6 +31,8 @@ MUTATIONS = {
                           "int ok = simplex_geom(pr, v, c->d, &s) && (c->d == 0 || ac2_holds(pr, v, c->d, &s));"),
     "quantise_centre_half_away_from_zero": ("pr->P[3 * i + c] = (int64_t)nearbyint(x * 1024.0);",
                                             "pr->P[3 * i + c] = (int64_t)round(x * 1024.0);"),
+    "quantise_alpha_half_away_from_zero": ("pr->A = (int64_t)nearbyint(alpha * 1048576.0);",
+                                           "pr->A = (int64_t)round(alpha * 1048576.0);"),
     "quantise_radius_truncates": ("int64_t R = (int64_t)nearbyint(rr * 1024.0);", "int64_t R = (int64_t)(rr * 1024.0);"),
     "violation_ignores_ties": ("return sos_sign(v, s, x, qx) < 0;", "return 0;"),
 }
@@ -107,6 +109,10 @@ def _quantisation_agrees(lib_path):
                                       lib_path=lib_path)
             if ac.simplices[1].tolist() != [[0, 1]] or ac.f[1][0] != 0.0:
                 return False
+        ac = oracle.alpha_complex(np.array([[0.0, 0.0, 0.0], [2050.0 / 1024.0, 0.0, 0.0]]), np.array([1.0, 1.0]),
+                                  2048.5 / 2.0**20, lib_path=lib_path)
+        if len(ac.simplices[1]) != 0:
+            return False
     except oracle.OracleError:
         return False
     return True

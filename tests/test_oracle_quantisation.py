@@ -66,3 +66,14 @@ def test_halfway_centre_rounding_up_to_even_loses_the_edge():
     res = oracle.alpha_complex(c, np.array([1.0, 1.0]), size)
     assert res.simplices[1].tolist() == [[0, 1]]
     assert res.f[1][0] == size
+
+
+@pytest.mark.parametrize("a_half,present", [(2048.5, False), (2049.5, True), (2050.5, True)])
+def test_halfway_alpha_rounds_to_even(a_half, present):
+    # equal balls 2050 quanta apart: edge Size (1025^2 - 1024^2) / 2^20 = 2049 / 2^20.
+    # alpha = a_half / 2^20: 2048.5 rounds to 2048 (edge absent); 2049.5 and 2050.5 round to 2050 (present).
+    c = np.array([[0.0, 0.0, 0.0], [2050.0 / Q, 0.0, 0.0]])
+    res = oracle.alpha_complex(c, np.array([1.0, 1.0]), a_half / 2.0**20)
+    assert (res.simplices[1].tolist() == [[0, 1]]) == present
+    if present:
+        assert res.f[1][0] == 2049.0 / 2.0**20
