@@ -10,8 +10,8 @@
  *
  * Conventions
  *   - Lengths in angstrom, alpha in angstrom^2. Centres and radii are quantised
- *     to 1/1024 A (round half to even); alpha to 2^-20 A^2. Every predicate is
- *     decided exactly on these integers.
+ *     to 1/1024 A and alpha to 2^-20 A^2, each rounded half to even. Every
+ *     predicate is decided exactly on these integers.
  *   - Ties (the paper's "symbolic perturbation", Section 2) are broken by
  *     perturbing the squared radii, W_k + eps_k, with eps_k decreasing steeply
  *     in the INPUT index k. The alpha bound itself (AC3) is not perturbed and
