@@ -36,3 +36,12 @@ def test_package_never_touches_the_oracle():
                 if pattern.search(line):
                     offenders.append(f"{os.path.relpath(path, ROOT)}:{k}: {line.strip()}")
     assert not offenders, "the package refers to the oracle:\n" + "\n".join(offenders)
+
+
+def test_oracle_shares_no_code_with_the_package():
+    # the oracle includes only the C standard library and imports nothing of the package
+    src = open(os.path.join(ROOT, "oracle", "alpha_oracle.c"), encoding="utf-8").read()
+    includes = re.findall(r'#include\s*[<"]([^>"]+)[>"]', src)
+    assert includes and all(i in ("math.h", "pthread.h", "stdint.h", "stdlib.h", "string.h") for i in includes)
+    py = open(os.path.join(ROOT, "oracle", "__init__.py"), encoding="utf-8").read()
+    assert not re.search(r"^\s*(import|from)\s+(paper_1908_05944_gb300|synth)\b", py, re.M)
