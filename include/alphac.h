@@ -124,8 +124,9 @@ AC_API int ac_create(const double* centres, const double* radii, int64_t n, doub
  * Create a context for a batch of independent molecules sharing one alpha.
  * Molecule m is atoms [offsets[m], offsets[m+1]) of centres/radii; offsets is
  * a HOST array of n_mol + 1 non-decreasing int64 starting at 0. Indices in the
- * results are per molecule (0-based within the molecule). Same errors as
- * ac_create.
+ * results are per molecule (0-based within the molecule). Each molecule's
+ * complex is the one ac_create would give it alone (Section 3.1, Steps 1-5):
+ * molecules never interact. Same errors as ac_create.
  */
 AC_API int ac_create_batch(const double* centres, const double* radii, const int64_t* offsets, int64_t n_mol,
                     double alpha, const ac_options* opt, ac_ctx** out);
@@ -144,8 +145,9 @@ AC_API int ac_create_batch(const double* centres, const double* radii, const int
 AC_API int ac_build(ac_ctx* ctx, void* stream);
 
 /*
- * Device pointer to the simplices of dimension dim (0..3): *count rows of
- * dim+1 ascending int32 input indices, sorted lexicographically. mol selects a
+ * Device pointer to the simplices of dimension dim (0..3) of the alpha
+ * complex K_alpha (Section 2.4; K^3..K^0 of Steps 2-5 of Section 3.1): *count
+ * rows of dim+1 ascending int32 input indices, sorted lexicographically. mol selects a
  * molecule of a batch context (-1 for a single-molecule context). Owned by ctx.
  * Errors: AC_ERR_INVALID_ARG, AC_ERR_STATE.
  */
@@ -155,20 +157,24 @@ AC_API int ac_get_simplices(ac_ctx* ctx, int dim, int64_t mol, const int32_t** d
  * Device pointer to one double per simplex of ac_get_simplices(dim, mol), in
  * the same order: Size (Section 2.3) in A^2, or OrthoSize when the context was
  * created with AC_FILTRATION_ORTHOSIZE. Owned by ctx.
+ * Errors: AC_ERR_INVALID_ARG, AC_ERR_STATE (as ac_get_simplices).
  */
 AC_API int ac_filtration_values(ac_ctx* ctx, int dim, int64_t mol, const double** d_f, int64_t* count);
 
 /*
  * Device pointer to one uint8 per simplex of (dim, mol): 1 if AC2 fails at the
  * simplex's own orthocentre (it is in the complex as a face of a larger
- * simplex, "attached"), else 0. Owned by ctx.
+ * simplex, "attached"; Section 2.3 and Steps 3-5 of Section 3.1), else 0.
+ * Owned by ctx. Errors: AC_ERR_INVALID_ARG, AC_ERR_STATE (as ac_get_simplices).
  */
 AC_API int ac_attached_flags(ac_ctx* ctx, int dim, int64_t mol, const uint8_t** d_flags, int64_t* count);
 
 /*
- * Device pointers to the estimation-pass lists Sigma_ortho^dim (dim 1..3) of a
- * context created with keep_candidates = 1 (single molecule only): rows of
- * ascending input indices, sorted lexicographically. AC_ERR_STATE otherwise.
+ * Device pointers to the estimation-pass lists Sigma_ortho^dim (dim 1..3; Step
+ * 1 of Section 3.1, Section 4.3) of a context created with keep_candidates = 1
+ * (single molecule only): rows of ascending input indices, sorted
+ * lexicographically. Owned by ctx. Errors: AC_ERR_INVALID_ARG (NULL, dim
+ * outside 1..3), AC_ERR_STATE (no build, or candidates not kept).
  */
 AC_API int ac_get_candidates(ac_ctx* ctx, int dim, const int32_t** d_tuples, int64_t* count);
 
@@ -179,6 +185,9 @@ AC_API int ac_get_candidates(ac_ctx* ctx, int dim, const int32_t** d_tuples, int
  * its closest witness) and takes that source's OrthoSize, in FP64.
  * d_f_out[dim] receives one double per simplex of dim (device, caller-owned;
  * NULL skips that dimension). For finite-difference checks of ac_backward.
+ * The value is the Size of Section 2.3 through its source. Errors:
+ * AC_ERR_INVALID_ARG (NULL ctx or inputs), AC_ERR_STATE (no build),
+ * AC_ERR_OOM, AC_ERR_CUDA.
  */
 AC_API int ac_eval_filtration(ac_ctx* ctx, const double* d_centres, const double* d_radii, double* const d_f_out[4],
                        void* stream);
@@ -190,6 +199,11 @@ AC_API int ac_eval_filtration(ac_ctx* ctx, const double* d_centres, const double
  * df/dp_k = 2 lambda_k (p_k - c), df/dr_k = -2 r_k lambda_k.
  * d_dLdf[dim]: device, one double per simplex (NULL = zero). Outputs are
  * device, caller-owned, n x 3 and n doubles, OVERWRITTEN (not accumulated).
+ * The paper gives no gradient: this is the derivative of the Size of Section
+ * 2.3, taken through the source simplex's OrthoSize with the source held fixed
+ * (an envelope argument: the multipliers of the equal-power constraints are
+ * the barycentric coordinates of c). Errors: AC_ERR_INVALID_ARG (NULL),
+ * AC_ERR_STATE (no build), AC_ERR_OOM, AC_ERR_CUDA.
  */
 AC_API int ac_backward(ac_ctx* ctx, const double* const d_dLdf[4], double* d_dLdcentres, double* d_dLdradii,
                 void* stream);
@@ -284,7 +298,8 @@ AC_API int ac_chunk_plan(const double* centres, const double* radii, int64_t n, 
                          int64_t* thresholds, int64_t cap, int64_t* n_chunks, int64_t* reach);
 
 /*
- * Build the alpha complex of n HOST balls slab by slab (see above), at most
+ * Build the alpha complex of n HOST balls slab by slab (Section 4.6: the data
+ * split into parts processed one at a time, each with its border), at most
  * max_core_atoms atoms per slab (plus halo) on the device at a time. opt as
  * for ac_create (keep_candidates must be 0). The slabs run one after another
  * on stream; *out receives a result whose lists live in host memory (read
@@ -312,8 +327,9 @@ AC_API int ac_chunked_info(const ac_chunked* res, ac_chunked_stats* out);
 AC_API void ac_chunked_free(ac_chunked* res);
 
 /*
- * Host copies of dimension dim (0..3) of molecule mol (-1 for a single-molecule
- * context), made by the last ac_build of a context created with
+ * Host copies of the K_alpha lists (Section 2.4) of dimension dim (0..3) of
+ * molecule mol (-1 for a single-molecule context), made by the last ac_build
+ * of a context created with
  * opt.host_results = 1: *count rows of dim+1 int32 indices (as
  * ac_get_simplices), their filtration values (as ac_filtration_values) and
  * attached flags (as ac_attached_flags). Page-locked host memory owned by the
@@ -325,10 +341,12 @@ AC_API void ac_chunked_free(ac_chunked* res);
 AC_API int ac_get_simplices_host(ac_ctx* ctx, int dim, int64_t mol, const int32_t** h_tuples, const double** h_f,
                                  const uint8_t** h_attached, int64_t* count);
 
-/* Counters and stage times of the last ac_build. */
+/* Counters and stage times of the last ac_build (all zero before one), copied
+ * to *out. Errors: AC_ERR_INVALID_ARG (NULL). */
 AC_API int ac_get_stats(ac_ctx* ctx, ac_stats* out);
 
-/* Number of molecules (1 for a single-molecule context) and atoms. */
+/* Number of molecules (1 for a single-molecule context) and atoms; either
+ * output may be NULL. Errors: AC_ERR_INVALID_ARG (NULL ctx). */
 AC_API int ac_get_sizes(ac_ctx* ctx, int64_t* n_mol, int64_t* n_atoms);
 
 /* Free the context and everything it owns. NULL is a no-op. */
