@@ -225,7 +225,8 @@ AC_API int ac_backward_noalloc(ac_ctx* ctx, const double* const d_dLdf[4], doubl
                                void* stream);
 
 /*
- * Choose the grid cell side (cell_factor in units of sqrt(r_max^2 + alpha))
+ * Choose the grid cell side (cell_factor in units of sqrt(r_max^2 + alpha),
+ * the side Section 4.2 fixes)
  * and the warps per block of the per-atom kernel by timing builds of this
  * context over a small grid of both (cell factors 0.5 to 2, 4 to 8 warps: 36
  * builds); the fastest is
@@ -283,7 +284,8 @@ typedef struct {
 } ac_chunked_stats;
 
 /*
- * The slab cut alone (host only; no GPU needed). centres n x 3 and radii n
+ * The slab cut of ac_build_chunked alone (Section 4.6; host only, no GPU
+ * needed). centres n x 3 and radii n
  * are HOST doubles (A). Slab k holds the atoms with thresholds[k] <= Z <
  * thresholds[k+1], Z = rint(1024 z); the cuts keep at most max_core_atoms
  * atoms in a slab unless more than that share one cut interval (a run of

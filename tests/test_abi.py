@@ -97,3 +97,23 @@ def test_struct_layouts_match_the_header(tmp_path):
         assert got[(name, "size")] == ctypes.sizeof(cls), name
         for field, _ in cls._fields_:
             assert got[(name, field)] == getattr(cls, field).offset, (name, field)
+
+
+PLUMBING = {"ac_destroy", "ac_error_string", "ac_last_error_detail", "ac_chunked_free", "ac_get_stats",
+            "ac_get_sizes", "ac_chunked_info", "ac_chunked_simplices"}
+
+
+def test_every_entry_point_cites_its_passage_and_errors():
+    """Each declaration of the method's calls cites the paper (a Section or Step), or says the paper
+    has none, and states its error behaviour."""
+    txt = open(HEADER).read()
+    seen = set()
+    for m in re.finditer(r"/\*((?:(?!\*/).)*)\*/\s*(AC_API[^;]*;)", txt, re.S):
+        com, decl = m.group(1), m.group(2)
+        name = re.search(r"\b(ac_\w+)\s*\(", decl).group(1)
+        seen.add(name)
+        if name in PLUMBING:
+            continue
+        assert re.search(r"Section|Step|paper has no counterpart|paper gives no", com), f"{name}: no citation"
+        assert re.search(r"Errors?:|errors", com), f"{name}: no error behaviour"
+    assert seen == set(_declared())
