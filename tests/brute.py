@@ -120,3 +120,98 @@ def brute_alpha_complex(P, R, A=None, delta_bits=160, with_source=False):
                 else:
                     out[k - 1][sigma] = (size, sigma not in witnessed)
     return out
+
+
+def _det3(m):
+    return (m[0][0] * (m[1][1] * m[2][2] - m[1][2] * m[2][1])
+            - m[0][1] * (m[1][0] * m[2][2] - m[1][2] * m[2][0])
+            + m[0][2] * (m[1][0] * m[2][1] - m[1][1] * m[2][0]))
+
+
+def witnessed_subsets(P, R, delta_bits=160):
+    """The same witnessed-at-orthocentre test as brute_alpha_complex, in scaled integers.
+
+    Every perturbed weight W_k + delta^(k+1) is multiplied by S = delta^-n, which
+    makes it an integer, and the orthocentre of the perturbed balls is kept as
+    num / (den * S) with integer num (Cramer's rule on the scaled equal-power
+    planes) and a small positive integer den. The power comparison against
+    every other ball is then an integer sign, with the loop stopping at the
+    first ball of smaller or equal power. Returns {tau: OrthoSize(tau)} for the
+    witnessed subsets, OrthoSize as an exact Fraction of the unperturbed balls.
+    """
+    n = len(P)
+    D = 1 << delta_bits
+    S = D ** n
+    W0 = [r * r for r in R]
+    Ws = [W0[k] * S + D ** (n - k - 1) for k in range(n)]  # S * (W_k + delta^(k+1))
+    sq = [_dot(p, p) for p in P]
+    out = {}
+    for k in range(1, 5):
+        for tau in combinations(range(n), k):
+            t0 = tau[0]
+            p0 = P[t0]
+            if k == 1:
+                den, num = 1, [p0[i] * S for i in range(3)]
+            elif k == 2:
+                q = _sub(P[tau[1]], p0)
+                qq = _dot(q, q)
+                if qq == 0:
+                    continue
+                # 2 q.c = rhs on the line c = p0 + t q
+                rhs = S * (sq[tau[1]] - sq[t0]) - Ws[tau[1]] + Ws[t0]
+                tn = rhs - 2 * S * _dot(q, p0)
+                den = 2 * qq
+                num = [p0[i] * den * S + tn * q[i] for i in range(3)]
+            else:
+                rows = [[2 * (P[j][i] - p0[i]) for i in range(3)] for j in tau[1:]]
+                rhs = [S * (sq[j] - sq[t0]) - Ws[j] + Ws[t0] for j in tau[1:]]
+                if k == 3:
+                    nrm = _cross(_sub(P[tau[1]], p0), _sub(P[tau[2]], p0))
+                    rows.append(nrm)
+                    rhs.append(S * _dot(nrm, p0))
+                den = _det3(rows)
+                if den == 0:
+                    continue
+                num = []
+                for i in range(3):
+                    m = [row[:] for row in rows]
+                    for r_ in range(3):
+                        m[r_][i] = rhs[r_]
+                    num.append(_det3(m))
+            if den < 0:
+                den, num = -den, [-v for v in num]
+            # (pi(c, x) - pi(c, t0)) * den * S with c = num / (den * S)
+            ok = True
+            for x in range(n):
+                if x in tau:
+                    continue
+                dx = _sub(P[x], p0)
+                if -2 * _dot(num, dx) + den * (S * (sq[x] - sq[t0]) - Ws[x] + Ws[t0]) <= 0:
+                    ok = False
+                    break
+            if ok:
+                c0 = orthocentre(P, [Fraction(w) for w in W0], tau)
+                out[tau] = power(c0, P, [Fraction(w) for w in W0], t0)
+    return out
+
+
+def alpha_complexes_from_witnessed(witnessed, alphas):
+    """K_alpha for each alpha of `alphas` (None = infinity), in brute_alpha_complex's format.
+
+    Size(sigma) is the smallest OrthoSize over the witnessed supersets of sigma,
+    gathered by visiting the (at most 15) non-empty subsets of each witnessed tau.
+    """
+    size = {}
+    for tau, v in witnessed.items():
+        for k in range(1, len(tau) + 1):
+            for sigma in combinations(tau, k):
+                if sigma not in size or v < size[sigma]:
+                    size[sigma] = v
+    res = []
+    for A in alphas:
+        out = {0: {}, 1: {}, 2: {}, 3: {}}
+        for sigma, s in size.items():
+            if A is None or s <= A:
+                out[len(sigma) - 1][sigma] = (s, sigma not in witnessed)
+        res.append(out)
+    return res
