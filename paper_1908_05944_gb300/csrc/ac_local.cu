@@ -90,9 +90,7 @@ struct WarpSmem {
     using Pair = typename std::conditional<(WORDS > 8), unsigned, unsigned short>::type;
     float4 qf[M];   // (qx, qy, qz, a_x): coordinates exact, a_x rounded once
     int ai[M];      // a_x exact
-    int s[M];       // W_x + A
     float rs[M];    // sqrt(W_x + A) rounded up
-    int gid[M];     // input index
     int idx[M];     // sorted position
     unsigned Mrow[M][WORDS];
     unsigned Trow[M][WORDS];
@@ -241,7 +239,7 @@ __device__ __forceinline__ int nth_set_bit(unsigned m, int r) {
 }
 
 template <class T>
-__device__ void stage_flush(const int lane, T* stage, int* n_stage, T* out, unsigned long long* counter, int64_t cap,
+__device__ __forceinline__ void stage_flush(const int lane, T* stage, int* n_stage, T* out, unsigned long long* counter, int64_t cap,
                             unsigned* err, unsigned bit) {
     __syncwarp();
     const int cnt = *n_stage;
@@ -258,12 +256,9 @@ __device__ void stage_flush(const int lane, T* stage, int* n_stage, T* out, unsi
     __syncwarp();
 }
 
-// warp-aggregated append of the lanes with want set
 template <class T>
-__device__ __forceinline__ void append_direct(bool want, const T& item, T* out, unsigned long long* counter, int64_t cap,
-                                              unsigned* err, unsigned bit) {
-    unsigned b = __ballot_sync(FULL, want);
-    if (b == 0) return;
+__device__ __forceinline__ void append_lanes(unsigned b, bool want, T item, T* out, unsigned long long* counter,
+                                          int64_t cap, unsigned* err, unsigned bit) {
     const int lane = threadIdx.x & 31;
     const int leader = __ffs(b) - 1;
     unsigned long long base = 0;
@@ -276,18 +271,23 @@ __device__ __forceinline__ void append_direct(bool want, const T& item, T* out, 
     }
 }
 
+// warp-aggregated append of the lanes with want set
+template <class T>
+__device__ __forceinline__ void append_direct(bool want, const T& item, T* out, unsigned long long* counter, int64_t cap,
+                                              unsigned* err, unsigned bit) {
+    const unsigned b = __ballot_sync(FULL, want);
+    if (b != 0u) append_lanes(b, want, item, out, counter, cap, err, bit);
+}
+
 // Staged append: items gather in shared memory and leave in runs of up to
-// STAGE; a warp step with more than STAGE items appends them directly.
+// STAGE (one warp step adds at most 32 = STAGE items).
+static_assert(STAGE >= 32, "a warp step must fit the staging buffer");
 template <class T>
 __device__ __forceinline__ void stage_push(const int lane, bool want, const T& item, T* stage, int* n_stage, T* out,
                                            unsigned long long* counter, int64_t cap, unsigned* err, unsigned bit) {
     unsigned b = __ballot_sync(FULL, want);
     if (b == 0) return;
     const int k = __popc(b);
-    if (k > STAGE) {
-        append_direct(want, item, out, counter, cap, err, bit);
-        return;
-    }
     if (*n_stage + k > STAGE) stage_flush(lane, stage, n_stage, out, counter, cap, err, bit);
     const int cur = *n_stage;
     if (want) stage[cur + __popc(b & lanemask_lt())] = item;
@@ -492,7 +492,7 @@ __device__ __forceinline__ int ac2_scan(const WarpSmem<WORDS>& S, int nw, const 
 
 // ---------------------------------------------------------------------------
 
-template <int WORDS, class R>
+template <int WORDS, class R, bool KEEP>
 __global__ void __launch_bounds__(256, 4) k_local(LocalArgs A) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     using SM = WarpSmem<WORDS>;
@@ -503,7 +503,7 @@ __global__ void __launch_bounds__(256, 4) k_local(LocalArgs A) {
     SM& S = reinterpret_cast<SM*>(smem_raw)[wib];
     DevCounters* cnt = A.cnt;
     const long long Aq = A.pc.A;
-    const bool keep = A.pc.keep_candidates != 0;
+    constexpr bool keep = KEEP;  // A.pc.keep_candidates
     const Bounds<R>& B = *reinterpret_cast<const Bounds<R>*>(is32 ? (const void*)&A.b32 : (const void*)&A.b64);
     unsigned n_tet = 0, n_tri = 0, n_edge = 0, n_ac3e = 0, n_ac3t = 0, n_ac3k = 0, n_s1 = 0, n_s2 = 0, n_s3 = 0;
     if (lane == 0) {
@@ -591,10 +591,8 @@ __global__ void __launch_bounds__(256, 4) k_local(LocalArgs A) {
                 const int ax = D - o.w + Wi;
                 S.qf[e] = make_float4((float)qx, (float)qy, (float)qz, (float)ax);
                 S.ai[e] = ax;
-                S.s[e] = (int)((long long)o.w + Aq);
                 S.rs[e] = __fsqrt_ru((float)((long long)o.w + Aq));  // W + A <= 2^24: exact in FP32
                 const int gx = A.order[x];
-                S.gid[e] = gx;
                 S.idx[e] = x;
                 // Delta_x = a_x at p_i; a tie goes against the larger input index
                 if (ax < 0 || (ax == 0 && gx < gi)) vert_bad = 1;
@@ -1294,9 +1292,10 @@ static int launch_local(ac_ctx* c, const LocalArgs& a, int64_t max_items, int wa
     if (warps > 8) warps = 8;  // __launch_bounds__(256)
     while (warps > 1 && (size_t)warps * sizeof(WarpSmem<WORDS>) > 200 * 1024) warps--;
     const size_t smem = (size_t)warps * sizeof(WarpSmem<WORDS>);
-    AC_CUDA(cudaFuncSetAttribute(k_local<WORDS, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    void (*kern)(LocalArgs) = a.pc.keep_candidates ? k_local<WORDS, R, true> : k_local<WORDS, R, false>;
+    AC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0, dev = 0, sms = 0;
-    AC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_local<WORDS, R>, warps * 32, smem));
+    AC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, warps * 32, smem));
     AC_CUDA(cudaGetDevice(&dev));
     AC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     if (per_sm < 1) return fail(AC_ERR_CUDA, "per-atom kernel does not fit on an SM");
@@ -1304,7 +1303,7 @@ static int launch_local(ac_ctx* c, const LocalArgs& a, int64_t max_items, int wa
     int64_t need = (max_items + warps - 1) / warps;
     if (blocks > need) blocks = need;
     if (blocks < 1) blocks = 1;
-    k_local<WORDS, R><<<(unsigned)blocks, warps * 32, smem, s>>>(a);
+    kern<<<(unsigned)blocks, warps * 32, smem, s>>>(a);
     AC_LAUNCHED();
     c->local_launches++;
     return AC_OK;
