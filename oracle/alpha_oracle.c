@@ -383,15 +383,18 @@ static int cmp_i32(const void *a, const void *b) {
     return x < y ? -1 : (x > y);
 }
 
-/* tuple width for qsort_cmp; only the (single-threaded) sort_unique sets it */
-static int g_sort_k;
-static int qsort_cmp(const void *a, const void *b) { return cmp_tuple((const int32_t *)a, (const int32_t *)b, g_sort_k); }
+/* one comparator per tuple width (no shared state: concurrent oracle runs
+   on several host threads each sort their own lists) */
+static int qsort_cmp1(const void *a, const void *b) { return cmp_tuple((const int32_t *)a, (const int32_t *)b, 1); }
+static int qsort_cmp2(const void *a, const void *b) { return cmp_tuple((const int32_t *)a, (const int32_t *)b, 2); }
+static int qsort_cmp3(const void *a, const void *b) { return cmp_tuple((const int32_t *)a, (const int32_t *)b, 3); }
+static int qsort_cmp4(const void *a, const void *b) { return cmp_tuple((const int32_t *)a, (const int32_t *)b, 4); }
 
-/* sort + unique in place; tuples have k entries */
+/* sort + unique in place; tuples have k (1..4) entries */
 static int64_t sort_unique(int32_t *v, int64_t n, int k) {
     if (n == 0) return 0;
-    g_sort_k = k;
-    qsort(v, (size_t)n, (size_t)k * sizeof(int32_t), qsort_cmp);
+    int (*cmp)(const void *, const void *) = k == 1 ? qsort_cmp1 : k == 2 ? qsort_cmp2 : k == 3 ? qsort_cmp3 : qsort_cmp4;
+    qsort(v, (size_t)n, (size_t)k * sizeof(int32_t), cmp);
     int64_t m = 1;
     for (int64_t i = 1; i < n; i++)
         if (cmp_tuple(v + (i - 1) * k, v + i * k, k) != 0) {

@@ -82,3 +82,21 @@ def test_threads_do_not_change_result(globule2k):
     for d in range(4):
         assert np.array_equal(ac.simplices[d], ac1.simplices[d])
         assert np.array_equal(ac.f[d], ac1.f[d])
+
+
+def test_concurrent_runs_equal_sequential_runs():
+    # the oracle keeps no shared state: runs on several host threads at once (as the full-size
+    # batch parity test makes them) give the lists and values of runs made one at a time
+    from concurrent.futures import ThreadPoolExecutor
+
+    mols = [synth.globule(1000 + m, 600 + 41 * m, probe=True) for m in range(16)]
+    seq = [oracle.alpha_complex(c, r, 0.0, threads=2) for c, r in mols]
+
+    def same(m):
+        got = oracle.alpha_complex(*mols[m], 0.0, threads=2)
+        return all(np.array_equal(got.simplices[d], seq[m].simplices[d]) and np.array_equal(got.f[d], seq[m].f[d])
+                   and np.array_equal(got.attached[d], seq[m].attached[d]) for d in range(4))
+
+    for _ in range(2):
+        with ThreadPoolExecutor(8) as ex:
+            assert all(ex.map(same, range(len(mols))))
