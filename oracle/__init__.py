@@ -77,9 +77,14 @@ def default_threads() -> int:
 
 
 class AlphaComplex:
-    """Result of one oracle run. ``simplices[d]`` is an int32 array (count, d+1)."""
+    """Result of one oracle run. ``simplices[d]`` is an int32 array (count, d+1).
 
-    def __init__(self, handle, n: int, lib):
+    ``candidates[d]`` holds Sigma_ortho^d unless the run was made with
+    candidates=False (then it is empty: the lists stay in the C result, which
+    saves host memory at millions of atoms).
+    """
+
+    def __init__(self, handle, n: int, lib, with_candidates: bool = True):
         self._h = handle
         self.n = n
         self._lib = lib
@@ -96,7 +101,7 @@ class AlphaComplex:
             if m:
                 lib.oracle_copy_simplices(handle, 0, d, s.ctypes.data)
             self.simplices.append(s)
-            c = lib.oracle_count(handle, 1, d)
+            c = lib.oracle_count(handle, 1, d) if with_candidates else 0
             cs = np.zeros((c, d + 1), dtype=np.int32)
             if c:
                 lib.oracle_copy_simplices(handle, 1, d, cs.ctypes.data)
@@ -144,10 +149,11 @@ class AlphaComplex:
 
 
 def alpha_complex(centres, radii, alpha: float = 0.0, alpha_inf: bool = False, threads: int | None = None,
-                  lib_path: str | None = None):
+                  lib_path: str | None = None, candidates: bool = True):
     """Run the exact oracle. centres (n,3) and radii (n,) in A; alpha in A^2.
 
     lib_path selects another build of the oracle source (the mutation test uses it).
+    candidates=False leaves the Sigma_ortho lists out of the returned object.
     """
     lib = _load() if lib_path is None else _open(lib_path)
     c = np.ascontiguousarray(centres, dtype=np.float64).reshape(-1, 3)
@@ -159,4 +165,4 @@ def alpha_complex(centres, radii, alpha: float = 0.0, alpha_inf: bool = False, t
                         threads or default_threads(), ctypes.byref(h))
     if rc != 0:
         raise OracleError(rc)
-    return AlphaComplex(h, len(r), lib)
+    return AlphaComplex(h, len(r), lib, with_candidates=candidates)

@@ -37,3 +37,27 @@ def assert_values(got, want, what=""):
     if rel.size:
         worst = int(np.argmax(rel))
         assert rel[worst] <= F_RTOL, f"{what}: relative error {rel[worst]:.3e} at {worst}"
+
+
+def host_lists(gpu, mol=-1):
+    """Rows, attached flags and filtration values of every dimension, copied to host memory."""
+    return [(gpu.simplices(d, mol, copy=False).cpu().numpy(), gpu.attached(d, mol, copy=False).cpu().numpy().astype(bool),
+             gpu.filtration_values(d, mol, copy=False).cpu().numpy()) for d in range(4)]
+
+
+def lists_differ(lists, ref):
+    """None if host lists (from host_lists) equal the oracle's complex, else what differs first."""
+    for d, (rows, att, f) in enumerate(lists):
+        want = ref.simplices[d]
+        if rows.shape != want.shape:
+            return f"dim {d}: {rows.shape[0]} simplices on the GPU, {want.shape[0]} in the oracle"
+        if not np.array_equal(rows, want):
+            bad = np.nonzero(np.any(rows != want, axis=1))[0][:3]
+            return f"dim {d}: rows {bad} differ: gpu {rows[bad].tolist()} oracle {want[bad].tolist()}"
+        if not np.array_equal(att, ref.attached[d]):
+            return f"dim {d}: attached flags differ"
+        try:
+            assert_values(f, ref.f[d], f"dim {d}")
+        except AssertionError as e:
+            return str(e)
+    return None
