@@ -140,7 +140,17 @@ AC_API int ac_create_batch(const double* centres, const double* radii, const int
  * as a CUDA graph, with every size the first build read checked on the device;
  * a mismatch (not expected: the computation is deterministic) makes that call
  * fall back to a synchronised build. Results are identical either way.
- * Errors: AC_ERR_DEGENERATE, AC_ERR_CAPACITY, AC_ERR_OOM, AC_ERR_CUDA.
+ * Errors: AC_ERR_DEGENERATE, AC_ERR_CAPACITY, AC_ERR_OOM, AC_ERR_CUDA,
+ * AC_ERR_TIMEOUT: a bounded device-side wait ran out. Scans of more than 4 M
+ * elements (list offsets) are single-pass, each tile waiting for the sums of
+ * the tiles before it; a tile polls one flag at most 2^24 times, or the
+ * number the environment variable ALPHAC_SCAN_SPIN_LIMIT gives when the scan
+ * is launched (a negative value makes every tile stop waiting once, to test
+ * this path). A tile whose wait runs out adds the missing sum from the
+ * inputs itself, so every offset, and every list built from them, is still
+ * exact and the context stays usable; the call reports AC_ERR_TIMEOUT all the
+ * same (a wait of that length means something else is holding the GPU), and
+ * the next ac_build on the context starts afresh.
  */
 AC_API int ac_build(ac_ctx* ctx, void* stream);
 
@@ -193,6 +203,20 @@ AC_API int ac_eval_filtration(ac_ctx* ctx, const double* d_centres, const double
                        void* stream);
 
 /*
+ * The filtration values of the last build evaluated in FP32 arithmetic, as a
+ * measure of the error single precision would make (the build itself takes
+ * every value from the exact rational, rounded to FP64). Each simplex takes
+ * its source's OrthoSize (the same source as ac_filtration_values), computed
+ * in single precision from the quantised centres and radii (exact in FP32):
+ * offsets, Gram matrix, its solve and the squared orthoradius, every
+ * operation rounded to FP32 (Section 2.3 definitions). d_f_out[dim]: device,
+ * caller-owned, one float per simplex of dim in list order (NULL skips it).
+ * Returns after the device work is finished. Errors: AC_ERR_INVALID_ARG
+ * (NULL), AC_ERR_STATE (no build), AC_ERR_CUDA.
+ */
+AC_API int ac_eval_filtration_fp32(ac_ctx* ctx, float* const d_f_out[4], void* stream);
+
+/*
  * Gradient of L = sum_dim sum_s dLdf[dim][s] * f[dim][s] with respect to the
  * centres and radii, combinatorics fixed (FP64). With lambda the barycentric
  * coordinates of the source's orthocentre c in its affine hull:
@@ -202,8 +226,12 @@ AC_API int ac_eval_filtration(ac_ctx* ctx, const double* d_centres, const double
  * The paper gives no gradient: this is the derivative of the Size of Section
  * 2.3, taken through the source simplex's OrthoSize with the source held fixed
  * (an envelope argument: the multipliers of the equal-power constraints are
- * the barycentric coordinates of c). Errors: AC_ERR_INVALID_ARG (NULL),
- * AC_ERR_STATE (no build), AC_ERR_OOM, AC_ERR_CUDA.
+ * the barycentric coordinates of c). Every sum is taken in a fixed order (per
+ * source simplex, then per atom; no floating-point atomics), so repeated calls
+ * give bit-identical gradients. Scratch: one double per simplex, allocated by
+ * the context on first use. Returns after the device work is finished.
+ * Errors: AC_ERR_INVALID_ARG (NULL), AC_ERR_STATE (no build), AC_ERR_OOM,
+ * AC_ERR_CUDA.
  */
 AC_API int ac_backward(ac_ctx* ctx, const double* const d_dLdf[4], double* d_dLdcentres, double* d_dLdradii,
                 void* stream);
@@ -212,14 +240,18 @@ AC_API int ac_backward(ac_ctx* ctx, const double* const d_dLdf[4], double* d_dLd
  * ac_backward without any device allocation. The paper has no counterpart:
  * this serves callers that cannot allocate device memory (a training step
  * whose memory belongs to another allocator, a service with a fixed device
- * memory budget). ac_backward allocates a small table of per-dimension list
- * pointers on its first call; here that table is a static device array of
- * 4 pointers (32 bytes, 256-byte aligned) that every GPU loading the library
- * holds until exit. Same arguments, results and errors as ac_backward
- * (AC_ERR_CAPACITY if a context had more lists than the table holds). The
- * first call on a device looks up the table's device address (with that
- * device current); make that first call before any stream capture. Every call
- * rewrites the whole table; calls that overlap on the GPU share it and race.
+ * memory budget). It runs the one-pass backward kernel (one thread per
+ * simplex, FP64 atomic adds into the outputs), whose only scratch is a table
+ * of the 4 per-dimension list pointers; here that table is a static device
+ * array (32 bytes, 256-byte aligned) that every GPU loading the library holds
+ * until exit. Same arguments and errors as ac_backward (AC_ERR_CAPACITY if a
+ * context had more lists than the table holds); the gradients agree with
+ * ac_backward's to rounding, the atomics adding in no fixed order. The first
+ * call on a device looks up the table's device address (with that device
+ * current) and keeps it for the process, so it is stale after a
+ * cudaDeviceReset; make that first call before any stream capture. Every call
+ * rewrites the whole table and synchronises the stream before returning;
+ * calls that overlap on the GPU share the table and race.
  */
 AC_API int ac_backward_noalloc(ac_ctx* ctx, const double* const d_dLdf[4], double* d_dLdcentres, double* d_dLdradii,
                                void* stream);
@@ -311,6 +343,54 @@ AC_API int ac_chunk_plan(const double* centres, const double* radii, int64_t n, 
  */
 AC_API int ac_build_chunked(const double* centres, const double* radii, int64_t n, double alpha,
                             const ac_options* opt, int64_t max_core_atoms, void* stream, ac_chunked** out);
+
+/*
+ * One molecule over several processes (Section 4.6: the grid split into
+ * parts, each processed with its border; here each part on its own GPU):
+ * ac_part_plan cuts the quantised z of the n HOST balls into n_parts ranges
+ * of about n / n_parts atoms each (host only, no GPU): thresholds (n_parts + 1
+ * int64, caller-owned) are in 1/1024 A, part p holding the atoms with
+ * thresholds[p] <= Z < thresholds[p + 1]; *reach is the halo, 2 sqrt(r_max^2 +
+ * alpha) in 1/1024 A (rounded up). Parts hold about equal numbers of atoms, or
+ * none when many atoms share one z. Errors: AC_ERR_INVALID_ARG (NULL, n < 0,
+ * n_parts < 1, non-finite input), AC_ERR_RANGE (as ac_create).
+ */
+AC_API int ac_part_plan(const double* centres, const double* radii, int64_t n, double alpha, int64_t n_parts,
+                        int64_t* thresholds, int64_t* reach);
+
+/*
+ * Part `part` of n_parts (the cut of ac_part_plan; Section 4.6, a part with
+ * its border) of the alpha complex of n HOST balls: every simplex whose first (smallest input index) vertex lies in
+ * the part, with its attached flag and filtration value, exactly as the whole
+ * molecule's build has them. Built like ac_build_chunked, restricted to the
+ * part: slabs of at most max_core_atoms atoms of the part, each with every
+ * atom within the halo (from all n). Every coface of such a simplex, and every
+ * ball that can violate AC2 at their orthocentres, has a grown ball meeting
+ * the first vertex's, so the halo holds them all; the shares of the parts are
+ * disjoint and together make the whole complex. The result (host lists, as
+ * ac_chunked_simplices reads them; free with ac_chunked_free) lists the rows
+ * in first-vertex order. Synchronous. Errors: those of ac_build_chunked,
+ * AC_ERR_INVALID_ARG (part outside [0, n_parts)). On error *out is NULL.
+ */
+AC_API int ac_build_part(const double* centres, const double* radii, int64_t n, double alpha, const ac_options* opt,
+                         int64_t n_parts, int64_t part, int64_t max_core_atoms, void* stream, ac_chunked** out);
+
+/*
+ * The whole complex from the shares of the parts (host only; Section 4.6
+ * concatenates the parts' results and removes duplicates, which first-vertex
+ * ownership makes unnecessary here): counts
+ * (n_parts x 4 int64, part-major) gives the rows of each part and dimension,
+ * tuples/f/attached (n_parts x 4 host pointers, the arrays ac_chunked_simplices
+ * gives for that part) the rows, values and flags. Each first vertex's rows
+ * come from one part, in order: they are placed at that vertex's place in the
+ * lexicographic order, with no search for duplicates. The result is read with
+ * ac_chunked_simplices and freed with ac_chunked_free. Errors:
+ * AC_ERR_INVALID_ARG (NULL, a negative count, a first vertex outside [0, n),
+ * two parts with rows of the same first vertex, a share out of order),
+ * AC_ERR_OOM. On error *out is NULL.
+ */
+AC_API int ac_merge_parts(int64_t n, int64_t n_parts, const int64_t* counts, const int32_t* const* tuples,
+                          const double* const* f, const uint8_t* const* attached, ac_chunked** out);
 
 /*
  * Host pointers to dimension dim of a chunked result: tuples (count, dim+1)

@@ -3,6 +3,7 @@
 // potential simplices and pruning (Sections 4.3-4.4, Steps 1-5 of Section 3.1),
 // then canonical lists and Size filtration values (Section 2.3).
 #include <math.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -137,7 +138,15 @@ __device__ T block_excl_scan(T v, T* total) {
 // from a counter in launch order, publish their sum, then add the sums (or the
 // inclusive prefix, once known) of the tiles before them. A tile only waits
 // on tiles that took an earlier index and are therefore running; the wait is
-// bounded all the same and sets DERR_TIMEOUT if it ever runs out.
+// bounded all the same. When it runs out (spin_limit polls of one tile's
+// flag), the tile sets DERR_TIMEOUT and sums that predecessor's inputs itself,
+// so the offsets stay exact and no later kernel writes where it should not:
+// a predecessor that has not published its sum has not written its outputs
+// either (it writes them after publishing), which is checked again after the
+// sum, so this holds for in-place scans too. The build still reports
+// AC_ERR_TIMEOUT, and the context stays usable.
+constexpr long long SCAN_SPIN_LIMIT = 1ll << 24;  // polls per flag: far beyond any real wait (microseconds)
+
 struct ScanState {
     unsigned next_tile;
     unsigned pad;
@@ -145,7 +154,8 @@ struct ScanState {
 
 template <class T>
 __global__ void __launch_bounds__(SCAN_THREADS) k_scan_lookback(const T* in, T* out, int64_t n, ScanState* st,
-                                                                 int* flags, T* agg, T* inc, unsigned* err) {
+                                                                 int* flags, T* agg, T* inc, unsigned* err,
+                                                                 long long spin_limit) {
     __shared__ int tile_s;
     __shared__ T prefix_s;
     __shared__ T total_s;
@@ -176,14 +186,26 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_lookback(const T* in, T* 
             vf[tile] = 1;
             int p = tile - 1;
             long long spins = 0;
+            bool force = spin_limit < 0;  // a negative limit: take the path below once, whatever the flag
             while (p >= 0) {
-                const int f = vf[p];
-                if (f == 0) {
-                    if (++spins > (1ll << 24)) {  // far beyond any real wait (microseconds): give up, flag it
-                        atomicOr(err, DERR_TIMEOUT);
-                        break;
+                int f = vf[p];
+                if (f == 0 || force) {
+                    if (!force && spins++ < spin_limit) continue;
+                    force = false;
+                    // the wait ran out: sum tile p's inputs here, then keep
+                    // that sum unless p has published in the meantime
+                    atomicOr(err, DERR_TIMEOUT);
+                    T own = 0;
+                    const int64_t b0 = (int64_t)p * SCAN_TILE;
+                    for (int64_t i = b0; i < b0 + SCAN_TILE && i < n; i++) own += __ldcg(in + i);
+                    __threadfence();
+                    f = vf[p];
+                    spins = 0;
+                    if (f == 0) {
+                        acc += own;
+                        p--;
+                        continue;
                     }
-                    continue;
                 }
                 __threadfence();
                 if (f == 2) {
@@ -191,6 +213,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_lookback(const T* in, T* 
                     break;
                 }
                 acc += *(volatile T*)&agg[p];
+                spins = 0;
                 p--;
             }
             inc[tile] = acc + total;
@@ -254,6 +277,18 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_tiles(const T* in, T* out
     }
 }
 
+// Polls of one flag before a look-back tile stops waiting: SCAN_SPIN_LIMIT, or
+// the value of the environment variable ALPHAC_SCAN_SPIN_LIMIT (read at every
+// launch): 0 stops at the first unpublished flag, and a negative value makes
+// every tile take that path once, for its nearest predecessor (a test of it).
+static long long scan_spin_limit() {
+    const char* e = getenv("ALPHAC_SCAN_SPIN_LIMIT");
+    if (!e || !*e) return SCAN_SPIN_LIMIT;
+    char* end = nullptr;
+    const long long v = strtoll(e, &end, 10);
+    return (end && *end == '\0') ? v : SCAN_SPIN_LIMIT;
+}
+
 template <class T>
 static int scan_entry(const T* in, T* out, int64_t n, DevBuf& tmp, DevCounters* dc, cudaStream_t s) {
     if (n <= 0) {
@@ -279,7 +314,8 @@ static int scan_entry(const T* in, T* out, int64_t n, DevBuf& tmp, DevCounters* 
     k_scan_lookback<T><<<(unsigned)tiles, SCAN_THREADS, 0, s>>>(in, out, n, reinterpret_cast<ScanState*>(b),
                                                                  reinterpret_cast<int*>(b + flags_off),
                                                                  reinterpret_cast<T*>(b + agg_off),
-                                                                 reinterpret_cast<T*>(b + inc_off), &dc->err);
+                                                                 reinterpret_cast<T*>(b + inc_off), &dc->err,
+                                                                 scan_spin_limit());
     AC_LAUNCHED();
     return AC_OK;
 }
@@ -1054,6 +1090,13 @@ extern "C" int ac_eval_filtration(ac_ctx* c, const double* d_centres, const doub
     if (!c->built) return fail(AC_ERR_STATE, "no successful ac_build on this context");
     StreamScope scope((cudaStream_t)stream);
     return eval_filtration(c, d_centres, d_radii, d_f_out, (cudaStream_t)stream);
+}
+
+extern "C" int ac_eval_filtration_fp32(ac_ctx* c, float* const d_f_out[4], void* stream) {
+    if (!c || !d_f_out) return fail(AC_ERR_INVALID_ARG, "bad argument");
+    if (!c->built) return fail(AC_ERR_STATE, "no successful ac_build on this context");
+    StreamScope scope((cudaStream_t)stream);
+    return eval_filtration_f32(c, d_f_out, (cudaStream_t)stream);
 }
 
 extern "C" int ac_backward(ac_ctx* c, const double* const d_dLdf[4], double* d_dLdcentres, double* d_dLdradii,
