@@ -12,6 +12,8 @@
 //   dOrthoSize/dp_k = 2 lambda_k (p_k - c),  dOrthoSize/dr_k = -2 r_k lambda_k.
 // The gradient is FP64 on the caller's continuous inputs; re-evaluated values
 // (for finite-difference checks) use double-double arithmetic.
+#include <string.h>
+
 #include <mutex>
 
 #include "ac_internal.cuh"
@@ -170,6 +172,79 @@ __device__ double orthosize_dd(const double* __restrict__ X, const double* __res
     return f.hi + f.lo;
 }
 
+// OrthoSize of K vertices in single precision throughout: offsets q_k =
+// p_k - p_0 and squared radii from the quantised atoms (exact in FP32), then
+// a_k, the Gram matrix, its solve and |y|^2 - w_0 rounded to FP32 at every
+// operation. Not used by the build: it measures what FP32 arithmetic would
+// do to the filtration values.
+__device__ float orthosize_f32(const int4* __restrict__ P, const int4& t, int K) {
+    const int v[4] = {t.x, t.y, t.z, t.w};
+    const int4 p0 = P[v[0]];
+    const float s = 1.0f / 1024.0f, s2 = 1.0f / 1048576.0f;
+    const float w0 = (float)p0.w * s2;
+    if (K == 1) return -w0;
+    float q[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}}, a[3] = {0.f, 0.f, 0.f};
+    for (int k = 1; k < K; k++) {
+        const int4 pk = P[v[k]];
+        q[k - 1][0] = (float)(pk.x - p0.x) * s;
+        q[k - 1][1] = (float)(pk.y - p0.y) * s;
+        q[k - 1][2] = (float)(pk.z - p0.z) * s;
+        a[k - 1] = q[k - 1][0] * q[k - 1][0] + q[k - 1][1] * q[k - 1][1] + q[k - 1][2] * q[k - 1][2] -
+                   (float)pk.w * s2 + w0;
+    }
+    const int d = K - 1;
+    float G[3][3];
+    for (int i = 0; i < d; i++)
+        for (int j = 0; j < d; j++) G[i][j] = q[i][0] * q[j][0] + q[i][1] * q[j][1] + q[i][2] * q[j][2];
+    float mu[3] = {0.f, 0.f, 0.f};
+    if (d == 1) {
+        mu[0] = a[0] / (2.0f * G[0][0]);
+    } else if (d == 2) {
+        const float det = G[0][0] * G[1][1] - G[0][1] * G[1][0];
+        mu[0] = (G[1][1] * a[0] - G[0][1] * a[1]) / (2.0f * det);
+        mu[1] = (G[0][0] * a[1] - G[1][0] * a[0]) / (2.0f * det);
+    } else {
+        float adj[3][3];
+        for (int i = 0; i < 3; i++)
+            for (int j = 0; j < 3; j++) {
+                const int r0 = (i + 1) % 3, r1 = (i + 2) % 3, c0 = (j + 1) % 3, c1 = (j + 2) % 3;
+                adj[j][i] = G[r0][c0] * G[r1][c1] - G[r0][c1] * G[r1][c0];
+            }
+        const float det = G[0][0] * adj[0][0] + G[0][1] * adj[1][0] + G[0][2] * adj[2][0];
+        for (int i = 0; i < 3; i++) mu[i] = (adj[i][0] * a[0] + adj[i][1] * a[1] + adj[i][2] * a[2]) / (2.0f * det);
+    }
+    float y[3] = {0.f, 0.f, 0.f};
+    for (int k = 0; k < d; k++)
+        for (int c = 0; c < 3; c++) y[c] += mu[k] * q[k][c];
+    return y[0] * y[0] + y[1] * y[1] + y[2] * y[2] - w0;
+}
+
+struct Rows4 {
+    const int4* G[4];
+};
+
+__global__ void k_eval_f32(const int4* __restrict__ P, const int8_t* __restrict__ sdim, const int64_t* __restrict__ sidx,
+                           int64_t m, Rows4 rows, float* __restrict__ out) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= m) return;
+    const int d = sdim[j];
+    out[j] = orthosize_f32(P, rows.G[d][sidx[j]], d + 1);
+}
+
+int eval_filtration_f32(ac_ctx* c, float* const f_out[4], cudaStream_t s) {
+    Rows4 rows;
+    for (int d = 0; d < 4; d++) rows.G[d] = c->Gbuf[d].as<int4>();
+    for (int d = 0; d < 4; d++) {
+        const int64_t m = c->K[d].count;
+        if (!f_out[d] || m == 0) continue;
+        k_eval_f32<<<(unsigned)((m + 127) / 128), 128, 0, s>>>(c->P.as<int4>(), c->K[d].src_dim.as<int8_t>(),
+                                                               c->K[d].src_idx.as<int64_t>(), m, rows, f_out[d]);
+        AC_LAUNCHED();
+    }
+    AC_CUDA(cudaStreamSynchronize(s));
+    return AC_OK;
+}
+
 __global__ void k_eval(const double* __restrict__ X, const double* __restrict__ R, const int8_t* __restrict__ sdim,
                        const int64_t* __restrict__ sidx, int64_t m, const int4* const* __restrict__ G,
                        double* __restrict__ out) {
@@ -221,37 +296,168 @@ int eval_filtration(ac_ctx* c, const double* centres, const double* radii, doubl
     return AC_OK;
 }
 
+// ---------------------------------------------------------------------------
+// ac_backward: the same gradient, with every sum taken in a fixed order, so
+// that repeated calls give bit-identical results (no floating-point atomics).
+//
+// Sum over the simplices sigma of w_sigma * dOrthoSize(src(sigma)): grouped by
+// source, each source s contributes W_s * dOrthoSize(s), W_s the sum of the
+// weights of the simplices whose source it is. Sources are unattached
+// simplices (witnessed at their own orthocentre), and a simplex whose source
+// is s is s itself or a face of s. So:
+//   1. k_source_weights, one thread per row of each list: W_s = w_s plus the
+//      weights of the faces of s whose source is s, faces visited in a fixed
+//      order and found in their first vertex's rows (0 for attached rows).
+//   2. k_backward_atoms, one thread per atom a: the sum over the unattached
+//      simplices s containing a of 2 W_s lambda_a(s) (p_a - c_s) and
+//      -2 W_s lambda_a(s) r_a, in a fixed order. Every vertex of a simplex of
+//      the complex has a grown ball meeting a's, so the first (smallest)
+//      vertex of s is a or one of a's neighbours with a smaller input index:
+//      their rows in every list, in neighbour-list order, are all the candidates.
+
+struct BackArgs {
+    const double* X;         // centres (n x 3), input order
+    const double* R;         // radii
+    const int4* G[4];        // rows per dimension, global input indices
+    const int64_t* v0[4];    // rows with first vertex g start at v0[d][g] (n + 1)
+    const int8_t* sdim[4];   // source of each row: dimension ...
+    const int64_t* sidx[4];  // ... and row
+    const uint8_t* att[4];   // attached flags
+    const double* w[4];      // dL/df per row (NULL: zero)
+    const double* W[4];      // per-row source weights (pass 1 output, pass 2 input)
+    int64_t rows[4];
+    const int32_t* rank;     // input index -> sorted position
+    const int32_t* order;    // sorted position -> input index
+    const int64_t* nb_off;   // neighbour rows (as in the per-atom pass)
+    const int32_t* nb;
+    int nb_stride;
+    int64_t n;
+};
+
+// row of the ascending tuple t (k entries) in list k - 1, or -1
+__device__ __forceinline__ int64_t find_row(const BackArgs& A, int k, const int* t) {
+    const int d = k - 1;
+    const int64_t lo = A.v0[d][t[0]], hi = A.v0[d][t[0] + 1];
+    for (int64_t r = lo; r < hi; r++) {
+        const int4 g = A.G[d][r];
+        if ((k < 2 || g.y == t[1]) && (k < 3 || g.z == t[2]) && (k < 4 || g.w == t[3])) return r;
+    }
+    return -1;
+}
+
+__global__ void k_source_weights(BackArgs A, int d, double* __restrict__ Wout) {
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= A.rows[d]) return;
+    double W = 0.0;
+    if (!A.att[d][r]) {
+        const int4 g = A.G[d][r];
+        const int v[4] = {g.x, g.y, g.z, g.w};
+        if (A.w[d] && A.sdim[d][r] == d && A.sidx[d][r] == r) W = A.w[d][r];
+        // proper faces, by decreasing dimension, each as the subset of v kept by a mask
+        for (int e = d - 1; e >= 0; e--) {
+            if (!A.w[e]) continue;
+            for (unsigned mask = 0; mask < (1u << (d + 1)); mask++) {
+                if (__popc(mask) != e + 1) continue;
+                int t[4] = {0, 0, 0, 0}, k = 0;
+                for (int j = 0; j <= d; j++)
+                    if (mask & (1u << j)) t[k++] = v[j];
+                const int64_t f = find_row(A, e + 1, t);
+                if (f >= 0 && A.sdim[e][f] == d && A.sidx[e][f] == r) W += A.w[e][f];
+            }
+        }
+    }
+    Wout[r] = W;
+}
+
+__global__ void k_backward_atoms(BackArgs A, double* __restrict__ dX, double* __restrict__ dR) {
+    const int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (a >= A.n) return;
+    const int ia = A.rank[a];
+    const int64_t off = A.nb_stride ? (int64_t)ia * A.nb_stride : A.nb_off[ia];
+    const int m = A.nb_stride ? (int)A.nb_off[ia] : (int)(A.nb_off[ia + 1] - off);
+    const double xa = A.X[3 * a], ya = A.X[3 * a + 1], za = A.X[3 * a + 2], ra = A.R[a];
+    double gx = 0.0, gy = 0.0, gz = 0.0, gr = 0.0;
+    for (int t = -1; t < m; t++) {
+        const int64_t b = t < 0 ? a : (int64_t)A.order[A.nb[off + t]];
+        if (t >= 0 && b >= a) continue;
+        for (int d = 0; d < 4; d++) {
+            for (int64_t r = A.v0[d][b]; r < A.v0[d][b + 1]; r++) {
+                const double W = A.W[d][r];
+                if (W == 0.0) continue;
+                const int4 g = A.G[d][r];
+                const int k = g.x == a ? 0 : (d >= 1 && g.y == a) ? 1 : (d >= 2 && g.z == a) ? 2 : (d >= 3 && g.w == a) ? 3 : -1;
+                if (k < 0) continue;
+                const Ortho o = ortho_fp64(A.X, A.R, g, d + 1);
+                const double l2 = 2.0 * W * o.lam[k];
+                gx += l2 * (xa - o.c[0]);
+                gy += l2 * (ya - o.c[1]);
+                gz += l2 * (za - o.c[2]);
+                gr -= l2 * ra;
+            }
+        }
+    }
+    dX[3 * a] = gx;
+    dX[3 * a + 1] = gy;
+    dX[3 * a + 2] = gz;
+    dR[a] = gr;
+}
+
 int backward(ac_ctx* c, const double* const dldf[4], double* dc, double* dr, cudaStream_t s) {
-    AC_TRY(gtable(c, c->scratch[5], s));
     const int64_t n = c->n;
-    AC_CUDA(cudaMemsetAsync(dc, 0, (size_t)(n > 0 ? n : 0) * 3 * sizeof(double), s));
-    AC_CUDA(cudaMemsetAsync(dr, 0, (size_t)(n > 0 ? n : 0) * sizeof(double), s));
+    if (n == 0) return AC_OK;
+    BackArgs A;
+    memset(&A, 0, sizeof(A));
+    A.X = c->centres.as<double>();
+    A.R = c->radii.as<double>();
+    size_t total = 0;
+    for (int d = 0; d < 4; d++) total += (size_t)c->K[d].count;
+    AC_TRY(c->scratch[3].reserve((total > 0 ? total : 1) * sizeof(double), s));
+    double* Wbuf = c->scratch[3].as<double>();
     for (int d = 0; d < 4; d++) {
-        const int64_t m = c->K[d].count;
-        if (!dldf[d] || m == 0) continue;
-        k_backward<<<(unsigned)((m + 127) / 128), 128, 0, s>>>(c->centres.as<double>(), c->radii.as<double>(),
-                                                               c->K[d].src_dim.as<int8_t>(), c->K[d].src_idx.as<int64_t>(),
-                                                               m, c->scratch[5].as<const int4*>(), dldf[d], dc, dr);
+        A.G[d] = c->Gbuf[d].as<int4>();
+        A.v0[d] = c->K[d].v0_off.as<int64_t>();
+        A.sdim[d] = c->K[d].src_dim.as<int8_t>();
+        A.sidx[d] = c->K[d].src_idx.as<int64_t>();
+        A.att[d] = c->K[d].attached.as<uint8_t>();
+        A.w[d] = c->K[d].count > 0 ? dldf[d] : nullptr;
+        A.W[d] = Wbuf;
+        A.rows[d] = c->K[d].count;
+        Wbuf += c->K[d].count;
+    }
+    A.rank = c->rank.as<int32_t>();
+    A.order = c->order.as<int32_t>();
+    A.nb_off = c->nb_cnt.as<int64_t>();
+    A.nb = c->nb.as<int32_t>();
+    A.nb_stride = c->nb_stride;
+    A.n = n;
+    for (int d = 0; d < 4; d++) {
+        const int64_t m = A.rows[d];
+        if (m == 0) continue;
+        k_source_weights<<<(unsigned)((m + 127) / 128), 128, 0, s>>>(A, d, const_cast<double*>(A.W[d]));
         AC_LAUNCHED();
     }
+    k_backward_atoms<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(A, dc, dr);
+    AC_LAUNCHED();
     AC_CUDA(cudaStreamSynchronize(s));
     return AC_OK;
 }
 
 // ---------------------------------------------------------------------------
-// ac_backward_noalloc: the same backward kernel without any device allocation.
+// ac_backward_noalloc: the gradient without any device allocation.
 //
-// ac_backward keeps the table of the four per-dimension source-list pointers
-// that k_backward reads in a context buffer it allocates on first use. Callers
-// that cannot allocate device memory (for example inside a training step
-// whose memory belongs to another allocator, or a service with a fixed device
-// memory budget) use this entry point instead: the table lives in the static
-// array below, which every GPU that loads the library holds until the process
-// exits. Maximum: NOALLOC_TABLE_ENTRIES = 4 pointers (one per dimension 0..3),
-// 32 bytes in a 256-byte-aligned array. Every call overwrites the whole table
-// before its kernels read it, so nothing in it has to start at zero; calls that
-// overlap on the GPU (other streams, other host threads) share the one table
-// and race.
+// ac_backward sums in a fixed order with per-simplex scratch it allocates.
+// Callers that cannot allocate device memory (for example inside a training
+// step whose memory belongs to another allocator, or a service with a fixed
+// device memory budget) use this entry point instead: it runs k_backward (one
+// thread per simplex, FP64 atomics), whose only scratch is the table of the
+// four per-dimension source-list pointers it reads, and that table lives in
+// the static array below, which every GPU that loads the library holds until
+// the process exits. Maximum: NOALLOC_TABLE_ENTRIES = 4 pointers (one per
+// dimension 0..3), 32 bytes in a 256-byte-aligned array. Every call overwrites
+// the whole table before its kernels read it, so nothing in it has to start at
+// zero; calls that overlap on the GPU (other streams, other host threads)
+// share the one table and race. The cached device address of the table does
+// not survive a cudaDeviceReset.
 constexpr int NOALLOC_TABLE_ENTRIES = 4;
 static __device__ __align__(256) const int4* g_noalloc_table[NOALLOC_TABLE_ENTRIES];
 

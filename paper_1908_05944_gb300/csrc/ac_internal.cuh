@@ -306,6 +306,7 @@ int run_local(ac_ctx* c, cudaStream_t s);
 int canonicalise(ac_ctx* c, cudaStream_t s);
 int compute_filtration(ac_ctx* c, cudaStream_t s);
 int eval_filtration(ac_ctx* c, const double* centres, const double* radii, double* const f_out[4], cudaStream_t s);
+int eval_filtration_f32(ac_ctx* c, float* const f_out[4], cudaStream_t s);
 int backward(ac_ctx* c, const double* const dldf[4], double* dc, double* dr, cudaStream_t s);
 int backward_noalloc(ac_ctx* c, const double* const dldf[4], double* dc, double* dr, cudaStream_t s);
 int subcomplex_flags(ac_ctx* c, int dim, int64_t first, int64_t m, double alpha2, uint8_t* flags, int64_t* count,

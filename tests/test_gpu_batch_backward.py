@@ -4,7 +4,8 @@
   and the oracle, molecule by molecule.
 * Backward (combinatorics fixed): against the oracle's closed-form gradient
   and against central differences of ac_eval_filtration (step 1e-6 A, 64
-  random coordinates, relative error <= 1e-6) on the 20,000-atom globule.
+  random centre coordinates and 64 random radii, relative error <= 1e-6) on
+  the 20,000-atom globule; repeated calls give bit-identical gradients.
 """
 import numpy as np
 import pytest
@@ -98,6 +99,55 @@ def test_backward_matches_finite_differences(globule20k):
             g += float(np.dot(w[d], diff))
         g /= 2 * h
         assert abs(g - dc[a, ax]) <= 1e-6 * max(abs(dc[a, ax]), 1e-3), (a, ax, g, dc[a, ax])
+
+
+def test_backward_radii_match_finite_differences(globule20k):
+    import torch
+
+    c, r, gpu, ref, w, wt = globule20k
+    _, dr = gpu.backward(wt)
+    dr = dr.cpu().numpy()
+    rng = np.random.default_rng(65)
+    h = 1e-6
+    ct = torch.from_numpy(c).cuda()
+    rt = torch.from_numpy(r).cuda()
+    for a in rng.choice(len(r), 64, replace=False):
+        rp = rt.clone()
+        rm = rt.clone()
+        rp[a] += h
+        rm[a] -= h
+        fp = gpu.eval_filtration(ct, rp)
+        fm = gpu.eval_filtration(ct, rm)
+        g = sum(float(np.dot(w[d], (fp[d] - fm[d]).cpu().numpy())) for d in range(4)) / (2 * h)
+        assert abs(g - dr[a]) <= 1e-6 * max(abs(dr[a]), 1e-3), (a, g, dr[a])
+
+
+def test_backward_is_deterministic(globule20k):
+    # sums in a fixed order (per source simplex, then per atom): bit-identical results, call after call
+    c, r, gpu, ref, w, wt = globule20k
+    dc0, dr0 = gpu.backward(wt)
+    for _ in range(3):
+        dc, dr = gpu.backward(wt)
+        assert np.array_equal(dc.cpu().numpy(), dc0.cpu().numpy())
+        assert np.array_equal(dr.cpu().numpy(), dr0.cpu().numpy())
+
+
+def test_fp32_values_close_to_fp64(globule20k):
+    # ac_eval_filtration_fp32: the same values in single precision (a measure, not part of the build)
+    c, r, gpu, ref, w, wt = globule20k
+    f32 = gpu.eval_filtration_fp32()
+    rel = []
+    for d in range(4):
+        want = gpu.filtration_values(d).cpu().numpy()
+        got = f32[d].cpu().numpy().astype(np.float64)
+        assert got.shape == want.shape and np.all(np.isfinite(got))
+        if d == 0:  # an unattached vertex is its own source: -r^2, exact in FP32
+            own = ~gpu.attached(0).cpu().numpy().astype(bool)
+            assert np.array_equal(got[own], want[own])
+        nz = want != 0.0
+        rel.append(np.abs(got[nz] - want[nz]) / np.abs(want[nz]))
+    rel = np.concatenate(rel)
+    assert np.median(rel) < 1e-5
 
 
 def test_eval_at_inputs_reproduces_values(globule20k):
