@@ -14,8 +14,12 @@ filtration values and attached flags delivered to page-locked host memory
 With --impl reference the exact CPU oracle (oracle/) is timed instead, on a
 bounded sub-ball of the same workload per step, on the host cores.
 
-Multi-GPU: independent replicas (the path has no exchange step); each rank
-builds its own copy; value = atoms of all ranks / max-over-ranks time.
+Multi-GPU: by default independent replicas (each rank builds its own copy;
+value = atoms of all ranks / max-over-ranks time, weak scaling). With
+--mode partitioned the ranks build the z-parts of one molecule from host
+arrays (ac_build_part: each part with its halo, Section 4.6) and rank 0
+gathers and merges the shares (ac_merge_parts); value = atoms of the molecule
+/ max-over-ranks time of a step (strong scaling; host in, host out).
 """
 from __future__ import annotations
 
@@ -60,7 +64,17 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-forms", action="store_true", help="skip the plain/shell side measurements")
+    p.add_argument("--mode", default="replicas", choices=["replicas", "partitioned"],
+                   help="replicas: every rank builds the whole workload (weak scaling); partitioned: the ranks "
+                        "build the parts of one molecule and rank 0 merges them (strong scaling)")
+    p.add_argument("--max-core-atoms", type=int, default=1 << 21, help="partitioned mode: atoms per slab of a part")
     return p.parse_args()
+
+
+def local_device():
+    """This rank's GPU: LOCAL_RANK, round-robin when ranks outnumber the GPUs (ranks then share one)."""
+    import torch
+    return int(os.environ.get("LOCAL_RANK", "0")) % max(1, torch.cuda.device_count())
 
 
 def dist_init(args):
@@ -69,9 +83,13 @@ def dist_init(args):
     if world > 1:
         import torch
         import torch.distributed as dist
-        backend = "nccl" if args.impl == "ours" else "gloo"
+        # the only collectives are a barrier and a max of one number: NCCL with one GPU per rank,
+        # gloo (host) when ranks share GPUs or for the reference arm
+        backend = "gloo"
         if args.impl == "ours":
-            torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+            torch.cuda.set_device(local_device())
+            if world <= torch.cuda.device_count():
+                backend = "nccl"
         dist.init_process_group(backend=backend)
     return rank, world
 
@@ -196,7 +214,7 @@ def run_ours(args, rank, world):
 
     import paper_1908_05944_gb300 as ac
 
-    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    dev = local_device()
     torch.cuda.set_device(dev)
     c_np, r_np = workload(args.workload)
     n = len(r_np)
@@ -454,6 +472,24 @@ def run_forms(args):
     t1.record(stream)
     torch.cuda.synchronize()
     bms = t0.elapsed_time(t1) / 5
+    # the filtration values in FP32 arithmetic against the build's (exact rationals rounded to FP64)
+    cg, rg = workload("globule100k_probe")
+    fx = ac.AlphaComplex(torch.from_numpy(cg).cuda(), torch.from_numpy(rg).cuda(), 0.0).build(stream)
+    f32 = fx.eval_filtration_fp32(stream)
+    rel, zeros = [], 0
+    for d in range(4):
+        want = fx.filtration_values(d).cpu().numpy()
+        got = f32[d].cpu().numpy().astype(np.float64)
+        nz = want != 0.0
+        zeros += int((~nz).sum())
+        rel.append(np.abs(got[nz] - want[nz]) / np.abs(want[nz]))
+    fx.close()
+    rel = np.concatenate(rel)
+    out["globule100k_probe/fp32_filtration_error"] = {
+        "rel_err_max": float(rel.max()), "rel_err_p50": float(np.median(rel)), "rel_err_p99": float(np.percentile(rel, 99)),
+        "values": int(rel.size), "exact_zeros_skipped": zeros,
+        "what": "each simplex's value (its source's OrthoSize) in FP32 arithmetic from the quantised inputs, "
+                "against the build's FP64 values (exact rationals rounded once)"}
     out["globule20k_probe/backward"] = {"ms_per_call": bms, "atoms_per_s": len(r20) / (bms / 1e3),
                                         "simplices": [gx.count(d) for d in range(4)]}
     gx.close()
@@ -493,19 +529,24 @@ def run_e2e(args, rank, world, steps):
     return {"value": n * world * steps / t, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
 
 
-def cpu_baseline(args, sample_atoms=20000):
+def cpu_baseline(args):
+    """The oracle, as it stands, on the whole workload (all host cores), and on the whole 2,000-atom
+    configuration; the GPU lists compared with it."""
     import oracle
-    import synth
 
     c, r = workload(args.workload)
-    sub_c, sub_r = sub_ball(c, r, sample_atoms)
     threads = os.cpu_count() or 1
     t0 = time.perf_counter()
-    res = oracle.alpha_complex(sub_c, sub_r, 0.0, threads=threads)
+    res = oracle.alpha_complex(c, r, 0.0, threads=threads, candidates=False)
     dt = time.perf_counter() - t0
-    return {"value": len(sub_r) / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": f"{len(sub_r)}-atom sub-ball of {args.workload} around its centre, 1 run, {dt:.2f} s",
-            "simplices": int(sum(res.counts())), "parity": parity_on(sub_c, sub_r, res)}
+    out = {"value": len(r) / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+           "sample": f"the whole {args.workload} ({len(r)} atoms), 1 run, {dt:.2f} s",
+           "simplices": int(sum(res.counts())), "parity": parity_on(c, r, res)}
+    c0, r0 = workload("globule2k_vdw")
+    t0 = time.perf_counter()
+    oracle.alpha_complex(c0, r0, 0.0, threads=threads, candidates=False)
+    out["globule2k_vdw"] = {"atoms_per_s": len(r0) / (time.perf_counter() - t0), "atoms": len(r0)}
+    return out
 
 
 def parity_on(c, r, ref):
@@ -573,9 +614,76 @@ def run_reference(args, rank, world):
     }
 
 
+def run_partitioned(args, rank, world):
+    """One molecule over the ranks: part build (host arrays in, host lists out), gather and merge on rank 0."""
+    import torch
+    import torch.distributed as dist
+
+    import paper_1908_05944_gb300 as ac
+
+    dev = local_device()
+    torch.cuda.set_device(dev)
+    c, r = workload(args.workload)
+    n = len(r)
+    group = dist.new_group(backend="gloo") if world > 1 else None  # the shares cross in host memory
+    stream = torch.cuda.current_stream()
+
+    def step():
+        part = ac.ChunkedComplex.part(c, r, 0.0, world, rank, args.max_core_atoms, stream=stream)
+        share = part.share()
+        part.close()
+        if world == 1:
+            return ac.merge_parts(n, [share])
+        got = [None] * world if rank == 0 else None
+        dist.gather_object(share, got, dst=0, group=group)
+        return ac.merge_parts(n, got) if rank == 0 else None
+
+    for _ in range(args.warmup):
+        m = step()
+        if m is not None:
+            m.close()
+    times = []
+    with ClockSampler(dev) as clk:
+        for _ in range(args.steps):
+            barrier(world)
+            t0 = time.perf_counter()
+            m = step()
+            barrier(world)
+            times.append(time.perf_counter() - t0)
+            counts = [m.count(d) for d in range(4)] if m is not None else None
+            if m is not None:
+                m.close()
+    total = max_over_ranks(float(sum(times)), world)
+    if rank != 0:
+        return None
+    value = n * args.steps / total
+    return {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": total / args.steps * 1e3, "higher_is_better": True, "scaling": "strong", "vs_baseline": None,
+        "dtype": "f32 filter, f64/int128 exact fallback", "data": "synthetic",
+        "config": {"workload": args.workload, "n_atoms": n, "alpha": 0.0, "parallelism": f"parts x{world}",
+                   "max_core_atoms": args.max_core_atoms, "l2": "inputs and lists in host memory (larger than L2)"},
+        "clocks": clk.summary(), "simplices": counts,
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": int(c.nbytes + r.nbytes),
+                "d2h_bytes_per_step": None},
+    }
+
+
 def main():
     args = parse()
     rank, world = dist_init(args)
+    if args.impl == "ours" and args.mode == "partitioned":
+        import importlib
+        if rank == 0:
+            importlib.import_module("paper_1908_05944_gb300.build").build()
+        barrier(world)
+        line = run_partitioned(args, rank, world)
+        if rank == 0:
+            print(json.dumps(line))
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return
     if args.impl == "reference":
         line = run_reference(args, rank, world)
         if rank == 0:

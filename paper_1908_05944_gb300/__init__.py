@@ -36,8 +36,9 @@ AC_FILTRATION_ORTHOSIZE = 1
 
 # every symbol include/alphac.h declares
 EXPORTS = ["ac_create", "ac_create_batch", "ac_build", "ac_get_simplices", "ac_filtration_values", "ac_attached_flags",
-           "ac_get_candidates", "ac_eval_filtration", "ac_backward", "ac_backward_noalloc", "ac_autotune",
-           "ac_subcomplex", "ac_get_simplices_host", "ac_chunk_plan", "ac_build_chunked", "ac_chunked_simplices", "ac_chunked_info",
+           "ac_get_candidates", "ac_eval_filtration", "ac_eval_filtration_fp32", "ac_backward", "ac_backward_noalloc", "ac_autotune",
+           "ac_subcomplex", "ac_get_simplices_host", "ac_chunk_plan", "ac_build_chunked", "ac_part_plan", "ac_build_part",
+           "ac_merge_parts", "ac_chunked_simplices", "ac_chunked_info",
            "ac_chunked_free", "ac_get_stats", "ac_get_sizes", "ac_destroy", "ac_error_string", "ac_last_error_detail"]
 
 
@@ -94,6 +95,7 @@ def _declare(lib):
     lib.ac_attached_flags.argtypes = [vp, i32, i64, P(vp), P(i64)]
     lib.ac_get_candidates.argtypes = [vp, i32, P(vp), P(i64)]
     lib.ac_eval_filtration.argtypes = [vp, vp, vp, vp, vp]
+    lib.ac_eval_filtration_fp32.argtypes = [vp, vp, vp]
     lib.ac_backward.argtypes = [vp, vp, vp, vp, vp]
     lib.ac_backward_noalloc.argtypes = [vp, vp, vp, vp, vp]
     lib.ac_autotune.argtypes = [vp, vp, P(ac_options)]
@@ -101,6 +103,9 @@ def _declare(lib):
     lib.ac_get_simplices_host.argtypes = [vp, i32, i64, P(vp), P(vp), P(vp), P(i64)]
     lib.ac_chunk_plan.argtypes = [vp, vp, i64, dbl, i64, vp, i64, P(i64), P(i64)]
     lib.ac_build_chunked.argtypes = [vp, vp, i64, dbl, P(ac_options), i64, vp, P(vp)]
+    lib.ac_part_plan.argtypes = [vp, vp, i64, dbl, i64, vp, P(i64)]
+    lib.ac_build_part.argtypes = [vp, vp, i64, dbl, P(ac_options), i64, i64, i64, vp, P(vp)]
+    lib.ac_merge_parts.argtypes = [i64, i64, vp, vp, vp, vp, P(vp)]
     lib.ac_chunked_simplices.argtypes = [vp, i32, P(vp), P(vp), P(vp), P(i64)]
     lib.ac_chunked_info.argtypes = [vp, P(ac_chunked_stats)]
     lib.ac_chunked_free.argtypes = [vp]
@@ -313,6 +318,15 @@ class AlphaComplex:
                                         _stream_ptr(stream)), "ac_eval_filtration")
         return outs
 
+    def eval_filtration_fp32(self, stream=None):
+        """The filtration values of the last build re-evaluated in FP32 arithmetic (CUDA float32 tensors)."""
+        import torch
+        outs = [torch.empty(self.count(d), dtype=torch.float32, device="cuda") for d in range(4)]
+        ptrs = (ctypes.c_void_p * 4)(*[o.data_ptr() if o.numel() else None for o in outs])
+        _check(lib().ac_eval_filtration_fp32(self._h, ctypes.cast(ptrs, ctypes.c_void_p), _stream_ptr(stream)),
+               "ac_eval_filtration_fp32")
+        return outs
+
     def backward(self, dldf, stream=None):
         """dL/dcentres (n,3) and dL/dradii (n,) for L = sum_d dldf[d] . f[d] (CUDA float64 tensors)."""
         import torch
@@ -375,21 +389,30 @@ def chunk_plan(centres, radii, alpha: float = 0.0, max_core_atoms: int = 1 << 21
     return thr[:k.value + 1] if n else thr[:0], reach.value
 
 
+def _host_balls(centres, radii):
+    c = _host_f64(centres)
+    r = _host_f64(radii)
+    n = int(r.shape[0])
+    if c.shape != (n, 3):
+        raise ValueError(f"centres must be ({n}, 3), got {c.shape}")
+    return c, r, n
+
+
 class ChunkedComplex:
     """ac_build_chunked: the alpha complex of host-resident balls, built slab by slab.
 
     Results are numpy arrays in host memory (copies), equal to what
-    AlphaComplex gives for the whole molecule.
+    AlphaComplex gives for the whole molecule. ChunkedComplex.part gives one
+    part's share (ac_build_part) and merge_parts joins shares (ac_merge_parts).
     """
 
     def __init__(self, centres, radii, alpha: float = 0.0, max_core_atoms: int = 1 << 21,
-                 opt: ac_options | None = None, stream=None):
+                 opt: ac_options | None = None, stream=None, _handle=None, _n=None):
         self._h = None
-        c = _host_f64(centres)
-        r = _host_f64(radii)
-        n = int(r.shape[0])
-        if c.shape != (n, 3):
-            raise ValueError(f"centres must be ({n}, 3), got {c.shape}")
+        if _handle is not None:
+            self._h, self.n, self.alpha = _handle, _n, alpha
+            return
+        c, r, n = _host_balls(centres, radii)
         o = opt if opt is not None else options()
         h = ctypes.c_void_p()
         _check(lib().ac_build_chunked(c.ctypes.data if n else None, r.ctypes.data if n else None, n, float(alpha),
@@ -398,6 +421,22 @@ class ChunkedComplex:
         self._h = h
         self.n = n
         self.alpha = alpha
+
+    @classmethod
+    def part(cls, centres, radii, alpha: float, n_parts: int, part: int, max_core_atoms: int = 1 << 21,
+             opt: ac_options | None = None, stream=None):
+        """ac_build_part: the rows whose first vertex lies in part `part` of n_parts z-ranges."""
+        c, r, n = _host_balls(centres, radii)
+        o = opt if opt is not None else options()
+        h = ctypes.c_void_p()
+        _check(lib().ac_build_part(c.ctypes.data if n else None, r.ctypes.data if n else None, n, float(alpha),
+                                   ctypes.byref(o), int(n_parts), int(part), int(max_core_atoms), _stream_ptr(stream),
+                                   ctypes.byref(h)), "ac_build_part")
+        return cls(None, None, alpha, _handle=h, _n=n)
+
+    def share(self):
+        """[(rows, filtration values, attached flags)] for dimensions 0..3, numpy copies."""
+        return [(self.simplices(d), self.filtration_values(d), self.attached(d)) for d in range(4)]
 
     def _get(self, dim):
         t, f, a = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p()
@@ -443,6 +482,66 @@ class ChunkedComplex:
             self.close()
         except Exception:
             pass
+
+
+def part_plan(centres, radii, alpha: float, n_parts: int):
+    """ac_part_plan (host only): z thresholds (n_parts + 1, in 1/1024 A) of the parts, and the halo reach."""
+    c, r, n = _host_balls(centres, radii)
+    thr = np.zeros(int(n_parts) + 1, dtype=np.int64)
+    reach = ctypes.c_int64()
+    _check(lib().ac_part_plan(c.ctypes.data if n else None, r.ctypes.data if n else None, n, float(alpha),
+                              int(n_parts), thr.ctypes.data, ctypes.byref(reach)), "ac_part_plan")
+    return thr, reach.value
+
+
+def merge_parts(n: int, shares, alpha: float = 0.0) -> ChunkedComplex:
+    """ac_merge_parts: the whole complex from the shares of all parts (each a ChunkedComplex.share())."""
+    k = len(shares)
+    arrs = []
+    counts = np.zeros((max(k, 1), 4), dtype=np.int64)
+    tp, fp, ap = (ctypes.c_void_p * (4 * max(k, 1)))(), (ctypes.c_void_p * (4 * max(k, 1)))(), \
+        (ctypes.c_void_p * (4 * max(k, 1)))()
+    for p, sh in enumerate(shares):
+        for d in range(4):
+            t = np.ascontiguousarray(sh[d][0], dtype=np.int32).reshape(-1, d + 1)
+            f = np.ascontiguousarray(sh[d][1], dtype=np.float64)
+            a = np.ascontiguousarray(sh[d][2], dtype=np.uint8)
+            if not (len(t) == len(f) == len(a)):
+                raise ValueError(f"share {p}, dimension {d}: rows, values and flags differ in length")
+            arrs += [t, f, a]
+            counts[p, d] = len(t)
+            tp[4 * p + d] = t.ctypes.data if len(t) else None
+            fp[4 * p + d] = f.ctypes.data if len(t) else None
+            ap[4 * p + d] = a.ctypes.data if len(t) else None
+    h = ctypes.c_void_p()
+    _check(lib().ac_merge_parts(int(n), k, counts.ctypes.data, ctypes.cast(tp, ctypes.c_void_p),
+                                ctypes.cast(fp, ctypes.c_void_p), ctypes.cast(ap, ctypes.c_void_p), ctypes.byref(h)),
+           "ac_merge_parts")
+    return ChunkedComplex(None, None, alpha, _handle=h, _n=int(n))
+
+
+def distributed_complex(centres, radii, alpha: float = 0.0, max_core_atoms: int = 1 << 21,
+                        opt: ac_options | None = None, stream=None, dst: int = 0, group=None):
+    """One molecule over the ranks of a torch.distributed process group (each rank on its own GPU).
+
+    Every rank passes the whole molecule (host arrays) and builds its part
+    (ac_build_part, part = rank of world size parts); the shares are gathered
+    on rank dst (torch.distributed.gather_object: host memory, any backend)
+    and merged there (ac_merge_parts). Returns the whole complex on dst, None
+    on the other ranks. There is no other exchange: the parts are disjoint.
+    """
+    import torch.distributed as dist
+
+    rank, world = dist.get_rank(group), dist.get_world_size(group)
+    mine = ChunkedComplex.part(centres, radii, alpha, world, rank, max_core_atoms, opt, stream)
+    share = mine.share()
+    mine.close()
+    got = [None] * world if rank == dst else None
+    dist.gather_object(share, got, dst=dst, group=group)
+    if rank != dst:
+        return None
+    n = int(_host_f64(radii).shape[0])
+    return merge_parts(n, got, alpha)
 
 
 def alpha_complex(centres, radii, alpha: float = 0.0, stream=None, **opt) -> AlphaComplex:

@@ -72,15 +72,16 @@ struct SlabPlan {
     std::vector<int64_t> thr;  // slab k: thr[k] <= Z < thr[k + 1]
     int64_t reach = 0;         // 2 h in quanta
     std::vector<int32_t> Z;    // quantised z of every atom
+    int64_t zmin = 0, zmax = -1;
 };
 
-// Quantised z, the largest weight and the slab cuts; the same input checks as
-// the device quantisation (so a chunked build fails where ac_create would).
-int plan_slabs(const double* centres, const double* radii, int64_t n, double alpha, int64_t max_core, SlabPlan& P) {
+// Quantised z and the largest weight of every atom, with the same input
+// checks as the device quantisation (so a chunked build fails where ac_create
+// would); the reach 2h follows.
+int quantise_z(const double* centres, const double* radii, int64_t n, double alpha, SlabPlan& P) {
     if (n < 0) return fail(AC_ERR_INVALID_ARG, "n < 0");
     if (n >= ((int64_t)1 << 31) - 1) return fail(AC_ERR_INVALID_ARG, "n out of range");
     if (n > 0 && (!centres || !radii)) return fail(AC_ERR_INVALID_ARG, "centres/radii NULL");
-    if (max_core < 1) return fail(AC_ERR_INVALID_ARG, "max_core_atoms < 1");
     if (!std::isfinite(alpha)) return fail(AC_ERR_INVALID_ARG, "alpha not finite");
     if (std::fabs(alpha) > 16.0) return fail(AC_ERR_RANGE, "|alpha| must be at most 16 A^2");
     P.Z.resize((size_t)n);
@@ -144,31 +145,92 @@ int plan_slabs(const double* centres, const double* radii, int64_t n, double alp
     }
     // two grown balls meet only if |dZ| <= sqrt(s_i) + sqrt(s_x) <= 2 sqrt(H2)
     P.reach = 2 * hq;
+    P.zmin = n > 0 ? zmin : 0;
+    P.zmax = n > 0 ? zmax : -1;
     P.thr.clear();
-    if (n == 0) return AC_OK;
-    // greedy cuts over a histogram of Z: bins of 2^shift quanta, at most 2^22 + 1 of them
-    const int64_t span = zmax - zmin;
+    return AC_OK;
+}
+
+// Histogram of the quantised z of the atoms with lo <= Z < hi: bins of
+// 2^shift quanta from lo, at most 2^22 + 1 of them.
+struct ZHist {
     int shift = 0;
-    while ((span >> shift) >= ((int64_t)1 << 22)) shift++;
-    const int64_t bins = (span >> shift) + 1;
-    std::vector<std::atomic<uint32_t>> hist((size_t)bins);
-    for (auto& h : hist) h.store(0, std::memory_order_relaxed);
-    parallel_ranges(n, T, [&](int, int64_t i0, int64_t i1) {
-        for (int64_t i = i0; i < i1; i++)
-            hist[(size_t)((P.Z[(size_t)i] - zmin) >> shift)].fetch_add(1, std::memory_order_relaxed);
+    int64_t lo = 0, bins = 0;
+    std::vector<std::atomic<uint32_t>> h;
+};
+
+void z_histogram(const SlabPlan& P, int64_t lo, int64_t hi, ZHist& H) {
+    const int64_t span = hi - 1 - lo;
+    H.shift = 0;
+    while ((span >> H.shift) >= ((int64_t)1 << 22)) H.shift++;
+    H.lo = lo;
+    H.bins = (span >> H.shift) + 1;
+    std::vector<std::atomic<uint32_t>> hist((size_t)H.bins);
+    for (auto& x : hist) x.store(0, std::memory_order_relaxed);
+    parallel_ranges((int64_t)P.Z.size(), host_threads(), [&](int, int64_t i0, int64_t i1) {
+        for (int64_t i = i0; i < i1; i++) {
+            const int64_t Z = P.Z[(size_t)i];
+            if (Z >= lo && Z < hi) hist[(size_t)((Z - lo) >> H.shift)].fetch_add(1, std::memory_order_relaxed);
+        }
     });
-    P.thr.push_back(zmin);
+    H.h.swap(hist);
+}
+
+// Greedy cuts of the atoms with lo <= Z < hi into slabs of at most max_core
+// atoms (more only when one bin holds more): P.thr, from the lowest to one past
+// the highest z in the range (empty when the range holds no atom).
+void cut_slabs(SlabPlan& P, int64_t lo, int64_t hi, int64_t max_core) {
+    P.thr.clear();
+    lo = std::max(lo, P.zmin);
+    hi = std::min(hi, P.zmax + 1);
+    if (lo >= hi) return;
+    ZHist H;
+    z_histogram(P, lo, hi, H);
+    int64_t first = -1, last = -1;
+    for (int64_t bi = 0; bi < H.bins; bi++)
+        if (H.h[(size_t)bi].load(std::memory_order_relaxed)) {
+            if (first < 0) first = bi;
+            last = bi;
+        }
+    if (first < 0) return;
+    P.thr.push_back(lo);
     int64_t run = 0;
-    for (int64_t bi = 0; bi < bins; bi++) {
-        const int64_t h = hist[(size_t)bi].load(std::memory_order_relaxed);
+    for (int64_t bi = first; bi <= last; bi++) {
+        const int64_t h = H.h[(size_t)bi].load(std::memory_order_relaxed);
         if (h == 0) continue;
         if (run > 0 && run + h > max_core) {
-            P.thr.push_back(zmin + (bi << shift));
+            P.thr.push_back(lo + (bi << H.shift));
             run = 0;
         }
         run += h;
     }
-    P.thr.push_back(zmax + 1);
+    P.thr.push_back(hi);
+}
+
+// n_parts ranges of z holding about n / n_parts atoms each (cuts at bin
+// boundaries of the histogram of all atoms: a part may hold more, or none,
+// when many atoms share one bin): thr[0] = zmin, thr[n_parts] = zmax + 1.
+void cut_parts(const SlabPlan& P, int64_t n_parts, std::vector<int64_t>& thr) {
+    const int64_t n = (int64_t)P.Z.size();
+    thr.assign((size_t)n_parts + 1, P.zmax + 1);
+    thr[0] = P.zmin;
+    if (n == 0) return;
+    ZHist H;
+    z_histogram(P, P.zmin, P.zmax + 1, H);
+    int64_t cum = 0, bi = 0;
+    for (int64_t k = 1; k < n_parts; k++) {
+        const int64_t target = (k * n + n_parts - 1) / n_parts;  // atoms below cut k
+        while (bi < H.bins && cum < target) cum += H.h[(size_t)bi++].load(std::memory_order_relaxed);
+        thr[(size_t)k] = std::max(thr[(size_t)k - 1], std::min(P.zmin + (bi << H.shift), P.zmax + 1));
+    }
+}
+
+// The slab cut of a whole molecule.
+int plan_slabs(const double* centres, const double* radii, int64_t n, double alpha, int64_t max_core, SlabPlan& P) {
+    if (n >= 0 && n < ((int64_t)1 << 31) - 1 && (n == 0 || (centres && radii)) && max_core < 1)
+        return fail(AC_ERR_INVALID_ARG, "max_core_atoms < 1");
+    AC_TRY(quantise_z(centres, radii, n, alpha, P));
+    if (n > 0) cut_slabs(P, P.zmin, P.zmax + 1, max_core);
     return AC_OK;
 }
 
@@ -318,20 +380,117 @@ extern "C" int ac_chunk_plan(const double* centres, const double* radii, int64_t
     return AC_OK;
 }
 
-extern "C" int ac_build_chunked(const double* centres, const double* radii, int64_t n, double alpha,
-                                const ac_options* opt, int64_t max_core_atoms, void* stream, ac_chunked** out) {
-    if (!out) return fail(AC_ERR_INVALID_ARG, "out is NULL");
-    *out = nullptr;
-    ac_options o{};
-    if (opt) o = *opt;
-    if (o.keep_candidates) return fail(AC_ERR_INVALID_ARG, "keep_candidates is not available in a chunked build");
-    cudaStream_t s = (cudaStream_t)stream;
-    StreamScope scope(s);
-    std::unique_ptr<ac_chunked> res(new (std::nothrow) ac_chunked());
-    if (!res) return fail(AC_ERR_OOM, "host allocation failed");
-    double t0 = now_ms();
-    SlabPlan P;
-    AC_TRY(plan_slabs(centres, radii, n, alpha, max_core_atoms, P));
+namespace ac {
+namespace {
+
+// One share of one list: rows (count, k) in first-vertex order, host memory.
+struct ShareView {
+    const int32_t* t;
+    const double* f;
+    const uint8_t* a;
+    int64_t rows;
+};
+
+// Placement: the rows of every first vertex come from one share, contiguous
+// and in order; the work is cut into pieces of whole runs of rows with the
+// same first vertex, many per share. Fails if two shares (or two runs of one
+// share) hold rows of the same first vertex, or a first vertex is outside
+// [0, n).
+int place(int64_t n, int d, const std::vector<ShareView>& shares, std::vector<int64_t>& off, ac_chunked* R) {
+    const int k = d + 1;
+    const int threads = host_threads();
+    struct Piece {
+        int64_t c, r0, r1;
+    };
+    std::vector<Piece> pieces;
+    int64_t rows_in = 0;
+    for (int64_t c = 0; c < (int64_t)shares.size(); c++) {
+        const ShareView& S = shares[(size_t)c];
+        rows_in += S.rows;
+        const int64_t rows = S.rows, per = std::max<int64_t>(8192, rows / (4 * threads) + 1);
+        for (int64_t r0 = 0; r0 < rows;) {
+            int64_t r1 = std::min(rows, r0 + per);
+            while (r1 < rows && S.t[(size_t)(r1 * k)] == S.t[(size_t)((r1 - 1) * k)]) r1++;
+            pieces.push_back({c, r0, r1});
+            r0 = r1;
+        }
+    }
+    off.assign((size_t)n + 1, 0);
+    std::atomic<int> bad{0};
+    // every share strictly increasing, row after row (lexicographic)
+    std::atomic<int> unordered{0};
+    parallel_for((int64_t)pieces.size(), threads, [&](int64_t pi) {
+        const Piece& q = pieces[(size_t)pi];
+        const int32_t* t = shares[(size_t)q.c].t;
+        for (int64_t r = std::max<int64_t>(q.r0, 1); r < q.r1; r++) {
+            const int32_t* x = t + (r - 1) * k;
+            const int32_t* y = t + r * k;
+            int j = 0;
+            while (j < k && x[j] == y[j]) j++;
+            if (j == k || x[j] > y[j]) {
+                unordered.store(1);
+                return;
+            }
+        }
+    });
+    if (unordered.load()) return fail(AC_ERR_INVALID_ARG, "a share's rows are not in lexicographic order");
+    auto runs = [&](const Piece& q, const std::function<void(int32_t, int64_t, int64_t)>& fn) {
+        const ShareView& S = shares[(size_t)q.c];
+        for (int64_t r = q.r0; r < q.r1;) {
+            const int32_t v = S.t[(size_t)(r * k)];
+            int64_t e = r + 1;
+            while (e < q.r1 && S.t[(size_t)(e * k)] == v) e++;
+            if (v < 0 || v >= n) bad.store(1);
+            else fn(v, r, e);
+            r = e;
+        }
+    };
+    parallel_for((int64_t)pieces.size(), threads, [&](int64_t pi) {
+        runs(pieces[(size_t)pi], [&](int32_t v, int64_t r, int64_t e) { off[(size_t)v + 1] = e - r; });
+    });
+    if (bad.load()) return fail(AC_ERR_INVALID_ARG, "a row's first vertex is outside [0, n)");
+    {
+        // inclusive prefix over off[1..n] in ranges: range sums, their prefix, then each range
+        std::vector<int64_t> part((size_t)threads + 1, 0);
+        parallel_ranges(n, threads, [&](int t, int64_t v0, int64_t v1) {
+            int64_t acc = 0;
+            for (int64_t v = v0; v < v1; v++) acc += off[(size_t)v + 1];
+            part[(size_t)t + 1] = acc;
+        });
+        for (int t = 0; t < threads; t++) part[(size_t)t + 1] += part[(size_t)t];
+        parallel_ranges(n, threads, [&](int t, int64_t v0, int64_t v1) {
+            int64_t acc = part[(size_t)t];
+            for (int64_t v = v0; v < v1; v++) {
+                acc += off[(size_t)v + 1];
+                off[(size_t)v + 1] = acc;
+            }
+        });
+    }
+    const int64_t total = n > 0 ? off[(size_t)n] : 0;
+    if (total != rows_in)
+        return fail(AC_ERR_INVALID_ARG, "two shares hold rows of the same first vertex (or a share is not in order)");
+    if (!R->t[d].reset(total * k) || !R->f[d].reset(total) || !R->a[d].reset(total))
+        return fail(AC_ERR_OOM, "host allocation of the result failed");
+    R->count[d] = total;
+    parallel_for((int64_t)pieces.size(), threads, [&](int64_t pi) {
+        const ShareView& S = shares[(size_t)pieces[(size_t)pi].c];
+        runs(pieces[(size_t)pi], [&](int32_t v, int64_t r, int64_t e) {
+            const int64_t p = off[(size_t)v];
+            std::copy(S.t + r * k, S.t + e * k, R->t[d].p.get() + p * k);
+            std::copy(S.f + r, S.f + e, R->f[d].p.get() + p);
+            std::copy(S.a + r, S.a + e, R->a[d].p.get() + p);
+        });
+    });
+    return AC_OK;
+}
+
+// The rows whose first vertex has lo <= Z < hi, built in slabs of at most
+// max_core atoms of that range (each with its halo, from all n atoms),
+// placed in first-vertex order into res (host). P holds Z and the reach.
+int build_range(const double* centres, const double* radii, int64_t n, double alpha, const ac_options& o,
+                int64_t max_core, SlabPlan& P, int64_t lo, int64_t hi, cudaStream_t s, ac_chunked* res) {
+    const double t0 = now_ms();
+    cut_slabs(P, lo, hi, max_core);
     const int64_t K = P.thr.empty() ? 0 : (int64_t)P.thr.size() - 1;
     // members of slab k (with halo): thr[k] - reach <= Z < thr[k+1] + reach, in input order;
     // T ranges of atoms counted apart, so each range writes its members in order
@@ -342,19 +501,20 @@ extern "C" int ac_build_chunked(const double* centres, const double* radii, int6
     };
     const int T = host_threads();
     std::vector<int64_t> tcnt((size_t)T * (size_t)K, 0), tcore((size_t)T * (size_t)K, 0);
-    parallel_ranges(n, T, [&](int t, int64_t i0, int64_t i1) {
-        int64_t* cnt = tcnt.data() + (size_t)t * K;
-        int64_t* core = tcore.data() + (size_t)t * K;
-        for (int64_t i = i0; i < i1; i++) {
-            const int64_t Z = P.Z[(size_t)i];
-            int64_t k0, k1;
-            range_of(Z, k0, k1);
-            for (int64_t k = k0; k <= k1; k++) {
-                cnt[k]++;
-                if (Z >= P.thr[(size_t)k] && Z < P.thr[(size_t)k + 1]) core[k]++;
+    if (K > 0)
+        parallel_ranges(n, T, [&](int t, int64_t i0, int64_t i1) {
+            int64_t* cnt = tcnt.data() + (size_t)t * K;
+            int64_t* core = tcore.data() + (size_t)t * K;
+            for (int64_t i = i0; i < i1; i++) {
+                const int64_t Z = P.Z[(size_t)i];
+                int64_t k0, k1;
+                range_of(Z, k0, k1);
+                for (int64_t k = k0; k <= k1; k++) {
+                    cnt[k]++;
+                    if (Z >= P.thr[(size_t)k] && Z < P.thr[(size_t)k + 1]) core[k]++;
+                }
             }
-        }
-    });
+        });
     std::vector<int64_t> moff((size_t)K + 1, 0);
     int64_t core_max = 0, sub_max = 0;
     for (int64_t k = 0; k < K; k++) {
@@ -370,15 +530,16 @@ extern "C" int ac_build_chunked(const double* centres, const double* radii, int6
         core_max = std::max(core_max, nc);
     }
     std::vector<int32_t> members((size_t)moff[(size_t)K]);
-    parallel_ranges(n, T, [&](int t, int64_t i0, int64_t i1) {
-        int64_t* cur = tcnt.data() + (size_t)t * K;
-        for (int64_t i = i0; i < i1; i++) {
-            int64_t k0, k1;
-            range_of(P.Z[(size_t)i], k0, k1);
-            for (int64_t k = k0; k <= k1; k++) members[(size_t)cur[k]++] = (int32_t)i;
-        }
-    });
-    double t1 = now_ms();
+    if (K > 0)
+        parallel_ranges(n, T, [&](int t, int64_t i0, int64_t i1) {
+            int64_t* cur = tcnt.data() + (size_t)t * K;
+            for (int64_t i = i0; i < i1; i++) {
+                int64_t k0, k1;
+                range_of(P.Z[(size_t)i], k0, k1);
+                for (int64_t k = k0; k <= k1; k++) members[(size_t)cur[k]++] = (int32_t)i;
+            }
+        });
+    const double t1 = now_ms();
 
     // pinned staging for one slab
     double *h_xyz = nullptr, *h_r = nullptr;
@@ -392,20 +553,19 @@ extern "C" int ac_build_chunked(const double* centres, const double* radii, int6
                 if (q) cudaFreeHost(q);
         }
     } pin;
-    const size_t sm = (size_t)std::max<int64_t>(sub_max, 1);
-    if (cudaMallocHost(&pin.p[0], sm * 3 * sizeof(double)) != cudaSuccess ||
-        cudaMallocHost(&pin.p[1], sm * sizeof(double)) != cudaSuccess ||
-        cudaMallocHost(&pin.p[2], sm * sizeof(int32_t)) != cudaSuccess || cudaMallocHost(&pin.p[3], sm) != cudaSuccess ||
-        cudaMallocHost(&pin.p[4], 4 * sizeof(int64_t)) != cudaSuccess)
-        return cuda_fail(cudaGetLastError(), "cudaMallocHost of the slab staging", __FILE__, __LINE__);
-    h_xyz = static_cast<double*>(pin.p[0]);
-    h_r = static_cast<double*>(pin.p[1]);
-    h_g = static_cast<int32_t*>(pin.p[2]);
-    h_core = static_cast<uint8_t*>(pin.p[3]);
-    h_cnt = static_cast<int64_t*>(pin.p[4]);
-
     std::vector<std::unique_ptr<Share[]>> shares((size_t)K);
-    {
+    if (K > 0) {
+        const size_t sm = (size_t)std::max<int64_t>(sub_max, 1);
+        if (cudaMallocHost(&pin.p[0], sm * 3 * sizeof(double)) != cudaSuccess ||
+            cudaMallocHost(&pin.p[1], sm * sizeof(double)) != cudaSuccess ||
+            cudaMallocHost(&pin.p[2], sm * sizeof(int32_t)) != cudaSuccess ||
+            cudaMallocHost(&pin.p[3], sm) != cudaSuccess || cudaMallocHost(&pin.p[4], 4 * sizeof(int64_t)) != cudaSuccess)
+            return cuda_fail(cudaGetLastError(), "cudaMallocHost of the slab staging", __FILE__, __LINE__);
+        h_xyz = static_cast<double*>(pin.p[0]);
+        h_r = static_cast<double*>(pin.p[1]);
+        h_g = static_cast<int32_t*>(pin.p[2]);
+        h_core = static_cast<uint8_t*>(pin.p[3]);
+        h_cnt = static_cast<int64_t*>(pin.p[4]);
         SlabBufs B;
         for (int64_t k = 0; k < K; k++) {
             shares[(size_t)k].reset(new (std::nothrow) Share[4]);
@@ -417,87 +577,113 @@ extern "C" int ac_build_chunked(const double* centres, const double* radii, int6
         }
         AC_CUDA(cudaStreamSynchronize(s));
     }
-    double t2 = now_ms();
-
-    // placement: all rows of a first vertex come from the one slab that holds it,
-    // contiguous and in order; the work is cut into pieces of whole runs of rows
-    // with the same first vertex, many per slab
-    const int threads = T;
-    std::vector<int64_t> off((size_t)n + 1);
-    struct Piece {
-        int64_t c, r0, r1;
-    };
+    const double t2 = now_ms();
+    std::vector<int64_t> off;
     for (int d = 0; d < 4; d++) {
-        const int k = d + 1;
-        std::vector<Piece> pieces;
+        std::vector<ShareView> views;
         for (int64_t c = 0; c < K; c++) {
             const Share& S = shares[(size_t)c][d];
-            const int64_t rows = S.f.n, per = std::max<int64_t>(8192, rows / (4 * threads) + 1);
-            for (int64_t r0 = 0; r0 < rows;) {
-                int64_t r1 = std::min(rows, r0 + per);
-                while (r1 < rows && S.t.p[(size_t)(r1 * k)] == S.t.p[(size_t)((r1 - 1) * k)]) r1++;
-                pieces.push_back({c, r0, r1});
-                r0 = r1;
-            }
+            views.push_back({S.t.p.get(), S.f.p.get(), S.a.p.get(), S.f.n});
         }
-        parallel_ranges(n + 1, threads, [&](int, int64_t v0, int64_t v1) {
-            std::fill(off.begin() + v0, off.begin() + v1, 0);
-        });
-        auto runs = [&](const Piece& q, const std::function<void(int32_t, int64_t, int64_t)>& fn) {
-            const Share& S = shares[(size_t)q.c][d];
-            for (int64_t r = q.r0; r < q.r1;) {
-                const int32_t v = S.t.p[(size_t)(r * k)];
-                int64_t e = r + 1;
-                while (e < q.r1 && S.t.p[(size_t)(e * k)] == v) e++;
-                fn(v, r, e);
-                r = e;
-            }
-        };
-        parallel_for((int64_t)pieces.size(), threads, [&](int64_t pi) {
-            runs(pieces[(size_t)pi], [&](int32_t v, int64_t r, int64_t e) { off[(size_t)v + 1] = e - r; });
-        });
-        {
-            // inclusive prefix over off[1..n] in ranges: range sums, their prefix, then each range
-            std::vector<int64_t> part((size_t)threads + 1, 0);
-            parallel_ranges(n, threads, [&](int t, int64_t v0, int64_t v1) {
-                int64_t acc = 0;
-                for (int64_t v = v0; v < v1; v++) acc += off[(size_t)v + 1];
-                part[(size_t)t + 1] = acc;
-            });
-            for (int t = 0; t < threads; t++) part[(size_t)t + 1] += part[(size_t)t];
-            parallel_ranges(n, threads, [&](int t, int64_t v0, int64_t v1) {
-                int64_t acc = part[(size_t)t];
-                for (int64_t v = v0; v < v1; v++) {
-                    acc += off[(size_t)v + 1];
-                    off[(size_t)v + 1] = acc;
-                }
-            });
-        }
-        const int64_t total = off[(size_t)n];
-        if (!res->t[d].reset(total * k) || !res->f[d].reset(total) || !res->a[d].reset(total))
-            return fail(AC_ERR_OOM, "host allocation of the result failed");
-        res->count[d] = total;
-        ac_chunked* R = res.get();
-        parallel_for((int64_t)pieces.size(), threads, [&](int64_t pi) {
-            const Share& S = shares[(size_t)pieces[(size_t)pi].c][d];
-            runs(pieces[(size_t)pi], [&](int32_t v, int64_t r, int64_t e) {
-                const int64_t p = off[(size_t)v];
-                std::copy(S.t.p.get() + r * k, S.t.p.get() + e * k, R->t[d].p.get() + p * k);
-                std::copy(S.f.p.get() + r, S.f.p.get() + e, R->f[d].p.get() + p);
-                std::copy(S.a.p.get() + r, S.a.p.get() + e, R->a[d].p.get() + p);
-            });
-        });
+        AC_TRY(place(n, d, views, off, res));
     }
-    double t3 = now_ms();
+    const double t3 = now_ms();
     ac_chunked_stats& st = res->st;
     st.n_chunks = K;
     st.reach = P.reach;
     st.core_max = core_max;
     st.subset_max = sub_max;
     st.subset_total = moff[(size_t)K];
-    st.ms_plan = t1 - t0;
+    st.ms_plan += t1 - t0;
     st.ms_device = t2 - t1;
     st.ms_assemble = t3 - t2;
+    return AC_OK;
+}
+
+}  // namespace
+}  // namespace ac
+
+extern "C" int ac_build_chunked(const double* centres, const double* radii, int64_t n, double alpha,
+                                const ac_options* opt, int64_t max_core_atoms, void* stream, ac_chunked** out) {
+    if (!out) return fail(AC_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    ac_options o{};
+    if (opt) o = *opt;
+    if (o.keep_candidates) return fail(AC_ERR_INVALID_ARG, "keep_candidates is not available in a chunked build");
+    cudaStream_t s = (cudaStream_t)stream;
+    StreamScope scope(s);
+    std::unique_ptr<ac_chunked> res(new (std::nothrow) ac_chunked());
+    if (!res) return fail(AC_ERR_OOM, "host allocation failed");
+    const double t0 = now_ms();
+    SlabPlan P;
+    AC_TRY(plan_slabs(centres, radii, n, alpha, max_core_atoms, P));
+    res->st.ms_plan = now_ms() - t0;
+    AC_TRY(build_range(centres, radii, n, alpha, o, max_core_atoms, P, P.zmin, P.zmax + 1, s, res.get()));
+    *out = res.release();
+    return AC_OK;
+}
+
+extern "C" int ac_part_plan(const double* centres, const double* radii, int64_t n, double alpha, int64_t n_parts,
+                            int64_t* thresholds, int64_t* reach) {
+    if (!thresholds || !reach) return fail(AC_ERR_INVALID_ARG, "NULL output");
+    if (n_parts < 1) return fail(AC_ERR_INVALID_ARG, "n_parts < 1");
+    SlabPlan P;
+    AC_TRY(quantise_z(centres, radii, n, alpha, P));
+    std::vector<int64_t> thr;
+    cut_parts(P, n_parts, thr);
+    std::copy(thr.begin(), thr.end(), thresholds);
+    *reach = P.reach;
+    return AC_OK;
+}
+
+extern "C" int ac_build_part(const double* centres, const double* radii, int64_t n, double alpha,
+                             const ac_options* opt, int64_t n_parts, int64_t part, int64_t max_core_atoms, void* stream,
+                             ac_chunked** out) {
+    if (!out) return fail(AC_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (n_parts < 1 || part < 0 || part >= n_parts) return fail(AC_ERR_INVALID_ARG, "part outside [0, n_parts)");
+    if (max_core_atoms < 1) return fail(AC_ERR_INVALID_ARG, "max_core_atoms < 1");
+    ac_options o{};
+    if (opt) o = *opt;
+    if (o.keep_candidates) return fail(AC_ERR_INVALID_ARG, "keep_candidates is not available in a part build");
+    cudaStream_t s = (cudaStream_t)stream;
+    StreamScope scope(s);
+    std::unique_ptr<ac_chunked> res(new (std::nothrow) ac_chunked());
+    if (!res) return fail(AC_ERR_OOM, "host allocation failed");
+    const double t0 = now_ms();
+    SlabPlan P;
+    AC_TRY(quantise_z(centres, radii, n, alpha, P));
+    std::vector<int64_t> thr;
+    cut_parts(P, n_parts, thr);
+    res->st.ms_plan = now_ms() - t0;
+    AC_TRY(build_range(centres, radii, n, alpha, o, max_core_atoms, P, thr[(size_t)part], thr[(size_t)part + 1], s,
+                       res.get()));
+    *out = res.release();
+    return AC_OK;
+}
+
+extern "C" int ac_merge_parts(int64_t n, int64_t n_parts, const int64_t* counts, const int32_t* const* tuples,
+                              const double* const* f, const uint8_t* const* attached, ac_chunked** out) {
+    if (!out) return fail(AC_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (n < 0 || n_parts < 0 || (n_parts > 0 && (!counts || !tuples || !f || !attached)))
+        return fail(AC_ERR_INVALID_ARG, "bad argument");
+    std::unique_ptr<ac_chunked> res(new (std::nothrow) ac_chunked());
+    if (!res) return fail(AC_ERR_OOM, "host allocation failed");
+    const double t0 = now_ms();
+    std::vector<int64_t> off;
+    for (int d = 0; d < 4; d++) {
+        std::vector<ShareView> views;
+        for (int64_t p = 0; p < n_parts; p++) {
+            const int64_t c = counts[4 * p + d];
+            if (c < 0 || (c > 0 && (!tuples[4 * p + d] || !f[4 * p + d] || !attached[4 * p + d])))
+                return fail(AC_ERR_INVALID_ARG, "a share has a negative count or a NULL array");
+            views.push_back({tuples[4 * p + d], f[4 * p + d], attached[4 * p + d], c});
+        }
+        AC_TRY(place(n, d, views, off, res.get()));
+    }
+    res->st.n_chunks = n_parts;
+    res->st.ms_assemble = now_ms() - t0;
     *out = res.release();
     return AC_OK;
 }
