@@ -226,9 +226,10 @@ AC_API int ac_eval_filtration_fp32(ac_ctx* ctx, float* const d_f_out[4], void* s
  * The paper gives no gradient: this is the derivative of the Size of Section
  * 2.3, taken through the source simplex's OrthoSize with the source held fixed
  * (an envelope argument: the multipliers of the equal-power constraints are
- * the barycentric coordinates of c). Every sum is taken in a fixed order (per
- * source simplex, then per atom; no floating-point atomics), so repeated calls
- * give bit-identical gradients. Scratch: one double per simplex, allocated by
+ * the barycentric coordinates of c). Every sum is taken in a fixed order (up
+ * the build's coface links to each source simplex, then per atom; no
+ * floating-point atomics), so repeated calls give bit-identical gradients.
+ * Scratch: 8 bytes per simplex and 32 per vertex of each simplex, allocated by
  * the context on first use. Returns after the device work is finished.
  * Errors: AC_ERR_INVALID_ARG (NULL), AC_ERR_STATE (no build), AC_ERR_OOM,
  * AC_ERR_CUDA.

@@ -302,29 +302,36 @@ int eval_filtration(ac_ctx* c, const double* centres, const double* radii, doubl
 //
 // Sum over the simplices sigma of w_sigma * dOrthoSize(src(sigma)): grouped by
 // source, each source s contributes W_s * dOrthoSize(s), W_s the sum of the
-// weights of the simplices whose source it is. Sources are unattached
-// simplices (witnessed at their own orthocentre), and a simplex whose source
-// is s is s itself or a face of s. So:
-//   1. k_source_weights, one thread per row of each list: W_s = w_s plus the
-//      weights of the faces of s whose source is s, faces visited in a fixed
-//      order and found in their first vertex's rows (0 for attached rows).
-//   2. k_backward_atoms, one thread per atom a: the sum over the unattached
-//      simplices s containing a of 2 W_s lambda_a(s) (p_a - c_s) and
-//      -2 W_s lambda_a(s) r_a, in a fixed order. Every vertex of a simplex of
-//      the complex has a grown ball meeting a's, so the first (smallest)
-//      vertex of s is a or one of a's neighbours with a smaller input index:
-//      their rows in every list, in neighbour-list order, are all the candidates.
+// weights of the simplices whose source it is. An attached simplex takes its
+// source from its parent, the coface its value came from (the build's
+// coface passes keep, for every coface, the rows of its attached facets, and
+// for every attached row its parent), and an unattached one is its own
+// source. So:
+//   1. k_weights_up, dimension 0 to 3, one thread per row: W'(sigma) =
+//      w(sigma) + the W' of the attached facets whose parent sigma is, in
+//      facet order. An unattached row's W' is its W_s; an attached row hands
+//      its W' up and is no source.
+//   2. k_contrib, one thread per unattached row with W_s != 0: the
+//      orthocentre and barycentric coordinates of s, and for each vertex k of
+//      s the contribution (2 W_s lambda_k (p_k - c), -2 W_s lambda_k r_k).
+//   3. k_gather_atoms, one warp per atom a: the contributions of the rows
+//      containing a, summed per lane and then over the lanes by a fixed tree.
+//      Every vertex of a simplex of the complex has a grown ball meeting a's,
+//      so the first (smallest) vertex of a row containing a is a or one of
+//      a's neighbours with a smaller input index: lane t takes neighbour t
+//      (and lane 0 a itself first), every list, every row of that first vertex.
 
 struct BackArgs {
     const double* X;         // centres (n x 3), input order
     const double* R;         // radii
     const int4* G[4];        // rows per dimension, global input indices
     const int64_t* v0[4];    // rows with first vertex g start at v0[d][g] (n + 1)
-    const int8_t* sdim[4];   // source of each row: dimension ...
-    const int64_t* sidx[4];  // ... and row
     const uint8_t* att[4];   // attached flags
     const double* w[4];      // dL/df per row (NULL: zero)
-    const double* W[4];      // per-row source weights (pass 1 output, pass 2 input)
+    double* Wp[4];           // W' per row (pass 1)
+    const int64_t* frows[3]; // frows[d]: rows of the attached facets (dim d) of each coface (dim d + 1), or -1
+    const unsigned long long* parent[3];  // parent[d][r]: the coface (row of dim d + 1) of attached row r of dim d
+    double4* C[4];           // per row, per vertex: (dL/dp, dL/dr) contributions (pass 2)
     int64_t rows[4];
     const int32_t* rank;     // input index -> sorted position
     const int32_t* order;    // sorted position -> input index
@@ -334,72 +341,80 @@ struct BackArgs {
     int64_t n;
 };
 
-// row of the ascending tuple t (k entries) in list k - 1, or -1
-__device__ __forceinline__ int64_t find_row(const BackArgs& A, int k, const int* t) {
-    const int d = k - 1;
-    const int64_t lo = A.v0[d][t[0]], hi = A.v0[d][t[0] + 1];
-    for (int64_t r = lo; r < hi; r++) {
-        const int4 g = A.G[d][r];
-        if ((k < 2 || g.y == t[1]) && (k < 3 || g.z == t[2]) && (k < 4 || g.w == t[3])) return r;
-    }
-    return -1;
-}
-
-__global__ void k_source_weights(BackArgs A, int d, double* __restrict__ Wout) {
-    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= A.rows[d]) return;
-    double W = 0.0;
-    if (!A.att[d][r]) {
-        const int4 g = A.G[d][r];
-        const int v[4] = {g.x, g.y, g.z, g.w};
-        if (A.w[d] && A.sdim[d][r] == d && A.sidx[d][r] == r) W = A.w[d][r];
-        // proper faces, by decreasing dimension, each as the subset of v kept by a mask
-        for (int e = d - 1; e >= 0; e--) {
-            if (!A.w[e]) continue;
-            for (unsigned mask = 0; mask < (1u << (d + 1)); mask++) {
-                if (__popc(mask) != e + 1) continue;
-                int t[4] = {0, 0, 0, 0}, k = 0;
-                for (int j = 0; j <= d; j++)
-                    if (mask & (1u << j)) t[k++] = v[j];
-                const int64_t f = find_row(A, e + 1, t);
-                if (f >= 0 && A.sdim[e][f] == d && A.sidx[e][f] == r) W += A.w[e][f];
-            }
+__global__ void k_weights_up(BackArgs A, int d) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= A.rows[d]) return;
+    double W = A.w[d] ? A.w[d][j] : 0.0;
+    if (d >= 1 && A.frows[d - 1]) {
+        const int64_t* fr = A.frows[d - 1] + j * (d + 1);
+        for (int drop = 0; drop <= d; drop++) {
+            const int64_t r = fr[drop];
+            if (r >= 0 && A.parent[d - 1][r] == (unsigned long long)j) W += A.Wp[d - 1][r];
         }
     }
-    Wout[r] = W;
+    A.Wp[d][j] = W;
 }
 
-__global__ void k_backward_atoms(BackArgs A, double* __restrict__ dX, double* __restrict__ dR) {
-    const int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void k_contrib(BackArgs A, int d) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= A.rows[d]) return;
+    double4* out = A.C[d] + j * (d + 1);
+    const double W = A.att[d][j] ? 0.0 : A.Wp[d][j];
+    if (W == 0.0) {
+        for (int k = 0; k <= d; k++) out[k] = make_double4(0.0, 0.0, 0.0, 0.0);
+        return;
+    }
+    const int4 g = A.G[d][j];
+    const int v[4] = {g.x, g.y, g.z, g.w};
+    const Ortho o = ortho_fp64(A.X, A.R, g, d + 1);
+    for (int k = 0; k <= d; k++) {
+        const int64_t a = v[k];
+        const double l2 = 2.0 * W * o.lam[k];
+        out[k] = make_double4(l2 * (A.X[3 * a] - o.c[0]), l2 * (A.X[3 * a + 1] - o.c[1]), l2 * (A.X[3 * a + 2] - o.c[2]),
+                              -l2 * A.R[a]);
+    }
+}
+
+constexpr int GATHER_WARPS = 4;
+
+__global__ void __launch_bounds__(GATHER_WARPS * 32) k_gather_atoms(BackArgs A, double* __restrict__ dX,
+                                                                     double* __restrict__ dR) {
+    const int lane = threadIdx.x & 31;
+    const int64_t a = (int64_t)blockIdx.x * GATHER_WARPS + (threadIdx.x >> 5);
     if (a >= A.n) return;
     const int ia = A.rank[a];
     const int64_t off = A.nb_stride ? (int64_t)ia * A.nb_stride : A.nb_off[ia];
     const int m = A.nb_stride ? (int)A.nb_off[ia] : (int)(A.nb_off[ia + 1] - off);
-    const double xa = A.X[3 * a], ya = A.X[3 * a + 1], za = A.X[3 * a + 2], ra = A.R[a];
     double gx = 0.0, gy = 0.0, gz = 0.0, gr = 0.0;
-    for (int t = -1; t < m; t++) {
+    for (int t = lane - 1; t < m; t += 32) {
         const int64_t b = t < 0 ? a : (int64_t)A.order[A.nb[off + t]];
         if (t >= 0 && b >= a) continue;
         for (int d = 0; d < 4; d++) {
             for (int64_t r = A.v0[d][b]; r < A.v0[d][b + 1]; r++) {
-                const double W = A.W[d][r];
-                if (W == 0.0) continue;
                 const int4 g = A.G[d][r];
                 const int k = g.x == a ? 0 : (d >= 1 && g.y == a) ? 1 : (d >= 2 && g.z == a) ? 2 : (d >= 3 && g.w == a) ? 3 : -1;
                 if (k < 0) continue;
-                const Ortho o = ortho_fp64(A.X, A.R, g, d + 1);
-                const double l2 = 2.0 * W * o.lam[k];
-                gx += l2 * (xa - o.c[0]);
-                gy += l2 * (ya - o.c[1]);
-                gz += l2 * (za - o.c[2]);
-                gr -= l2 * ra;
+                const double4 q = A.C[d][r * (d + 1) + k];
+                gx += q.x;
+                gy += q.y;
+                gz += q.z;
+                gr += q.w;
             }
         }
     }
-    dX[3 * a] = gx;
-    dX[3 * a + 1] = gy;
-    dX[3 * a + 2] = gz;
-    dR[a] = gr;
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) {  // a fixed tree: the same additions in the same order every call
+        gx += __shfl_xor_sync(0xffffffffu, gx, o);
+        gy += __shfl_xor_sync(0xffffffffu, gy, o);
+        gz += __shfl_xor_sync(0xffffffffu, gz, o);
+        gr += __shfl_xor_sync(0xffffffffu, gr, o);
+    }
+    if (lane == 0) {
+        dX[3 * a] = gx;
+        dX[3 * a + 1] = gy;
+        dX[3 * a + 2] = gz;
+        dR[a] = gr;
+    }
 }
 
 int backward(ac_ctx* c, const double* const dldf[4], double* dc, double* dr, cudaStream_t s) {
@@ -409,20 +424,31 @@ int backward(ac_ctx* c, const double* const dldf[4], double* dc, double* dr, cud
     memset(&A, 0, sizeof(A));
     A.X = c->centres.as<double>();
     A.R = c->radii.as<double>();
-    size_t total = 0;
-    for (int d = 0; d < 4; d++) total += (size_t)c->K[d].count;
-    AC_TRY(c->scratch[3].reserve((total > 0 ? total : 1) * sizeof(double), s));
-    double* Wbuf = c->scratch[3].as<double>();
+    size_t wrows = 0, crows = 0;
     for (int d = 0; d < 4; d++) {
+        wrows += (size_t)c->K[d].count;
+        crows += (size_t)c->K[d].count * (d + 1);
+    }
+    const size_t wbytes = ((wrows > 0 ? wrows : 1) * sizeof(double) + 255) & ~(size_t)255;
+    AC_TRY(c->scratch[3].reserve(wbytes + (crows > 0 ? crows : 1) * sizeof(double4), s));
+    double* Wbuf = c->scratch[3].as<double>();
+    double4* Cbuf = reinterpret_cast<double4*>(static_cast<char*>(c->scratch[3].p) + wbytes);
+    for (int d = 0; d < 4; d++) {
+        const int64_t m = c->K[d].count;
         A.G[d] = c->Gbuf[d].as<int4>();
         A.v0[d] = c->K[d].v0_off.as<int64_t>();
-        A.sdim[d] = c->K[d].src_dim.as<int8_t>();
-        A.sidx[d] = c->K[d].src_idx.as<int64_t>();
         A.att[d] = c->K[d].attached.as<uint8_t>();
-        A.w[d] = c->K[d].count > 0 ? dldf[d] : nullptr;
-        A.W[d] = Wbuf;
-        A.rows[d] = c->K[d].count;
-        Wbuf += c->K[d].count;
+        A.w[d] = m > 0 ? dldf[d] : nullptr;
+        A.Wp[d] = Wbuf;
+        A.C[d] = Cbuf;
+        A.rows[d] = m;
+        Wbuf += m;
+        Cbuf += m * (d + 1);
+        if (d < 3) {
+            const bool cof = c->K[d + 1].count > 0;  // the coface passes ran: frows[d], fargs[d] hold this build's
+            A.frows[d] = cof ? c->frows[d].as<int64_t>() : nullptr;
+            A.parent[d] = cof ? c->fargs[d].as<unsigned long long>() : nullptr;
+        }
     }
     A.rank = c->rank.as<int32_t>();
     A.order = c->order.as<int32_t>();
@@ -433,10 +459,16 @@ int backward(ac_ctx* c, const double* const dldf[4], double* dc, double* dr, cud
     for (int d = 0; d < 4; d++) {
         const int64_t m = A.rows[d];
         if (m == 0) continue;
-        k_source_weights<<<(unsigned)((m + 127) / 128), 128, 0, s>>>(A, d, const_cast<double*>(A.W[d]));
+        k_weights_up<<<(unsigned)((m + 127) / 128), 128, 0, s>>>(A, d);
         AC_LAUNCHED();
     }
-    k_backward_atoms<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(A, dc, dr);
+    for (int d = 0; d < 4; d++) {
+        const int64_t m = A.rows[d];
+        if (m == 0) continue;
+        k_contrib<<<(unsigned)((m + 127) / 128), 128, 0, s>>>(A, d);
+        AC_LAUNCHED();
+    }
+    k_gather_atoms<<<(unsigned)((n + GATHER_WARPS - 1) / GATHER_WARPS), GATHER_WARPS * 32, 0, s>>>(A, dc, dr);
     AC_LAUNCHED();
     AC_CUDA(cudaStreamSynchronize(s));
     return AC_OK;
