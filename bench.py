@@ -401,6 +401,17 @@ def run_forms(args):
                             "simplices": pst["simplices"], "max_degree": pst["max_degree"],
                             "neighbour_pairs_per_atom": pst["neighbour_pairs"] / len(rp)}
     px.close()
+    # the same cloud with radii over a factor of 16: dozens of atoms per thousand have 513..1,024
+    # neighbours (32-word rows, working sets in global memory)
+    cw, rw = synth.particles(15, 200000, r_hi=4.0)
+    wx = ac.AlphaComplex(torch.from_numpy(cw).cuda(), torch.from_numpy(rw).cuda(), 0.0)
+    ms = time_builds(wx, steps, warm, stream, flush)
+    wst = wx.stats()
+    out["particles200k_wide"] = {"atoms_per_s": len(rw) * steps / (sum(ms) / 1e3), "ms_per_step": sum(ms) / steps,
+                                 "simplices": wst["simplices"], "max_degree": wst["max_degree"],
+                                 "neighbour_pairs_per_atom": wst["neighbour_pairs"] / len(rw),
+                                 "local_kernel_ms": wst["ms_stage"][7]}
+    wx.close()
     # batch: one context over all molecules vs one context per molecule
     sizes = synth.batch_sizes(4, 1024)
     mols = [synth.globule(1000 + m, int(n), probe=True) for m, n in enumerate(sizes)]

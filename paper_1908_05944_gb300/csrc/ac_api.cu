@@ -927,6 +927,7 @@ static int record_build(ac_ctx* c, const DevCounters& post, cudaStream_t s) {
     r.nb_total = c->nb_total;
     r.nb_stride = c->nb_stride;
     r.n_wide = c->n_wide;
+    r.n_huge = c->n_huge;
     r.post = post;
     r.post.err = 0;
     r.n_pending = (int64_t)post.n_pending;

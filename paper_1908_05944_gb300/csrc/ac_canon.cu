@@ -600,7 +600,7 @@ __global__ void __launch_bounds__(EW_WARPS * 32) k_edge_write(EdgeMarkArgs a, in
                                                               const int64_t* __restrict__ mol_off, int4* __restrict__ G,
                                                               int32_t* __restrict__ out, uint8_t* __restrict__ attached,
                                                               uint8_t* __restrict__ endpoint) {
-    __shared__ int hs_all[EW_WARPS][512];  // an atom's marked entries: at most its row length (512)
+    __shared__ int hs_all[EW_WARPS][MAX_DEGREE];  // an atom's marked entries: at most its row length
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     int* hs = hs_all[wib];
     const int64_t g = (int64_t)blockIdx.x * EW_WARPS + wib;

@@ -196,9 +196,9 @@ __global__ void k_neighbours(const int4* __restrict__ Ps, const int32_t* __restr
 // Work order of the per-atom pass: sorted positions by decreasing neighbour
 // count (ties in any order), so the costliest atoms start first and the
 // kernel's tail is short; the atoms with more than 64 neighbours form its head.
-constexpr int DEG_BINS = 258;  // counts 0..256, and 257 for anything above
+constexpr int DEG_BINS = 259;  // counts 0..256, 257 for 257..512, 258 for anything above
 
-__device__ __forceinline__ int deg_bin(int64_t m) { return m > 256 ? 257 : (int)m; }
+__device__ __forceinline__ int deg_bin(int64_t m) { return m > 512 ? 258 : m > 256 ? 257 : (int)m; }
 
 __global__ void k_deg_hist(const int64_t* __restrict__ cnt, int64_t n, unsigned* __restrict__ hist) {
     __shared__ unsigned h[DEG_BINS];
@@ -211,7 +211,8 @@ __global__ void k_deg_hist(const int64_t* __restrict__ cnt, int64_t n, unsigned*
         if (h[t]) atomicAdd(&hist[t], h[t]);
 }
 
-// start of each bin in decreasing order, and the head size: one thread per bin
+// start of each bin in decreasing order, and the head sizes (atoms with more
+// than 64, and more than 512, neighbours): one thread per bin
 __global__ void k_deg_starts(const unsigned* __restrict__ hist, unsigned* __restrict__ cursor,
                              long long* __restrict__ n_wide) {
     __shared__ unsigned h[DEG_BINS];
@@ -222,7 +223,8 @@ __global__ void k_deg_starts(const unsigned* __restrict__ hist, unsigned* __rest
     unsigned run = 0;
     for (int q = DEG_BINS - 1; q > b; q--) run += h[q];
     cursor[b] = run;
-    if (b == 65) *n_wide = run + h[65];
+    if (b == 65) n_wide[0] = run + h[65];
+    if (b == DEG_BINS - 1) n_wide[1] = h[DEG_BINS - 1];
 }
 
 __global__ void k_deg_scatter(const int64_t* __restrict__ cnt, int64_t n, unsigned* __restrict__ cursor,
@@ -281,7 +283,8 @@ int build_neighbours(ac_ctx* c, cudaStream_t s) {
     AC_TRY(c->deg.reserve(2 * DEG_BINS * sizeof(unsigned) + 64, s));
     unsigned* hist = c->deg.as<unsigned>();
     unsigned* cursor = hist + DEG_BINS;
-    long long* n_wide = reinterpret_cast<long long*>(hist + 2 * DEG_BINS);  // byte 2064: 8-aligned
+    static_assert((2 * DEG_BINS * sizeof(unsigned)) % 8 == 0, "head counts 8-aligned");
+    long long* n_wide = reinterpret_cast<long long*>(hist + 2 * DEG_BINS);  // n_wide[0], n_huge = n_wide[1]
     AC_CUDA(cudaMemsetAsync(hist, 0, DEG_BINS * sizeof(unsigned), s));
     k_deg_hist<<<nb, 128, 0, s>>>(cntp, n, hist);
     AC_LAUNCHED();
@@ -295,17 +298,21 @@ int build_neighbours(ac_ctx* c, cudaStream_t s) {
         // sizes of the recorded build, checked on the device
         total = c->rec.nb_total;
         c->n_wide = c->rec.n_wide;
+        c->n_huge = c->rec.n_huge;
         AC_TRY(expect_u64(c, &dc->nb_sum, (unsigned long long)total, s));
         AC_TRY(expect_i64(c, reinterpret_cast<const int64_t*>(n_wide), c->n_wide, s));
+        AC_TRY(expect_i64(c, reinterpret_cast<const int64_t*>(n_wide + 1), c->n_huge, s));
         AC_TRY(expect_i64(c, c->pair_moff.as<int64_t>() + n, c->pair_words, s));
     } else {
         AC_CUDA(cudaMemcpyAsync(c->h_stage + 1, n_wide, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        AC_CUDA(cudaMemcpyAsync(c->h_stage + 3, n_wide + 1, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
         AC_CUDA(cudaMemcpyAsync(c->h_stage + 2, c->pair_moff.as<int64_t>() + n, sizeof(int64_t),
                                 cudaMemcpyDeviceToHost, s));
         DevCounters h;
         AC_TRY(read_counters(c, &h, s));  // also completes the copies above
         total = (int64_t)h.nb_sum;
         c->n_wide = c->h_stage[1];
+        c->n_huge = c->h_stage[3];
         c->pair_words = c->h_stage[2];
         if (h.err & DERR_COINCIDENT)
             return fail(AC_ERR_DEGENERATE, "two centres coincide after quantisation to 1/1024 A");

@@ -109,6 +109,7 @@ struct DevCounters {
     unsigned long long n_pending;     // simplices escalated to the resolve kernel
     unsigned long long work_next;     // persistent-kernel work counter (narrow-row launch)
     unsigned long long work_next2;    // work counter of the wide-row launch
+    unsigned long long work_next3;    // work counter of the launch for atoms beyond 512 neighbours
     unsigned int err;
     int max_degree;
     int bad_index;
@@ -119,6 +120,9 @@ struct DevCounters {
 // Row length of the padded neighbour layout: L(i) at nb[i * NB_STRIDE ..]
 // when no atom has more neighbours, else a compact list at scanned offsets.
 constexpr int NB_STRIDE = 128;
+// Most grown-ball neighbours an atom may have (rows of 32 words of 32 bits,
+// 10-bit row positions in the per-atom pass).
+constexpr int MAX_DEGREE = 1024;
 
 // Grid of one molecule: origin (quanta), cell side, dims, first global cell.
 struct MolGrid {
@@ -176,7 +180,7 @@ struct BuildRecord {
     bool valid = false;
     ac_options opt{};
     int wmax = 0;
-    int64_t nb_total = 0, n_wide = 0;
+    int64_t nb_total = 0, n_wide = 0, n_huge = 0;
     int nb_stride = 0;      // layout of the neighbour lists (0: compact)
     int64_t n_pending = 0;  // escalated simplices before the resolve kernel
     DevCounters post{};     // counters after the resolve kernel
@@ -230,6 +234,8 @@ struct ac_ctx {
     ac::DevBuf work;      // int32 sorted positions by decreasing neighbour count
     ac::DevBuf deg;       // degree histogram and cursors of the work order
     int64_t n_wide = 0;   // atoms with more than 64 neighbours (the head of work)
+    int64_t n_huge = 0;   // atoms with more than 512 neighbours (the head of the head)
+    ac::DevBuf huge_ws;   // per-warp working sets of the launch for those atoms (global memory)
     int64_t cap_tet = 0, cap_tri = 0, cap_edge = 0, cap_cand[4] = {0, 0, 0, 0}, cap_pending = 0;
 
     // canonical results; Gbuf/CGbuf hold the same rows as int4 of global input indices

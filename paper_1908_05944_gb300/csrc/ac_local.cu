@@ -134,10 +134,13 @@ struct LocalArgs {
     const int32_t* nb;
     int nb_stride;
     int64_t n;
-    // Work of one launch: the atoms work[0..n-1], taken through work_next (or
-    // work_next2 when counter2 is set, for a launch running beside another).
+    // Work of one launch: the atoms work[0..n-1], taken through work_next,
+    // work_next2 or work_next3 (counter 0, 1, 2: launches running beside one another).
     const int32_t* work;
-    int counter2;
+    int counter;
+    // rows of more than 16 words: the per-warp working sets, in global memory
+    // (one per warp of the launch), as they do not fit shared memory
+    void* gws;
     PredConst pc;
     Bounds<float> b32;
     Bounds<double> b64;
@@ -500,7 +503,8 @@ __global__ void __launch_bounds__(256, 4) k_local(LocalArgs A) {
     constexpr bool is32 = sizeof(R) == 4;
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
-    SM& S = reinterpret_cast<SM*>(smem_raw)[wib];
+    SM& S = WORDS > 16 ? reinterpret_cast<SM*>(A.gws)[(size_t)blockIdx.x * (blockDim.x >> 5) + wib]
+                       : reinterpret_cast<SM*>(smem_raw)[wib];
     DevCounters* cnt = A.cnt;
     const long long Aq = A.pc.A;
     constexpr bool keep = KEEP;  // A.pc.keep_candidates
@@ -514,7 +518,7 @@ __global__ void __launch_bounds__(256, 4) k_local(LocalArgs A) {
     __syncwarp();
 
     const long long n_items = A.n;
-    unsigned long long* next = A.counter2 ? &cnt->work_next2 : &cnt->work_next;
+    unsigned long long* next = A.counter == 2 ? &cnt->work_next3 : A.counter == 1 ? &cnt->work_next2 : &cnt->work_next;
     for (;;) {
         long long i_ll = 0;
         if (lane == 0) i_ll = (long long)atomicAdd(next, 1ull);
@@ -1309,6 +1313,27 @@ static int launch_local(ac_ctx* c, const LocalArgs& a, int64_t max_items, int wa
     return AC_OK;
 }
 
+// Atoms with 513..1024 neighbours: rows of 32 words, each warp's working set
+// (about 300 KB) in global memory, one warp per atom up to 16 per SM (the
+// kernel waits on memory: warps hide it), 2 GB of working sets at most;
+// blocks of two warps.
+template <class R>
+static int launch_huge(ac_ctx* c, LocalArgs a, cudaStream_t s) {
+    int dev = 0, sms = 0;
+    AC_CUDA(cudaGetDevice(&dev));
+    AC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int64_t cap = ((int64_t)2 << 30) / (int64_t)sizeof(WarpSmem<32>);
+    const int64_t warps = std::min<int64_t>(std::min<int64_t>(a.n, 16 * (int64_t)sms), cap);
+    const int64_t blocks = (warps + 1) / 2;
+    AC_TRY(c->huge_ws.reserve((size_t)blocks * 2 * sizeof(WarpSmem<32>), s));
+    a.gws = c->huge_ws.p;
+    void (*kern)(LocalArgs) = a.pc.keep_candidates ? k_local<32, R, true> : k_local<32, R, false>;
+    kern<<<(unsigned)blocks, 64, 0, s>>>(a);
+    AC_LAUNCHED();
+    c->local_launches++;
+    return AC_OK;
+}
+
 template <class R>
 static int launch_words(ac_ctx* c, int words, const LocalArgs& a, int warps, cudaStream_t s) {
     return words == 1 ? launch_local<1, R>(c, a, a.n, warps, s)
@@ -1323,25 +1348,37 @@ static int launch_words(ac_ctx* c, int words, const LocalArgs& a, int warps, cud
 // run in a kernel with wider rows on a side stream, concurrently with the
 // narrow kernel (64-bit rows: smaller shared-memory footprint, twice the
 // resident warps) over the rest; the wide launch is small and starts first.
+// Atoms with more than 512 neighbours (the head of the head) run before it on
+// the side stream, with their working sets in global memory.
 template <class R>
 static int launch_pass(ac_ctx* c, int words, LocalArgs& a, cudaStream_t s) {
     AC_TRY(stage_mark(c, 8, s));
     const int32_t* work = c->work.as<int32_t>();
     const int64_t n_wide = words > 2 ? c->n_wide : 0;
+    const int64_t n_huge = words > 16 ? std::min(c->n_huge, n_wide) : 0;
     if (n_wide > 0) {
-        LocalArgs wide = a;
-        wide.work = work;
-        wide.n = n_wide;
-        wide.counter2 = 1;
         AC_CUDA(cudaEventRecord(c->ev_fork, s));
         AC_CUDA(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
-        AC_TRY(launch_words<R>(c, words, wide, 4, c->side));
+        if (n_huge > 0) {
+            LocalArgs huge = a;
+            huge.work = work;
+            huge.n = n_huge;
+            huge.counter = 2;
+            AC_TRY(launch_huge<R>(c, huge, c->side));
+        }
+        if (n_wide > n_huge) {
+            LocalArgs wide = a;
+            wide.work = work + n_huge;
+            wide.n = n_wide - n_huge;
+            wide.counter = 1;
+            AC_TRY(launch_words<R>(c, words > 16 ? 16 : words, wide, 4, c->side));
+        }
         AC_CUDA(cudaEventRecord(c->ev_join, c->side));
     }
     LocalArgs narrow = a;
     narrow.work = work + n_wide;
     narrow.n = a.n - n_wide;
-    narrow.counter2 = 0;
+    narrow.counter = 0;
     if (narrow.n > 0) AC_TRY(launch_words<R>(c, n_wide > 0 ? 2 : words, narrow, 0, s));
     if (n_wide > 0) AC_CUDA(cudaStreamWaitEvent(s, c->ev_join, 0));
     AC_TRY(stage_mark(c, 9, s));
@@ -1410,10 +1447,11 @@ int run_local(ac_ctx* c, cudaStream_t s) {
     const int64_t n = c->n;
     DevCounters h = c->replaying ? c->rec.post : c->hc;  // read after the neighbour count pass
     const int maxdeg = h.max_degree;
-    int words = maxdeg <= 32 ? 1 : maxdeg <= 64 ? 2 : maxdeg <= 128 ? 4 : maxdeg <= 256 ? 8 : maxdeg <= 512 ? 16 : 0;
+    int words = maxdeg <= 32 ? 1 : maxdeg <= 64 ? 2 : maxdeg <= 128 ? 4 : maxdeg <= 256 ? 8 : maxdeg <= 512 ? 16
+              : maxdeg <= MAX_DEGREE ? 32 : 0;
     if (words == 0) {
         char b[128];
-        snprintf(b, sizeof(b), "an atom has %d neighbours; the per-atom kernel handles at most 512", maxdeg);
+        snprintf(b, sizeof(b), "an atom has %d neighbours; the per-atom kernel handles at most %d", maxdeg, MAX_DEGREE);
         return fail(AC_ERR_CAPACITY, b);
     }
     size_t nn = (size_t)(n > 0 ? n : 1);

@@ -1,6 +1,7 @@
 """Point sets unlike proteins: an SPH-like particle cloud with radii spread over a
 factor of 8 (against about 1.2 for atoms), so neighbour counts vary from a few
-to over a hundred and many atoms take the wide-row path of the per-atom kernel.
+to over a hundred and many atoms take the wide-row path of the per-atom kernel;
+spreads of 12 and 16 reach 257..512 and 513..1,024 neighbours.
 The whole complex must equal the oracle's, for alpha 0 and alpha > 0, in both
 predicate modes.
 """
@@ -44,10 +45,20 @@ def test_particles_beyond_256_neighbours():
     assert_same_complex(gpu, oracle.alpha_complex(c, r, 0.0))
 
 
-def test_particles_beyond_512_neighbours_refused():
+def test_particles_beyond_512_neighbours():
+    """Radii over a factor of 16: dozens of particles have 513..667 grown-ball neighbours and take the
+    per-atom kernel's 32-word rows (working sets in global memory); the complex equals the oracle's."""
+    c, r = synth.particles(14, 3000, r_hi=4.0)
+    for mode in (0, 1):
+        gpu = run_gpu(c, r, 0.0, precision=mode)
+        assert 512 < gpu.stats()["max_degree"] <= 1024
+        assert_same_complex(gpu, oracle.alpha_complex(c, r, 0.0))
+
+
+def test_particles_beyond_1024_neighbours_refused():
     import paper_1908_05944_gb300 as ac
 
-    c, r = synth.particles(14, 3000, r_hi=4.0)
+    c, r = synth.particles(14, 4000, spacing=0.55, r_hi=4.0)  # denser: over 1,024 neighbours
     with pytest.raises(ac.AlphacError) as e:
         run_gpu(c, r, 0.0)
-    assert e.value.code == ac.AC_ERR_CAPACITY and "at most 512" in str(e.value)
+    assert e.value.code == ac.AC_ERR_CAPACITY and "at most 1024" in str(e.value)
