@@ -616,8 +616,8 @@ using namespace ac;
 struct CtxRes {
     int device = -1;
     cudaEvent_t ev[10] = {};
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
-    cudaStream_t side = nullptr, cap_stream = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_copy = nullptr, ev_cjoin = nullptr;
+    cudaStream_t side = nullptr, cap_stream = nullptr, copy = nullptr;
     void* pinned = nullptr;
     size_t pinned_bytes = 0;
 };
@@ -631,7 +631,10 @@ static void res_free(CtxRes& r) {
         if (r.ev[k]) cudaEventDestroy(r.ev[k]);
     if (r.ev_fork) cudaEventDestroy(r.ev_fork);
     if (r.ev_join) cudaEventDestroy(r.ev_join);
+    if (r.ev_copy) cudaEventDestroy(r.ev_copy);
+    if (r.ev_cjoin) cudaEventDestroy(r.ev_cjoin);
     if (r.side) cudaStreamDestroy(r.side);
+    if (r.copy) cudaStreamDestroy(r.copy);
     if (r.cap_stream) cudaStreamDestroy(r.cap_stream);
     if (r.pinned) cudaFreeHost(r.pinned);
     r = CtxRes{};
@@ -656,7 +659,10 @@ static int res_take(size_t pinned_bytes, CtxRes& out) {
     for (int k = 0; k < 10 && ok; k++) ok = cudaEventCreate(&r.ev[k]) == cudaSuccess;
     ok = ok && cudaEventCreateWithFlags(&r.ev_fork, cudaEventDisableTiming) == cudaSuccess &&
          cudaEventCreateWithFlags(&r.ev_join, cudaEventDisableTiming) == cudaSuccess &&
+         cudaEventCreateWithFlags(&r.ev_copy, cudaEventDisableTiming) == cudaSuccess &&
+         cudaEventCreateWithFlags(&r.ev_cjoin, cudaEventDisableTiming) == cudaSuccess &&
          cudaStreamCreateWithFlags(&r.side, cudaStreamNonBlocking) == cudaSuccess &&
+         cudaStreamCreateWithFlags(&r.copy, cudaStreamNonBlocking) == cudaSuccess &&
          cudaStreamCreateWithFlags(&r.cap_stream, cudaStreamNonBlocking) == cudaSuccess &&
          cudaMallocHost(&r.pinned, pinned_bytes) == cudaSuccess;
     if (!ok) {
@@ -777,7 +783,10 @@ static int create_impl(const double* centres, const double* radii, const int64_t
         for (int k = 0; k < 10; k++) c->ev[k] = r.ev[k];
         c->ev_fork = r.ev_fork;
         c->ev_join = r.ev_join;
+        c->ev_copy = r.ev_copy;
+        c->ev_cjoin = r.ev_cjoin;
         c->side = r.side;
+        c->copy = r.copy;
         c->cap_stream = r.cap_stream;
         c->h_pinned = r.pinned;
         c->h_pinned_bytes = r.pinned_bytes;
@@ -1182,12 +1191,16 @@ extern "C" void ac_destroy(ac_ctx* c) {
     for (int k = 0; k < 10; k++) r.ev[k] = c->ev[k];
     r.ev_fork = c->ev_fork;
     r.ev_join = c->ev_join;
+    r.ev_copy = c->ev_copy;
+    r.ev_cjoin = c->ev_cjoin;
     r.side = c->side;
+    r.copy = c->copy;
     r.cap_stream = c->cap_stream;
     r.pinned = c->h_pinned;
     r.pinned_bytes = c->h_pinned_bytes;
     // a set from a failed creation is incomplete: free it rather than cache it
-    bool whole = r.device >= 0 && r.pinned && r.side && r.cap_stream && r.ev_fork && r.ev_join;
+    bool whole = r.device >= 0 && r.pinned && r.side && r.cap_stream && r.copy && r.ev_fork && r.ev_join &&
+                 r.ev_copy && r.ev_cjoin;
     for (int k = 0; k < 10; k++) whole = whole && r.ev[k];
     if (whole && cudaGetLastError() == cudaSuccess) res_give(r);
     else res_free(r);

@@ -1278,18 +1278,40 @@ int subcomplex_flags(ac_ctx* c, int dim, int64_t first, int64_t m, double alpha2
 }
 
 // opt.host_results: list d (rows, the selected filtration values, attached
-// flags) to its page-locked host block, on stream t once its values are final
-static int copy_to_host(ac_ctx* c, int d, cudaStream_t t) {
+// flags) to its page-locked host block, on the context's copy stream (the
+// device-to-host link, about 190 GB/s here, is the limit, so the copies start
+// as early as they can and never hold up the filtration): the rows and flags
+// once the list's rows are written (after stream `from`), the values once
+// they are final (after stream `from`); compute_filtration joins the copies.
+static int copy_after(ac_ctx* c, cudaStream_t from) {
+    AC_CUDA(cudaEventRecord(c->ev_copy, from));
+    AC_CUDA(cudaStreamWaitEvent(c->copy, c->ev_copy, 0));
+    c->copy_forked = true;
+    return AC_OK;
+}
+
+static int copy_rows_to_host(ac_ctx* c, int d, cudaStream_t from) {
     if (!c->opt.host_results) return AC_OK;
     const SimplexList& L = c->K[d];
     const int64_t m = L.count;
     const int k = d + 1;
     AC_TRY(host_block_for(c, d, hres_bytes_for(m, k)));
     char* b = static_cast<char*>(c->hres[d]);
+    AC_TRY(copy_after(c, from));
+    AC_CUDA(cudaMemcpyAsync(b, L.tuples.p, (size_t)m * k * sizeof(int32_t), cudaMemcpyDeviceToHost, c->copy));
+    AC_CUDA(cudaMemcpyAsync(b + hres_a_off(m, k), L.attached.p, (size_t)m, cudaMemcpyDeviceToHost, c->copy));
+    return AC_OK;
+}
+
+static int copy_values_to_host(ac_ctx* c, int d, cudaStream_t from) {
+    if (!c->opt.host_results) return AC_OK;
+    const SimplexList& L = c->K[d];
+    const int64_t m = L.count;
+    const int k = d + 1;
+    char* b = static_cast<char*>(c->hres[d]);
     const DevBuf& f = c->opt.filtration == AC_FILTRATION_ORTHOSIZE ? L.orthosize : L.f;
-    AC_CUDA(cudaMemcpyAsync(b, L.tuples.p, (size_t)m * k * sizeof(int32_t), cudaMemcpyDeviceToHost, t));
-    AC_CUDA(cudaMemcpyAsync(b + hres_f_off(m, k), f.p, (size_t)m * sizeof(double), cudaMemcpyDeviceToHost, t));
-    AC_CUDA(cudaMemcpyAsync(b + hres_a_off(m, k), L.attached.p, (size_t)m, cudaMemcpyDeviceToHost, t));
+    AC_TRY(copy_after(c, from));
+    AC_CUDA(cudaMemcpyAsync(b + hres_f_off(m, k), f.p, (size_t)m * sizeof(double), cudaMemcpyDeviceToHost, c->copy));
     return AC_OK;
 }
 
@@ -1310,6 +1332,7 @@ static int fork_orthosize(ac_ctx* c, int d, cudaStream_t s) {
         AC_TRY(c->fargs[d].reserve((size_t)m * sizeof(unsigned long long), s));
         if (mu > 0) AC_TRY(c->frows[d].reserve((size_t)mu * (d + 2) * sizeof(int64_t), s));
     }
+    AC_TRY(copy_rows_to_host(c, d, s));
     AC_CUDA(cudaEventRecord(c->ev_fork, s));
     cudaStream_t t = c->side;
     AC_CUDA(cudaStreamWaitEvent(t, c->ev_fork, 0));
@@ -1320,7 +1343,7 @@ static int fork_orthosize(ac_ctx* c, int d, cudaStream_t s) {
                                                             L.src_idx.as<int64_t>(), keyb);
     AC_LAUNCHED();
     c->os_forked = true;
-    if (!U) return copy_to_host(c, d, t);
+    if (!U) return copy_values_to_host(c, d, t);
     unsigned long long* argb = c->fargs[d].as<unsigned long long>();
     AC_CUDA(cudaMemsetAsync(argb, 0xff, (size_t)m * sizeof(unsigned long long), t));
     if (mu > 0) {
@@ -1336,7 +1359,7 @@ static int fork_orthosize(ac_ctx* c, int d, cudaStream_t s) {
         m, L.attached.as<uint8_t>(), keyb, argb, U->src_dim.as<int8_t>(), U->src_idx.as<int64_t>(), L.f.as<double>(),
         L.src_dim.as<int8_t>(), L.src_idx.as<int64_t>(), &c->counters.as<DevCounters>()->err);
     AC_LAUNCHED();
-    return copy_to_host(c, d, t);
+    return copy_values_to_host(c, d, t);
 }
 
 // Size of every list (Section 2.3): computed on the side stream as the lists
@@ -1346,6 +1369,11 @@ int compute_filtration(ac_ctx* c, cudaStream_t s) {
         AC_CUDA(cudaEventRecord(c->ev_join, c->side));
         AC_CUDA(cudaStreamWaitEvent(s, c->ev_join, 0));
         c->os_forked = false;
+    }
+    if (c->copy_forked) {
+        AC_CUDA(cudaEventRecord(c->ev_cjoin, c->copy));
+        AC_CUDA(cudaStreamWaitEvent(s, c->ev_cjoin, 0));
+        c->copy_forked = false;
     }
     return AC_OK;
 }

@@ -285,6 +285,9 @@ struct ac_ctx {
     cudaEvent_t ev[10] = {};  // stage boundaries; ev[8], ev[9] bracket the per-atom kernel
     cudaStream_t side = nullptr;                    // wide-row launch, concurrent with the narrow one
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaStream_t copy = nullptr;                    // host copies of the lists (opt.host_results)
+    cudaEvent_t ev_copy = nullptr, ev_cjoin = nullptr;
+    bool copy_forked = false;                       // copies on the copy stream await their join
     int local_launches = 0;
 };
 
