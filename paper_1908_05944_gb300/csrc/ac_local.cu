@@ -1244,7 +1244,8 @@ __device__ __forceinline__ void resolve_item(const LocalArgs& A, int64_t j, int 
             violated = true;
             break;
         }
-    }    n32 = __reduce_add_sync(gmask, n32);
+    }
+    n32 = __reduce_add_sync(gmask, n32);
     n64 = __reduce_add_sync(gmask, n64);
     nx = __reduce_add_sync(gmask, nx);
     if (sub != 0) return;
