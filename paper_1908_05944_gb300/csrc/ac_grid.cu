@@ -107,12 +107,23 @@ __device__ __forceinline__ bool grown_meet(int64_t D, int64_t si, int64_t sx) {
     return t <= 0 || t * t <= 4 * si * sx;
 }
 
-// GUARD: the stencil may span 2^29 quanta or more (very coarse cells), so a
-// pair's coordinate differences are bounded before the 64-bit squares.
+// L(i) for every atom (Section 4.2: the atoms of the cells around the atom's
+// own), one thread per atom. The thread walks the stencil rows (one z, one y,
+// a run of cells along x: a contiguous range of the sorted atoms) in (z, y)
+// order, four candidates per step (their int4 loads issued together), so L(i)
+// comes out in increasing sorted position. Neighbouring threads hold atoms of
+// the same or adjacent cells, so their candidate loads overlap in L1.
+// SMALL: the stencil spans less than NB_SPAN_SMALL quanta per axis, and a
+// pair's test runs in 32-bit integers: squared distances below 2^32, exact
+// 64-bit products of 32-bit factors. Otherwise the test runs in 64-bit
+// integers, with the coordinate differences bounded first (very coarse cells).
 // MODE: NB_COUNT counts L(i); NB_CSR writes it at the offsets nb_off (a scan of
 // the counts); NB_PADDED counts it and writes its first NB_STRIDE entries to the
 // row nb[s * NB_STRIDE ..] in the same pass.
 enum { NB_COUNT = 0, NB_CSR = 1, NB_PADDED = 2 };
+constexpr int NB_UNROLL = 4;
+constexpr int NB_THREADS = 256;
+constexpr int NB_SPAN_SMALL = 37837;  // 3 * 37837^2 < 2^32
 
 struct GridView {
     const int4* Ps;
@@ -121,61 +132,74 @@ struct GridView {
     const uint32_t* cell_start;
 };
 
-template <int MODE, bool GUARD>
-__global__ void k_neighbours(const int4* __restrict__ Ps, const int32_t* __restrict__ mol_s,
-                             const MolGrid* __restrict__ grids, const uint32_t* __restrict__ cell_start,
-                             PredConst pc, int64_t n, int64_t* __restrict__ nb_cnt, const int64_t* __restrict__ nb_off,
-                             int32_t* __restrict__ nb, DevCounters* __restrict__ cnt, int64_t* __restrict__ pw) {
-    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+// Does candidate o meet the atom p (grown squared radius si)? Sets the
+// coincidence error for a second atom at p's centre.
+template <bool SMALL>
+__device__ __forceinline__ bool nb_meet(const int4& p, int64_t si, int32_t si32, int A32, const PredConst& pc,
+                                        const int4& o, DevCounters* cnt) {
+    if (SMALL) {
+        // |differences| < NB_SPAN_SMALL: the squared distance fits 32 bits
+        const int dx = o.x - p.x, dy = o.y - p.y, dz = o.z - p.z;
+        const uint32_t D = (uint32_t)(dx * dx) + (uint32_t)(dy * dy) + (uint32_t)(dz * dz);
+        const int sx = o.w + A32;
+        if (D == 0) {
+            atomicOr(&cnt->err, DERR_COINCIDENT);
+            return false;
+        }
+        if (sx < 0) return false;
+        // meet iff D <= si + sx or (D - si - sx)^2 <= 4 si sx
+        const uint32_t ss = (uint32_t)(si32 + sx), e = D - ss;
+        return D <= ss || (uint64_t)e * e <= (uint64_t)(4u * (uint32_t)si32) * (uint32_t)sx;
+    } else {
+        const int64_t dx = (int64_t)o.x - p.x, dy = (int64_t)o.y - p.y, dz = (int64_t)o.z - p.z;
+        // grown balls meet only within 2h <= 2^13 quanta per axis
+        const int64_t lim = 1 << 20;
+        if (dx >= lim || dx <= -lim || dy >= lim || dy <= -lim || dz >= lim || dz <= -lim) return false;
+        if (dx == 0 && dy == 0 && dz == 0) {
+            atomicOr(&cnt->err, DERR_COINCIDENT);
+            return false;
+        }
+        const int64_t sx = (int64_t)o.w + pc.A;
+        return sx >= 0 && grown_meet(dx * dx + dy * dy + dz * dz, si, sx);
+    }
+}
+
+template <int MODE, bool SMALL>
+__global__ void __launch_bounds__(NB_THREADS)
+    k_neighbours(const int4* __restrict__ Ps, const int32_t* __restrict__ mol_s, const MolGrid* __restrict__ grids,
+                 const uint32_t* __restrict__ cell_start, PredConst pc, int64_t n, int64_t* __restrict__ nb_cnt,
+                 const int64_t* __restrict__ nb_off, int32_t* __restrict__ nb, DevCounters* __restrict__ cnt,
+                 int64_t* __restrict__ pw) {
+    const int64_t s = (int64_t)blockIdx.x * NB_THREADS + threadIdx.x;
     int64_t count = 0;
     if (s < n) {
-        int4 p = Ps[s];
-        int64_t si = (int64_t)p.w + pc.A;
+        const int4 p = Ps[s];
+        const int64_t si = (int64_t)p.w + pc.A;
         const int64_t w = MODE == NB_CSR ? nb_off[s] : MODE == NB_PADDED ? s * NB_STRIDE : 0;
         if (si >= 0) {
-            MolGrid g = grids[mol_s[s]];
+            const MolGrid g = grids[mol_s[s]];
             const int cell = pc.cell, R = pc.reach;
-            int cx = (p.x - g.org[0]) / cell, cy = (p.y - g.org[1]) / cell, cz = (p.z - g.org[2]) / cell;
-            int z0 = max(cz - R, 0), z1 = min(cz + R, g.dims[2] - 1);
-            int y0 = max(cy - R, 0), y1 = min(cy + R, g.dims[1] - 1);
-            int x0 = max(cx - R, 0), x1 = min(cx + R, g.dims[0] - 1);
+            const int cx = (p.x - g.org[0]) / cell, cy = (p.y - g.org[1]) / cell, cz = (p.z - g.org[2]) / cell;
+            const int z0 = max(cz - R, 0), z1 = min(cz + R, g.dims[2] - 1);
+            const int y0 = max(cy - R, 0), y1 = min(cy + R, g.dims[1] - 1);
+            const int x0 = max(cx - R, 0), x1 = min(cx + R, g.dims[0] - 1);
+            const int32_t si32 = (int32_t)si;  // W + A <= 2^24
+            const int A32 = (int)max(pc.A, -(int64_t)(1 << 30));  // below -2^24 no grown ball exists
             for (int z = z0; z <= z1; z++)
                 for (int y = y0; y <= y1; y++) {
-                    int64_t row = g.cell_base + ((int64_t)z * g.dims[1] + y) * g.dims[0];
-                    uint32_t a = cell_start[row + x0], b = cell_start[row + x1 + 1];
-                    // four candidates per step: their loads are issued together
-                    for (uint32_t t0 = a; t0 < b; t0 += 4) {
-                        int4 ov[4];
+                    const int64_t row = g.cell_base + ((int64_t)z * g.dims[1] + y) * g.dims[0];
+                    const uint32_t a = cell_start[row + x0], b = cell_start[row + x1 + 1];
+                    for (uint32_t t0 = a; t0 < b; t0 += NB_UNROLL) {
+                        int4 ov[NB_UNROLL];
 #pragma unroll
-                        for (int u = 0; u < 4; u++) ov[u] = Ps[t0 + u < b ? t0 + u : a];
+                        for (int u = 0; u < NB_UNROLL; u++) ov[u] = __ldg(&Ps[t0 + u < b ? t0 + u : a]);
 #pragma unroll
-                        for (int u = 0; u < 4; u++) {
+                        for (int u = 0; u < NB_UNROLL; u++) {
                             const uint32_t t = t0 + u;
-                            if (t >= b || t == (uint32_t)s) continue;
-                            const int4 o = ov[u];
-                            int64_t dx, dy, dz;
-                            if (GUARD) {
-                                dx = (int64_t)o.x - p.x;
-                                dy = (int64_t)o.y - p.y;
-                                dz = (int64_t)o.z - p.z;
-                                // grown balls meet only within 2h <= 2^13 quanta per axis
-                                const int64_t lim = 1 << 20;
-                                if (dx >= lim || dx <= -lim || dy >= lim || dy <= -lim || dz >= lim || dz <= -lim) continue;
-                            } else {
-                                // the stencil spans less than 2^29 quanta: 32-bit differences, squares below 2^58
-                                dx = o.x - p.x;
-                                dy = o.y - p.y;
-                                dz = o.z - p.z;
+                            if (t < b && t != (uint32_t)s && nb_meet<SMALL>(p, si, si32, A32, pc, ov[u], cnt)) {
+                                if (MODE == NB_CSR || (MODE == NB_PADDED && count < NB_STRIDE)) nb[w + count] = (int32_t)t;
+                                count++;
                             }
-                            if (dx == 0 && dy == 0 && dz == 0) {
-                                atomicOr(&cnt->err, DERR_COINCIDENT);
-                                continue;
-                            }
-                            const int64_t D = dx * dx + dy * dy + dz * dz;
-                            const int64_t sx = (int64_t)o.w + pc.A;
-                            if (sx < 0 || !grown_meet(D, si, sx)) continue;
-                            if (MODE == NB_CSR || (MODE == NB_PADDED && count < NB_STRIDE)) nb[w + count] = (int32_t)t;
-                            count++;
                         }
                     }
                 }
@@ -183,15 +207,34 @@ __global__ void k_neighbours(const int4* __restrict__ Ps, const int32_t* __restr
         if (MODE != NB_CSR) {
             nb_cnt[s] = count;
             pw[s] = pair_mask_words((int)count);  // the K^2 pair mask of this atom
-            atomicMax(&cnt->max_degree, (int)count);
         }
     }
     if (MODE != NB_CSR) {
-        // every lane of the warp reaches here (no early exit above)
-        const unsigned tot = __reduce_add_sync(0xffffffffu, (unsigned)count);
-        if ((threadIdx.x & 31) == 0 && tot) atomicAdd(&cnt->nb_sum, (unsigned long long)tot);
+        // one pair of atomics per block; every thread reaches here (no early exit above)
+        __shared__ unsigned long long b_tot[NB_THREADS / 32];
+        __shared__ int b_max[NB_THREADS / 32];
+        const unsigned wt = __reduce_add_sync(0xffffffffu, (unsigned)count);
+        const unsigned wm = __reduce_max_sync(0xffffffffu, (unsigned)count);
+        if ((threadIdx.x & 31) == 0) {
+            b_tot[threadIdx.x >> 5] = wt;
+            b_max[threadIdx.x >> 5] = (int)wm;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            unsigned long long tot = 0;
+            int m = 0;
+            for (int k = 0; k < NB_THREADS / 32; k++) {
+                tot += b_tot[k];
+                m = max(m, b_max[k]);
+            }
+            if (tot) atomicAdd(&cnt->nb_sum, tot);
+            atomicMax(&cnt->max_degree, m);
+        }
     }
 }
+
+// Blocks of k_neighbours: one thread per atom.
+static unsigned neighbour_blocks(int64_t n) { return (unsigned)((n + NB_THREADS - 1) / NB_THREADS); }
 
 // Work order of the per-atom pass: sorted positions by decreasing neighbour
 // count (ties in any order), so the costliest atoms start first and the
@@ -261,7 +304,8 @@ int build_neighbours(ac_ctx* c, cudaStream_t s) {
     }
     const unsigned nb = (unsigned)((n + 127) / 128);
     DevCounters* dc = c->counters.as<DevCounters>();
-    const bool guard = (int64_t)c->pc.cell * (2 * c->pc.reach + 1) >= ((int64_t)1 << 29);
+    const bool small = (int64_t)(c->pc.reach + 1) * c->pc.cell < NB_SPAN_SMALL;
+    const unsigned kb = neighbour_blocks(n);
     // a replay keeps the recorded layout; a synchronised build tries the padded one
     const bool padded = c->replaying ? c->rec.nb_stride == NB_STRIDE : true;
     const GridView g{c->Ps.as<int4>(), c->mol_s.as<int32_t>(), c->grids.as<MolGrid>(), c->cell_start.as<uint32_t>()};
@@ -269,11 +313,11 @@ int build_neighbours(ac_ctx* c, cudaStream_t s) {
     int64_t* pw = c->cw.cnt.as<int64_t>();
     if (padded) {
         AC_TRY(c->nb.reserve((size_t)n * NB_STRIDE * sizeof(int32_t), s));
-        auto k = guard ? k_neighbours<NB_PADDED, true> : k_neighbours<NB_PADDED, false>;
-        k<<<nb, 128, 0, s>>>(g.Ps, g.mol_s, g.grids, g.cell_start, c->pc, n, cntp, nullptr, c->nb.as<int32_t>(), dc, pw);
+        auto k = small ? k_neighbours<NB_PADDED, true> : k_neighbours<NB_PADDED, false>;
+        k<<<kb, NB_THREADS, 0, s>>>(g.Ps, g.mol_s, g.grids, g.cell_start, c->pc, n, cntp, nullptr, c->nb.as<int32_t>(), dc, pw);
     } else {
-        auto k = guard ? k_neighbours<NB_COUNT, true> : k_neighbours<NB_COUNT, false>;
-        k<<<nb, 128, 0, s>>>(g.Ps, g.mol_s, g.grids, g.cell_start, c->pc, n, cntp, nullptr, nullptr, dc, pw);
+        auto k = small ? k_neighbours<NB_COUNT, true> : k_neighbours<NB_COUNT, false>;
+        k<<<kb, NB_THREADS, 0, s>>>(g.Ps, g.mol_s, g.grids, g.cell_start, c->pc, n, cntp, nullptr, nullptr, dc, pw);
     }
     AC_LAUNCHED();
     // layout of the K^2 pair masks, from the words per atom
@@ -324,8 +368,8 @@ int build_neighbours(ac_ctx* c, cudaStream_t s) {
     AC_TRY(scan_exclusive_i64(c, cntp, cntp, n, s));
     if (c->replaying) AC_TRY(expect_i64(c, cntp + n, total, s));
     AC_TRY(c->nb.reserve((size_t)(total > 0 ? total : 1) * sizeof(int32_t), s));
-    auto k_fill = guard ? k_neighbours<NB_CSR, true> : k_neighbours<NB_CSR, false>;
-    k_fill<<<nb, 128, 0, s>>>(g.Ps, g.mol_s, g.grids, g.cell_start, c->pc, n, nullptr, cntp, c->nb.as<int32_t>(), dc,
+    auto k_fill = small ? k_neighbours<NB_CSR, true> : k_neighbours<NB_CSR, false>;
+    k_fill<<<kb, NB_THREADS, 0, s>>>(g.Ps, g.mol_s, g.grids, g.cell_start, c->pc, n, nullptr, cntp, c->nb.as<int32_t>(), dc,
                               nullptr);
     AC_LAUNCHED();
     return AC_OK;

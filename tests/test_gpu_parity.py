@@ -241,3 +241,20 @@ def test_star_with_oversized_buckets(k):
     assert_same_complex(gpu, ref)
     gpu.build()  # and its replay
     assert_same_complex(gpu, ref)
+
+
+def test_sparse_clusters_coarse_grid():
+    """Eight clusters at the corners of a 20,000 A cube: the dense cell table is coarsened until the
+    cells are far wider than 2h, and the neighbour search takes its 64-bit path."""
+    parts = []
+    for k in range(8):
+        c, r = synth.globule(70 + k, 150, probe=True)
+        corner = np.array([(k >> 0) & 1, (k >> 1) & 1, (k >> 2) & 1]) * 20000.0
+        parts.append((c + corner, r))
+    c = np.concatenate([p[0] for p in parts])
+    r = np.concatenate([p[1] for p in parts])
+    ref = oracle.alpha_complex(c, r, 0.0)
+    gpu = run_gpu(c, r, 0.0)
+    assert_same_complex(gpu, ref)
+    dims = gpu.stats()["grid_dims"]
+    assert max(dims) < 400  # cells over 37,837 quanta wide (about 6,000 cells per axis uncoarsened)
