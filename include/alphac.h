@@ -104,6 +104,8 @@ typedef struct {
     int64_t kernel_launches; /* kernels the last ac_build launched (graph nodes when replayed) */
     int32_t replayed;        /* 1: the last ac_build ran as a CUDA graph replay */
     int32_t host_syncs;      /* host waits for the device during the last ac_build */
+    int64_t escalated;       /* simplices whose AC3 or AC2 the per-atom kernel's bounds left open,
+                                settled by the FP64 / exact-integer kernel */
 } ac_stats;
 
 /*

@@ -55,7 +55,7 @@ class ac_stats(ctypes.Structure):
                 ("ac2_tests_edge", ctypes.c_int64), ("ac3_tests", ctypes.c_int64 * 4), ("ac3_exact", ctypes.c_int64),
                 ("ms_total", ctypes.c_double),
                 ("ms_stage", ctypes.c_double * 8), ("kernel_launches", ctypes.c_int64),
-                ("replayed", ctypes.c_int32), ("host_syncs", ctypes.c_int32)]
+                ("replayed", ctypes.c_int32), ("host_syncs", ctypes.c_int32), ("escalated", ctypes.c_int64)]
 
     def to_dict(self):
         out = {}

@@ -8,6 +8,7 @@
 
 #include <algorithm>
 #include <cstdio>
+#include <map>
 #include <mutex>
 #include <new>
 #include <vector>
@@ -60,8 +61,57 @@ static void prepare_pool() {
     done.push_back(dev);
 }
 
+// Device blocks of destroyed contexts. ac_destroy synchronises the device
+// before it releases a context's buffers, so a block released then is idle and
+// may serve a later reserve on any stream: the next context of a similar size
+// takes its buffers from here instead of from the stream-ordered allocator
+// (an allocation call per buffer).
+struct IdleBlock {
+    void* p;
+    int dev;
+};
+static std::mutex g_idle_mu;
+static std::multimap<size_t, IdleBlock> g_idle;  // by size
+static size_t g_idle_bytes = 0;
+static constexpr size_t IDLE_KEEP_BYTES = 8ull << 30;
+static constexpr size_t IDLE_KEEP_BLOCKS = 1024;
+static thread_local bool g_release_idle = false;  // set by ac_destroy once the device is idle
+
+static bool idle_give(void* p, size_t bytes) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    std::lock_guard<std::mutex> g(g_idle_mu);
+    if (g_idle_bytes + bytes > IDLE_KEEP_BYTES || g_idle.size() >= IDLE_KEEP_BLOCKS) return false;
+    g_idle.emplace(bytes, IdleBlock{p, dev});
+    g_idle_bytes += bytes;
+    return true;
+}
+
+// The smallest idle block of this device with want..2 want + 1 MB bytes, or null.
+static void* idle_take(size_t want, size_t* got) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    std::lock_guard<std::mutex> g(g_idle_mu);
+    const size_t limit = 2 * want + (1u << 20);
+    for (auto it = g_idle.lower_bound(want); it != g_idle.end() && it->first <= limit; ++it) {
+        if (it->second.dev != dev) continue;
+        void* p = it->second.p;
+        *got = it->first;
+        g_idle_bytes -= it->first;
+        g_idle.erase(it);
+        return p;
+    }
+    return nullptr;
+}
+
 DevBuf::~DevBuf() {
-    if (p) cudaFreeAsync(p, release_stream());
+    if (p && !(g_release_idle && idle_give(p, bytes))) cudaFreeAsync(p, release_stream());
 }
 
 DevBuf& DevBuf::operator=(DevBuf&& o) noexcept {
@@ -83,8 +133,14 @@ int DevBuf::reserve(size_t nbytes, cudaStream_t s) {
         p = nullptr;
         bytes = 0;
     }
-    prepare_pool();
     size_t want = nbytes < 256 ? 256 : nbytes;
+    size_t got = 0;
+    if (void* q = idle_take(want, &got)) {
+        p = q;
+        bytes = got;
+        return AC_OK;
+    }
+    prepare_pool();
     cudaError_t e = cudaMallocAsync(&p, want, s);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -569,7 +625,8 @@ int quantise_and_plan(ac_ctx* c, cudaStream_t s) {
     int64_t cell = (int64_t)ceil(c->opt.cell_factor * (double)(hq > 0 ? hq : 1024));
     if (cell < 1) cell = 1;
     // grid dims; coarsen if the dense table would be far larger than the atom count
-    std::vector<MolGrid> grids((size_t)n_mol);
+    std::vector<MolGrid>& grids = c->h_grids;
+    grids.assign((size_t)n_mol, MolGrid{});
     int64_t total = 0;
     for (int iter = 0; iter < 40; iter++) {
         total = 0;
@@ -592,8 +649,9 @@ int quantise_and_plan(ac_ctx* c, cudaStream_t s) {
     if (pc.reach < 1) pc.reach = 1;
     c->n_cells = total;
     AC_TRY(c->grids.reserve((size_t)n_mol * sizeof(MolGrid), s));
+    // from pageable memory: the call returns once the source is staged, so the
+    // next plan may overwrite the host copy
     AC_CUDA(cudaMemcpyAsync(c->grids.p, grids.data(), (size_t)n_mol * sizeof(MolGrid), cudaMemcpyHostToDevice, s));
-    AC_TRY(sync_host(c, s));  // the host copy of the grids goes out of scope
     c->stats.grid_dims[0] = grids[0].dims[0];
     c->stats.grid_dims[1] = grids[0].dims[1];
     c->stats.grid_dims[2] = grids[0].dims[2];
@@ -1017,6 +1075,7 @@ extern "C" int ac_build(ac_ctx* c, void* stream) {
     st.ac2_tests_edge = (int64_t)hl.ac2_edge;
     for (int d = 0; d < 4; d++) st.ac3_tests[d] = (int64_t)hl.ac3[d];
     st.ac3_exact = (int64_t)hl.ac3_exact;
+    st.escalated = (int64_t)hl.n_pending;
     st.ms_stage[0] = elapsed(c->ev[0], c->ev[1]);
     st.ms_stage[1] = elapsed(c->ev[1], c->ev[2]);
     st.ms_stage[2] = elapsed(c->ev[2], c->ev[3]);
@@ -1181,9 +1240,14 @@ extern "C" int ac_get_sizes(ac_ctx* c, int64_t* n_mol, int64_t* n_atoms) {
 
 extern "C" void ac_destroy(ac_ctx* c) {
     if (!c) return;
-    // the context's buffers go back to the pool once no work can still use them
-    cudaDeviceSynchronize();
+    // the context's buffers go back to the pool once no work can still use them;
+    // after a clean synchronisation they are idle and wait for the next context
+    const bool idle = cudaDeviceSynchronize() == cudaSuccess;
     StreamScope scope(nullptr);
+    struct IdleScope {
+        explicit IdleScope(bool on) { g_release_idle = on; }
+        ~IdleScope() { g_release_idle = false; }
+    } idle_scope(idle);
     drop_graph(c);
     for (int d = 0; d < 4; d++) host_block_give(c->hres[d], c->hres_bytes[d]);
     CtxRes r;

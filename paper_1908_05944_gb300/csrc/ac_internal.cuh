@@ -65,7 +65,9 @@ enum : uint32_t {
 // which keeps freed blocks for reuse by later contexts instead of returning
 // them to the driver. Growth and release are ordered on the stream of the
 // entry point running (StreamScope), so no device-wide synchronisation is
-// needed, and a block is reused only after the work that used it.
+// needed, and a block is reused only after the work that used it. The buffers
+// of a destroyed context (released after a device synchronisation, so idle)
+// go to a process-wide cache that later reserves draw on first.
 struct DevBuf {
     void* p = nullptr;
     size_t bytes = 0;
@@ -205,6 +207,7 @@ struct ac_ctx {
     ac::DevBuf mol_of;   // int32 molecule of each atom (input order)
     ac::DevBuf d_moloff; // int64 n_mol + 1
     ac::DevBuf grids;    // MolGrid per molecule
+    std::vector<ac::MolGrid> h_grids;  // host copy (the source of the device copy)
     int64_t n_cells = 0;
 
     // grid + sorted order
