@@ -108,7 +108,8 @@ struct DevCounters {
     unsigned long long ac2_edge;
     unsigned long long ac3[4];
     unsigned long long ac3_exact;     // AC3 decisions left to exact integers
-    unsigned long long n_pending;     // simplices escalated to the resolve kernel
+    unsigned long long n_pending;     // simplices escalated to the resolve kernels
+    unsigned long long n_scan;        // escalated simplices whose AC3 holds (their AC2 scan list)
     unsigned long long work_next;     // persistent-kernel work counter (narrow-row launch)
     unsigned long long work_next2;    // work counter of the wide-row launch
     unsigned long long work_next3;    // work counter of the launch for atoms beyond 512 neighbours
@@ -234,6 +235,7 @@ struct ac_ctx {
     ac::DevBuf vert_pass; // uint8 per sorted atom
     ac::DevBuf cand[4];   // Sigma^d candidate lists when kept (int4 / int2)
     ac::DevBuf pending;   // int4 escalated simplices (see ac_local.cu)
+    ac::DevBuf resolve_scan;  // their AC2 scan records (ResolveScan, ac_local.cu)
     ac::DevBuf work;      // int32 sorted positions by decreasing neighbour count
     ac::DevBuf deg;       // degree histogram and cursors of the work order
     int64_t n_wide = 0;   // atoms with more than 64 neighbours (the head of work)

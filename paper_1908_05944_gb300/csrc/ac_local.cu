@@ -49,11 +49,14 @@
 // 2 gamma_3 H h, K1 = 2 sqrt3 H (1 + gamma_3).
 // A simplex whose AC3, or whose AC2 with no decided violator, stays open is
 // appended to a pending list (an undecided triangle still counts as potential
-// for the enumeration of tetrahedra: a superset is harmless there). k_resolve
-// settles each pending simplex with one thread: exact AC3, then every AC2 test
-// in FP64 from the exact integer minors (relative error <= 4.0001 u_64 per
-// component of y) and, where that is undecided too, in exact 128-bit integers.
-// Keeping the exact arithmetic out of k_local keeps its register budget small.
+// for the enumeration of tetrahedra: a superset is harmless there). Two kernels
+// settle the pending simplices: k_resolve_prep, one thread per simplex, takes
+// the exact AC3 in 128-bit integers and the FP64 orthocentre from the exact
+// integer minors (relative error <= 4.0001 u_64 per component of y); then
+// k_resolve_scan, a group of lanes per simplex whose AC3 holds, makes every AC2
+// test in FP32 and FP64 from that orthocentre and, where both are undecided,
+// in exact 128-bit integers. Keeping the exact arithmetic out of k_local keeps
+// its register budget small.
 // Edge AC3 and the vertex test are exact 64-bit integers in every mode.
 //
 // Ties (Section 2, symbolic perturbation): squared radii W_k + eps_k with eps_k
@@ -1023,7 +1026,7 @@ __global__ void __launch_bounds__(256, 4) k_local(LocalArgs A) {
 }
 
 // ---------------------------------------------------------------------------
-// k_resolve: exact settlement of the pending simplices, one thread each
+// k_resolve_prep / k_resolve_scan: settlement of the pending simplices
 
 __device__ __forceinline__ i128 mul64x64(long long a, long long b) { return (i128)a * (i128)b; }
 
@@ -1040,253 +1043,331 @@ __device__ __forceinline__ bool sos_violates(int nv, const int* g, const long lo
     return sign < 0;
 }
 
-__device__ __forceinline__ bool meet(long long D, long long s1, long long s2) {
-    const long long t = D - s1 - s2;
-    return t <= 0 || t * t <= 4 * s1 * s2;
-}
+constexpr int RESOLVE_LANES = 16;
 
-constexpr int RESOLVE_LANES = 8;
+// Exact quantities of an escalated simplex (owner i, vertices v, nv of them),
+// relative to p_i: vertex offsets q, a_v = |q_v|^2 - W_v + W_i, grown weights
+// s_v = W_v + A, input indices, and the integer minors of its orthocentre
+// (y = N / (2 det) for a tetrahedron; mu = (n1, n2) / (2 det) on the Gram
+// matrix (g11, g12; g12, g22) for a triangle; mu = a / (2 det) for an edge).
+struct Minors {
+    long long q[3][3], a[3], sv[3];
+    int gv[3];
+    long long det, g11, g22, g12, n1, n2, C[3][3], N[3];
+};
 
-// AC2 test of one candidate (entry e of L(i)) against an escalated simplex:
-// the FP32 test with y rounded from y64 (filtered mode), then FP64, then exact
-// integers with the symbolic perturbation. True if the candidate violates AC2.
-__device__ __forceinline__ bool resolve_one(const LocalArgs& A, int e, int64_t off, const int4& Pi, long long Wi,
-                                            int gi, int nv, const int* v, const long long (*q)[3], const long long* a,
-                                            const long long* sv, const int* gv, long long det, long long g11,
-                                            long long g22, long long g12, long long n1, long long n2,
-                                            const long long (*C)[3], const long long* N, bool f32, const float* yf,
-                                            float E32, const double* y, double E, unsigned& n32, unsigned& n64,
-                                            unsigned& nx) {
-    const long long Aq = A.pc.A;
-    const int x = A.nb[off + e];
-    if (x == v[0] || (nv >= 2 && x == v[1]) || (nv == 3 && x == v[2])) return false;
-    const int4 Px = A.Ps[x];
-    const long long sx = (long long)Px.w + Aq;
-    const long long qx[3] = {(long long)Px.x - Pi.x, (long long)Px.y - Pi.y, (long long)Px.z - Pi.z};
-    bool adj = true;
-    for (int t = 0; t < nv && adj; t++) {
-        // both points lie within 2h <= 2^13 quanta of p_i: differences below 2^14, squares in 32 bits
-        const int dx = (int)(qx[0] - q[t][0]), dy = (int)(qx[1] - q[t][1]), dz = (int)(qx[2] - q[t][2]);
-        adj = meet((long long)(dx * dx + dy * dy + dz * dz), sv[t], sx);
+__device__ __forceinline__ void make_minors(const LocalArgs& A, const int4& Pi, const int* v, int nv, Minors& M) {
+    const long long Aq = A.pc.A, Wi = Pi.w;
+    for (int t = 0; t < 3; t++) {
+        M.q[t][0] = M.q[t][1] = M.q[t][2] = 0;
+        M.a[t] = M.sv[t] = 0;
+        M.gv[t] = 0;
     }
-    if (!adj) return false;
-    const long long ax = qx[0] * qx[0] + qx[1] * qx[1] + qx[2] * qx[2] - Px.w + Wi;
-    int dec = 0;
-    if (f32) {
-        // the per-atom kernel's FP32 test (same operands and operations)
-        const float t = __fmaf_rn((float)qx[2], yf[2], __fmaf_rn((float)qx[1], yf[1], __fmul_rn((float)qx[0], yf[0])));
-        const float d = __fmaf_rn(-2.0f, t, (float)ax);
-        if (d > E32) dec = 1;
-        else if (d < -E32) dec = -1;
-        if (dec) n32++;
+    for (int t = 0; t < nv; t++) {
+        const int4 P = A.Ps[v[t]];
+        M.q[t][0] = P.x - Pi.x;
+        M.q[t][1] = P.y - Pi.y;
+        M.q[t][2] = P.z - Pi.z;
+        M.a[t] = M.q[t][0] * M.q[t][0] + M.q[t][1] * M.q[t][1] + M.q[t][2] * M.q[t][2] - P.w + Wi;
+        M.sv[t] = (long long)P.w + Aq;
+        M.gv[t] = A.order[v[t]];
     }
-    if (nv >= 2 && !dec) {
-        const double t = fma((double)qx[2], y[2], fma((double)qx[1], y[1], (double)qx[0] * y[0]));
-        const double d = fma(-2.0, t, (double)ax);
-        if (d > E) dec = 1;
-        else if (d < -E) dec = -1;
-        if (dec) n64++;
+    M.det = M.g11 = M.g22 = M.g12 = M.n1 = M.n2 = 0;
+    for (int t = 0; t < 3; t++) {
+        M.N[t] = 0;
+        M.C[t][0] = M.C[t][1] = M.C[t][2] = 0;
     }
-    if (!dec) {
-        nx++;
-        const int gx = A.order[x];
-        if (nv == 1) {
-            const long long qq = q[0][0] * qx[0] + q[0][1] * qx[1] + q[0][2] * qx[2];
-            const long long vv = ax * det - a[0] * qq;  // |.| < 2^55
-            if (vv != 0) {
-                dec = vv > 0 ? 1 : -1;
-            } else {
-                const long long coef[2] = {det - qq, qq};
-                const int g[2] = {gi, gv[0]};
-                dec = sos_violates(2, g, coef, gx) ? -1 : 1;
-            }
-        } else if (nv == 2) {
-            const long long gx1 = q[0][0] * qx[0] + q[0][1] * qx[1] + q[0][2] * qx[2];
-            const long long gx2 = q[1][0] * qx[0] + q[1][1] * qx[1] + q[1][2] * qx[2];
-            const i128 vv = mul64x64(ax, det) - (mul64x64(n1, gx1) + mul64x64(n2, gx2));
-            if (vv != 0) {
-                dec = vv > 0 ? 1 : -1;
-            } else {
-                const long long c1 = g22 * gx1 - g12 * gx2, c2 = g11 * gx2 - g12 * gx1;
-                const long long coef[3] = {det - c1 - c2, c1, c2};
-                const int g[3] = {gi, gv[0], gv[1]};
-                dec = sos_violates(3, g, coef, gx) ? -1 : 1;
-            }
-        } else {
-            const int sD = det > 0 ? 1 : -1;
-            i128 vv = mul64x64(ax, det) - (mul64x64(qx[0], N[0]) + mul64x64(qx[1], N[1]) + mul64x64(qx[2], N[2]));
-            if (sD < 0) vv = -vv;
-            if (vv != 0) {
-                dec = vv > 0 ? 1 : -1;
-            } else {
-                const long long D1 = qx[0] * C[0][0] + qx[1] * C[0][1] + qx[2] * C[0][2];
-                const long long D2 = qx[0] * C[1][0] + qx[1] * C[1][1] + qx[2] * C[1][2];
-                const long long D3 = qx[0] * C[2][0] + qx[1] * C[2][1] + qx[2] * C[2][2];
-                const long long coef[4] = {sD * (det - D1 - D2 - D3), sD * D1, sD * D2, sD * D3};
-                const int g[4] = {gi, gv[0], gv[1], gv[2]};
-                dec = sos_violates(4, g, coef, gx) ? -1 : 1;
-            }
+    const long long(*q)[3] = M.q;
+    if (nv == 1) {
+        M.det = q[0][0] * q[0][0] + q[0][1] * q[0][1] + q[0][2] * q[0][2];
+    } else if (nv == 2) {
+        M.g11 = q[0][0] * q[0][0] + q[0][1] * q[0][1] + q[0][2] * q[0][2];
+        M.g22 = q[1][0] * q[1][0] + q[1][1] * q[1][1] + q[1][2] * q[1][2];
+        M.g12 = q[0][0] * q[1][0] + q[0][1] * q[1][1] + q[0][2] * q[1][2];
+        M.det = M.g11 * M.g22 - M.g12 * M.g12;
+        M.n1 = M.g22 * M.a[0] - M.g12 * M.a[1];
+        M.n2 = M.g11 * M.a[1] - M.g12 * M.a[0];
+    } else {
+        for (int t = 0; t < 3; t++) {
+            const long long* b = q[(t + 1) % 3];
+            const long long* e = q[(t + 2) % 3];
+            M.C[t][0] = b[1] * e[2] - b[2] * e[1];
+            M.C[t][1] = b[2] * e[0] - b[0] * e[2];
+            M.C[t][2] = b[0] * e[1] - b[1] * e[0];
         }
+        M.det = q[0][0] * M.C[0][0] + q[0][1] * M.C[0][1] + q[0][2] * M.C[0][2];
+        for (int c = 0; c < 3; c++) M.N[c] = M.a[0] * M.C[0][c] + M.a[1] * M.C[1][c] + M.a[2] * M.C[2][c];
     }
-    return dec < 0;
 }
 
-// Escalated simplex j, settled by the RESOLVE_LANES lanes of gmask (sub is this
-// lane's place among them): each works out the exact minors (the same values),
-// then they share the candidates. Every return is taken by the whole group.
-__device__ __forceinline__ void resolve_item(const LocalArgs& A, int64_t j, int sub, unsigned gmask) {
-    DevCounters* cnt = A.cnt;
-    const long long Aq = A.pc.A;
+// An escalated simplex whose AC3 holds, with its orthocentre for the AC2
+// tests: yf and E32 for the FP32 test (E32 < 0: none), y and E for the FP64 test
+// (triangles and tetrahedra; an edge goes to exact integers directly).
+struct ResolveScan {
+    int i, v0, v1, v2;  // owner and vertices (sorted positions), v1 / v2 = -1 for fewer
+    float yf[3];
+    float E32;
+    double y[3];
+    double E;
+};
+static_assert(sizeof(ResolveScan) == 64, "one scan record per 64 bytes");
+
+// Pending simplex j: exact AC3 where the per-atom kernel left it open, then the
+// FP64 orthocentre from the exact minors. False when its AC3 fails.
+__device__ __forceinline__ bool prep_item(const LocalArgs& A, int64_t j, ResolveScan& r, unsigned& n_exact,
+                                          unsigned (&n_cand)[4]) {
     const int4 rec = A.pending[j];
     const bool ac3_open = rec.x < 0;
     const int i = ac3_open ? ~rec.x : rec.x;
     const int v[3] = {rec.y, rec.z, rec.w};
     const int nv = rec.z < 0 ? 1 : rec.w < 0 ? 2 : 3;
     const int4 Pi = A.Ps[i];
-    const long long Wi = Pi.w, si = Wi + Aq;
-    const int gi = A.order[i];
-    long long q[3][3] = {{0}}, a[3] = {0, 0, 0}, sv[3] = {0, 0, 0};
-    int gv[3] = {0, 0, 0};
-    for (int t = 0; t < nv; t++) {
-        const int4 P = A.Ps[v[t]];
-        q[t][0] = P.x - Pi.x;
-        q[t][1] = P.y - Pi.y;
-        q[t][2] = P.z - Pi.z;
-        a[t] = q[t][0] * q[t][0] + q[t][1] * q[t][1] + q[t][2] * q[t][2] - P.w + Wi;
-        sv[t] = (long long)P.w + Aq;
-        gv[t] = A.order[v[t]];
-    }
-    // exact minors
-    long long det = 0, g11 = 0, g22 = 0, g12 = 0, n1 = 0, n2 = 0, C[3][3] = {{0}}, N[3] = {0, 0, 0};
-    if (nv == 1) {
-        det = q[0][0] * q[0][0] + q[0][1] * q[0][1] + q[0][2] * q[0][2];
-    } else if (nv == 2) {
-        g11 = q[0][0] * q[0][0] + q[0][1] * q[0][1] + q[0][2] * q[0][2];
-        g22 = q[1][0] * q[1][0] + q[1][1] * q[1][1] + q[1][2] * q[1][2];
-        g12 = q[0][0] * q[1][0] + q[0][1] * q[1][1] + q[0][2] * q[1][2];
-        det = g11 * g22 - g12 * g12;
-        n1 = g22 * a[0] - g12 * a[1];
-        n2 = g11 * a[1] - g12 * a[0];
-    } else {
-        for (int t = 0; t < 3; t++) {
-            const long long* b = q[(t + 1) % 3];
-            const long long* e = q[(t + 2) % 3];
-            C[t][0] = b[1] * e[2] - b[2] * e[1];
-            C[t][1] = b[2] * e[0] - b[0] * e[2];
-            C[t][2] = b[0] * e[1] - b[1] * e[0];
-        }
-        det = q[0][0] * C[0][0] + q[0][1] * C[0][1] + q[0][2] * C[0][2];
-        for (int c = 0; c < 3; c++) N[c] = a[0] * C[0][c] + a[1] * C[1][c] + a[2] * C[2][c];
-    }
+    const long long si = (long long)Pi.w + A.pc.A;
+    Minors M;
+    make_minors(A, Pi, v, nv, M);
     if (ac3_open) {
-        if (sub == 0) atomicAdd(&cnt->ac3_exact, 1ull);
+        n_exact++;
         bool ok;
         if (nv == 2)
-            ok = det > 0 && mul64x64(n1, a[0]) + mul64x64(n2, a[1]) <= (i128)(4 * det) * (i128)si;
+            ok = M.det > 0 && mul64x64(M.n1, M.a[0]) + mul64x64(M.n2, M.a[1]) <= (i128)(4 * M.det) * (i128)si;
         else
-            ok = det != 0 && mul64x64(N[0], N[0]) + mul64x64(N[1], N[1]) + mul64x64(N[2], N[2]) <=
-                                 mul64x64(det, det) * (i128)(4 * si);
-        if (!ok) return;  // the whole group
-        if (sub == 0) atomicAdd(&cnt->n_cand[nv], 1ull);
-        if (A.pc.keep_candidates && sub == 0) {
+            ok = M.det != 0 && mul64x64(M.N[0], M.N[0]) + mul64x64(M.N[1], M.N[1]) + mul64x64(M.N[2], M.N[2]) <=
+                                   mul64x64(M.det, M.det) * (i128)(4 * si);
+        if (!ok) return false;
+        n_cand[nv]++;
+        if (A.pc.keep_candidates) {
             const int4 item = make_int4(i, v[0], v[1], nv == 3 ? v[2] : 0);
-            const unsigned long long slot = atomicAdd(&cnt->n_cand_out[nv], 1ull);
+            const unsigned long long slot = atomicAdd(&A.cnt->n_cand_out[nv], 1ull);
             if ((int64_t)slot < A.cap_cand[nv]) (nv == 3 ? A.cand3 : A.cand2)[slot] = item;
-            else atomicOr(&cnt->err, DERR_OVF_CAND);
+            else atomicOr(&A.cnt->err, DERR_OVF_CAND);
         }
     }
+    r.i = i;
+    r.v0 = v[0];
+    r.v1 = nv >= 2 ? v[1] : -1;
+    r.v2 = nv == 3 ? v[2] : -1;
     // FP64 orthocentre from the exact minors and its decision threshold; ey64
     // bounds |y64_c - y_c| for every c
     double y[3] = {0, 0, 0}, E = 0.0, ey64 = 0.0;
     if (nv == 2) {
-        const double rd = 1.0 / (2.0 * (double)det);
-        const double m1 = (double)n1 * rd, m2 = (double)n2 * rd;
+        const double rd = 1.0 / (2.0 * (double)M.det);
+        const double m1 = (double)M.n1 * rd, m2 = (double)M.n2 * rd;
         double e = 0.0;
         for (int c = 0; c < 3; c++) {
-            y[c] = fma(m1, (double)q[0][c], m2 * (double)q[1][c]);
-            e += fabs(m1) * fabs((double)q[0][c]) + fabs(m2) * fabs((double)q[1][c]);
+            y[c] = fma(m1, (double)M.q[0][c], m2 * (double)M.q[1][c]);
+            e += fabs(m1) * fabs((double)M.q[0][c]) + fabs(m2) * fabs((double)M.q[1][c]);
         }
         e *= 6.05 * 1.1102230246251565e-16 * (1.0 + 1e-10);
         ey64 = e;
         E = (A.tri_k0_64 + A.tri_k1_64 * e) * (1.0 + 1e-10);
     } else if (nv == 3) {
-        const double rd = 1.0 / (2.0 * (double)det);
-        for (int c = 0; c < 3; c++) y[c] = (double)N[c] * rd;
+        const double rd = 1.0 / (2.0 * (double)M.det);
+        for (int c = 0; c < 3; c++) y[c] = (double)M.N[c] * rd;
         ey64 = 4.0002 * 1.1102230246251565e-16 * fmax(fabs(y[0]), fmax(fabs(y[1]), fabs(y[2])));
         E = A.tet_eps64;
     }
     // filtered mode: an FP32 test first, with y rounded to FP32 from y64 and the
     // per-atom kernel's FP32 threshold for |y~_c - y_c| <= ey32, where
     // |y32_c - y_c| <= u32 |y64_c| + ey64 <= 1.0001 u32 |y32_c| + ey64
-    const bool f32 = A.pc.precision == AC_PRECISION_FILTERED && nv >= 2;
-    float yf[3] = {0.f, 0.f, 0.f}, E32 = 0.f;
-    if (f32) {
+    r.E32 = -1.0f;
+    r.yf[0] = r.yf[1] = r.yf[2] = 0.0f;
+    if (A.pc.precision == AC_PRECISION_FILTERED && nv >= 2) {
         double ymax = 0.0;
         for (int c = 0; c < 3; c++) {
-            yf[c] = __double2float_rn(y[c]);
-            ymax = fmax(ymax, fabs((double)yf[c]));
+            r.yf[c] = __double2float_rn(y[c]);
+            ymax = fmax(ymax, fabs((double)r.yf[c]));
         }
         const double ey32 = 1.0001 * 5.9604644775390625e-08 * ymax + ey64;
         const double e32 = ((double)A.b32.K1 * ey32 + (double)A.b32.K0) * (double)A.b32.up1 * (1.0 + 1e-6);
-        E32 = __double2float_ru(e32);
+        r.E32 = __double2float_ru(e32);
     }
-    // candidates: neighbours of i adjacent to every vertex
-    const int64_t off = A.nb_stride ? (int64_t)i * A.nb_stride : A.nb_off[i];
-    const int m = A.nb_stride ? min((int)A.nb_off[i], A.nb_stride) : (int)(A.nb_off[i + 1] - off);
-    unsigned n32 = 0, n64 = 0, nx = 0;
-    bool violated = false;
-    for (int e0 = 0; e0 < m; e0 += RESOLVE_LANES) {
-        const int e = e0 + sub;
-        bool viol = false;
-        if (e < m) viol = resolve_one(A, e, off, Pi, Wi, gi, nv, v, q, a, sv, gv, det, g11, g22, g12, n1, n2, C, N, f32, yf,
-                                      E32, y, E, n32, n64, nx);
-        if (__any_sync(gmask, viol)) {
-            violated = true;
-            break;
-        }
+    for (int c = 0; c < 3; c++) r.y[c] = y[c];
+    r.E = E;
+    return true;
+}
+
+// One thread per pending simplex (the FP64 and 128-bit work at full lane
+// occupancy); the simplices whose AC3 holds go to the scan list. n_pending < 0:
+// the count the per-atom pass left on the device.
+__global__ void __launch_bounds__(128, 4) k_resolve_prep(LocalArgs A, int64_t n_pending, ResolveScan* __restrict__ scan) {
+    DevCounters* cnt = A.cnt;
+    const int lane = threadIdx.x & 31;
+    const int64_t np = n_pending >= 0 ? n_pending
+                                      : (int64_t)min(cnt->n_pending, (unsigned long long)A.cap_pending);
+    unsigned n_exact = 0, n_cand[4] = {0, 0, 0, 0};
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    // whole warps step together, so the append below is warp-aggregated
+    for (int64_t j0 = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); j0 < np; j0 += stride) {
+        const int64_t j = j0 + lane;
+        ResolveScan r;
+        const bool keep = j < np && prep_item(A, j, r, n_exact, n_cand);
+        const unsigned b = __ballot_sync(FULL, keep);
+        if (!b) continue;
+        unsigned long long base = 0;
+        if (lane == 0) base = atomicAdd(&cnt->n_scan, (unsigned long long)__popc(b));
+        base = __shfl_sync(FULL, base, 0);
+        if (keep) scan[base + __popc(b & lanemask_lt())] = r;  // at most n_pending <= the list's capacity
     }
-    n32 = __reduce_add_sync(gmask, n32);
-    n64 = __reduce_add_sync(gmask, n64);
-    nx = __reduce_add_sync(gmask, nx);
-    if (sub != 0) return;
-    if (nv == 3) {
-        if (n32) atomicAdd(&cnt->ac2_tet[0], (unsigned long long)n32);
-        if (n64) atomicAdd(&cnt->ac2_tet[1], (unsigned long long)n64);
-        if (nx) atomicAdd(&cnt->ac2_tet[2], (unsigned long long)nx);
-    } else if (nv == 2) {
-        if (n32) atomicAdd(&cnt->ac2_tri[0], (unsigned long long)n32);
-        if (n64) atomicAdd(&cnt->ac2_tri[1], (unsigned long long)n64);
-        if (nx) atomicAdd(&cnt->ac2_tri[2], (unsigned long long)nx);
-    } else {
-        atomicAdd(&cnt->ac2_edge, (unsigned long long)(n64 + nx));
-    }
-    if (violated) return;
-    if (nv == 3) {
-        const unsigned long long slot = atomicAdd(&cnt->n_tet_out, 1ull);
-        if ((int64_t)slot < A.cap_tet) A.tet_out[slot] = make_int4(i, v[0], v[1], v[2]);
-        else atomicOr(&cnt->err, DERR_OVF_TET);
-    } else if (nv == 2) {
-        const unsigned long long slot = atomicAdd(&cnt->n_tri_pass, 1ull);
-        if ((int64_t)slot < A.cap_tri) A.tri_out[slot] = make_int4(i, v[0], v[1], 0);
-        else atomicOr(&cnt->err, DERR_OVF_TRI);
-    } else {
-        const unsigned long long slot = atomicAdd(&cnt->n_edge_pass, 1ull);
-        if ((int64_t)slot < A.cap_edge) A.edge_out[slot] = make_int2(i, v[0]);
-        else atomicOr(&cnt->err, DERR_OVF_EDGE);
+    n_exact = __reduce_add_sync(FULL, n_exact);
+    n_cand[2] = __reduce_add_sync(FULL, n_cand[2]);
+    n_cand[3] = __reduce_add_sync(FULL, n_cand[3]);
+    if (lane == 0) {
+        if (n_exact) atomicAdd(&cnt->ac3_exact, (unsigned long long)n_exact);
+        if (n_cand[2]) atomicAdd(&cnt->n_cand[2], (unsigned long long)n_cand[2]);
+        if (n_cand[3]) atomicAdd(&cnt->n_cand[3], (unsigned long long)n_cand[3]);
     }
 }
 
-// One group of RESOLVE_LANES lanes per escalated simplex, grid-stride over the
-// list. n_pending < 0: the count the per-atom pass left on the device (at most
-// the list's capacity), so a synchronised build need not read it first.
-__global__ void __launch_bounds__(128) k_resolve(LocalArgs A, int64_t n_pending) {
-    const int sub = threadIdx.x % RESOLVE_LANES;
-    const unsigned gmask = ((1u << RESOLVE_LANES) - 1u) << ((threadIdx.x & 31) & ~(RESOLVE_LANES - 1));
-    const int64_t np = n_pending >= 0 ? n_pending
-                                      : (int64_t)min(A.cnt->n_pending, (unsigned long long)A.cap_pending);
+// Exact AC2 decision for candidate x (offset qx from p_i, a_x = ax) against the
+// escalated simplex (i, v): the sign of Delta_x times the orthocentre's
+// denominator in 128-bit integers, and the symbolic perturbation when it is
+// zero. Out of line: the FP32 and FP64 tests settle nearly every case.
+__device__ __noinline__ bool exact_violates(const LocalArgs& A, int i, const int* v, int nv, int x,
+                                            const long long* qx, long long ax) {
+    const int4 Pi = A.Ps[i];
+    Minors M;
+    make_minors(A, Pi, v, nv, M);
+    const long long(*q)[3] = M.q;
+    const int gi = A.order[i], gx = A.order[x];
+    if (nv == 1) {
+        const long long qq = q[0][0] * qx[0] + q[0][1] * qx[1] + q[0][2] * qx[2];
+        const long long vv = ax * M.det - M.a[0] * qq;  // |.| < 2^55
+        if (vv != 0) return vv < 0;
+        const long long coef[2] = {M.det - qq, qq};
+        const int g[2] = {gi, M.gv[0]};
+        return sos_violates(2, g, coef, gx);
+    }
+    if (nv == 2) {
+        const long long gx1 = q[0][0] * qx[0] + q[0][1] * qx[1] + q[0][2] * qx[2];
+        const long long gx2 = q[1][0] * qx[0] + q[1][1] * qx[1] + q[1][2] * qx[2];
+        const i128 vv = mul64x64(ax, M.det) - (mul64x64(M.n1, gx1) + mul64x64(M.n2, gx2));
+        if (vv != 0) return vv < 0;
+        const long long c1 = M.g22 * gx1 - M.g12 * gx2, c2 = M.g11 * gx2 - M.g12 * gx1;
+        const long long coef[3] = {M.det - c1 - c2, c1, c2};
+        const int g[3] = {gi, M.gv[0], M.gv[1]};
+        return sos_violates(3, g, coef, gx);
+    }
+    const int sD = M.det > 0 ? 1 : -1;
+    i128 vv = mul64x64(ax, M.det) - (mul64x64(qx[0], M.N[0]) + mul64x64(qx[1], M.N[1]) + mul64x64(qx[2], M.N[2]));
+    if (sD < 0) vv = -vv;
+    if (vv != 0) return vv < 0;
+    const long long D1 = qx[0] * M.C[0][0] + qx[1] * M.C[0][1] + qx[2] * M.C[0][2];
+    const long long D2 = qx[0] * M.C[1][0] + qx[1] * M.C[1][1] + qx[2] * M.C[1][2];
+    const long long D3 = qx[0] * M.C[2][0] + qx[1] * M.C[2][1] + qx[2] * M.C[2][2];
+    const long long coef[4] = {sD * (M.det - D1 - D2 - D3), sD * D1, sD * D2, sD * D3};
+    const int g[4] = {gi, M.gv[0], M.gv[1], M.gv[2]};
+    return sos_violates(4, g, coef, gx);
+}
+
+__device__ __forceinline__ bool meet(long long D, long long s1, long long s2) {
+    const long long t = D - s1 - s2;
+    return t <= 0 || t * t <= 4 * s1 * s2;
+}
+
+// The AC2 tests of the scan list: RESOLVE_LANES lanes per simplex share the
+// entries of L(i), each candidate adjacent to every vertex tested in FP32
+// (filtered mode), then FP64, then exact integers; the group stops at the
+// first violator. Survivors join the output lists.
+__global__ void __launch_bounds__(128) k_resolve_scan(LocalArgs A, const ResolveScan* __restrict__ scan) {
+    DevCounters* cnt = A.cnt;
+    const int lane = threadIdx.x & 31, sub = lane % RESOLVE_LANES;
+    const unsigned gmask = ((1u << RESOLVE_LANES) - 1u) << (lane & ~(RESOLVE_LANES - 1));
+    const int64_t ns = (int64_t)min(cnt->n_scan, (unsigned long long)A.cap_pending);
+    const long long Aq = A.pc.A;
+    unsigned c32[4] = {0, 0, 0, 0}, c64[4] = {0, 0, 0, 0}, cx[4] = {0, 0, 0, 0};  // by vertex count
     const int64_t groups = (int64_t)gridDim.x * blockDim.x / RESOLVE_LANES;
-    for (int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / RESOLVE_LANES; j < np; j += groups)
-        resolve_item(A, j, sub, gmask);
+    for (int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / RESOLVE_LANES; j < ns; j += groups) {
+        const ResolveScan r = scan[j];
+        const int v[3] = {r.v0, r.v1, r.v2};
+        const int nv = r.v1 < 0 ? 1 : r.v2 < 0 ? 2 : 3;
+        const int4 Pi = A.Ps[r.i];
+        const long long Wi = Pi.w;
+        int qv[3][3];  // vertex offsets from p_i: below 2^14 in magnitude
+        long long sv[3];
+        for (int t = 0; t < 3; t++) {
+            const int4 P = A.Ps[t < nv ? v[t] : r.i];
+            qv[t][0] = P.x - Pi.x;
+            qv[t][1] = P.y - Pi.y;
+            qv[t][2] = P.z - Pi.z;
+            sv[t] = (long long)P.w + Aq;
+        }
+        const int64_t off = A.nb_stride ? (int64_t)r.i * A.nb_stride : A.nb_off[r.i];
+        const int m = A.nb_stride ? min((int)A.nb_off[r.i], A.nb_stride) : (int)(A.nb_off[r.i + 1] - off);
+        bool violated = false;
+        for (int e0 = 0; e0 < m; e0 += RESOLVE_LANES) {
+            const int e = e0 + sub;
+            bool viol = false;
+            if (e < m) {
+                const int x = A.nb[off + e];
+                if (x != v[0] && x != v[1] && x != v[2]) {
+                    const int4 Px = A.Ps[x];
+                    const long long sx = (long long)Px.w + Aq;
+                    const int qx0 = Px.x - Pi.x, qx1 = Px.y - Pi.y, qx2 = Px.z - Pi.z;
+                    bool adj = true;
+                    for (int t = 0; t < nv && adj; t++) {
+                        // both points lie within 2h <= 2^13 quanta of p_i: differences below 2^14
+                        const int dx = qx0 - qv[t][0], dy = qx1 - qv[t][1], dz = qx2 - qv[t][2];
+                        adj = meet((long long)(dx * dx + dy * dy + dz * dz), sv[t], sx);
+                    }
+                    if (adj) {
+                        const long long ax = (long long)qx0 * qx0 + (long long)qx1 * qx1 + (long long)qx2 * qx2 - Px.w + Wi;
+                        int dec = 0;
+                        if (r.E32 >= 0.0f) {
+                            // the per-atom kernel's FP32 test (same operands and operations)
+                            const float t = __fmaf_rn((float)qx2, r.yf[2],
+                                                      __fmaf_rn((float)qx1, r.yf[1], __fmul_rn((float)qx0, r.yf[0])));
+                            const float d = __fmaf_rn(-2.0f, t, (float)ax);
+                            if (d > r.E32) dec = 1;
+                            else if (d < -r.E32) dec = -1;
+                            if (dec) c32[nv]++;
+                        }
+                        if (nv >= 2 && !dec) {
+                            const double t = fma((double)qx2, r.y[2], fma((double)qx1, r.y[1], (double)qx0 * r.y[0]));
+                            const double d = fma(-2.0, t, (double)ax);
+                            if (d > r.E) dec = 1;
+                            else if (d < -r.E) dec = -1;
+                            if (dec) c64[nv]++;
+                        }
+                        if (!dec) {
+                            cx[nv]++;
+                            const long long qx[3] = {qx0, qx1, qx2};
+                            dec = exact_violates(A, r.i, v, nv, x, qx, ax) ? -1 : 1;
+                        }
+                        viol = dec < 0;
+                    }
+                }
+            }
+            if (__any_sync(gmask, viol)) {
+                violated = true;
+                break;
+            }
+        }
+        if (violated || sub != 0) continue;
+        if (nv == 3) {
+            const unsigned long long slot = atomicAdd(&cnt->n_tet_out, 1ull);
+            if ((int64_t)slot < A.cap_tet) A.tet_out[slot] = make_int4(r.i, v[0], v[1], v[2]);
+            else atomicOr(&cnt->err, DERR_OVF_TET);
+        } else if (nv == 2) {
+            const unsigned long long slot = atomicAdd(&cnt->n_tri_pass, 1ull);
+            if ((int64_t)slot < A.cap_tri) A.tri_out[slot] = make_int4(r.i, v[0], v[1], 0);
+            else atomicOr(&cnt->err, DERR_OVF_TRI);
+        } else {
+            const unsigned long long slot = atomicAdd(&cnt->n_edge_pass, 1ull);
+            if ((int64_t)slot < A.cap_edge) A.edge_out[slot] = make_int2(r.i, v[0]);
+            else atomicOr(&cnt->err, DERR_OVF_EDGE);
+        }
+    }
+    // counters: one atomic per warp and level
+    unsigned red[7] = {c32[3], c64[3], cx[3], c32[2], c64[2], cx[2], cx[1] + c64[1] + c32[1]};
+#pragma unroll
+    for (int t = 0; t < 7; t++) red[t] = __reduce_add_sync(FULL, red[t]);
+    if (lane == 0) {
+        for (int k = 0; k < 3; k++) {
+            if (red[k]) atomicAdd(&cnt->ac2_tet[k], (unsigned long long)red[k]);
+            if (red[3 + k]) atomicAdd(&cnt->ac2_tri[k], (unsigned long long)red[3 + k]);
+        }
+        if (red[6]) atomicAdd(&cnt->ac2_edge, (unsigned long long)red[6]);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -1430,17 +1511,18 @@ static void set_constants(const PredConst& pc, int64_t wmax, LocalArgs& a) {
     a.tri_k1_64 = nextafter((2 * g3d * H + 2 * H) * s3 * sf * (1 + 1e-12), INFINITY);
 }
 
-// blocks of k_resolve for up to `items` escalated simplices: one group per
-// simplex, at most four resident waves of the device (the kernel strides over
-// the rest, so the cap only bounds the blocks that start with nothing to do)
-static unsigned resolve_blocks(int64_t items) {
+// blocks of a resolve kernel for up to `items` escalated simplices: `lanes`
+// threads per simplex, at most four resident waves of the device (the kernels
+// stride over the rest, so the cap only bounds the blocks that start with
+// nothing to do)
+static unsigned resolve_blocks(int64_t items, int lanes) {
     static int sms = 0;
     if (sms == 0) {
         int dev = 0;
         if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0)
             sms = 152;
     }
-    const int64_t want = (items * RESOLVE_LANES + 127) / 128;
+    const int64_t want = (items * lanes + 127) / 128;
     return (unsigned)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)sms * 16 * 4));
 }
 
@@ -1473,6 +1555,8 @@ int run_local(ac_ctx* c, cudaStream_t s) {
         AC_TRY(c->tri_pass.reserve((size_t)c->cap_tri * sizeof(int4), s));
         AC_TRY(c->edge_pass.reserve((size_t)c->cap_edge * sizeof(int2), s));
         AC_TRY(c->pending.reserve((size_t)c->cap_pending * sizeof(int4), s));
+        AC_TRY(c->resolve_scan.reserve((size_t)c->cap_pending * sizeof(ResolveScan), s));
+        ResolveScan* scan = c->resolve_scan.as<ResolveScan>();
         AC_TRY(c->vert_pass.reserve(nn, s));
         if (c->pc.keep_candidates) {
             AC_TRY(c->cand[1].reserve((size_t)c->cap_cand[1] * sizeof(int2), s));
@@ -1519,7 +1603,9 @@ int run_local(ac_ctx* c, cudaStream_t s) {
             const BuildRecord& r = c->rec;
             AC_TRY(expect_u64(c, &dc->n_pending, (unsigned long long)r.n_pending, s));
             if (r.n_pending > 0) {
-                k_resolve<<<resolve_blocks(r.n_pending), 128, 0, s>>>(a, r.n_pending);
+                k_resolve_prep<<<resolve_blocks(r.n_pending, 1), 128, 0, s>>>(a, r.n_pending, scan);
+                AC_LAUNCHED();
+                k_resolve_scan<<<resolve_blocks(r.n_pending, RESOLVE_LANES), 128, 0, s>>>(a, scan);
                 AC_LAUNCHED();
             }
             AC_TRY(expect_u64(c, &dc->n_tet_out, r.post.n_tet_out, s));
@@ -1529,9 +1615,11 @@ int run_local(ac_ctx* c, cudaStream_t s) {
             c->hc = r.post;
             return AC_OK;
         }
-        // the resolve kernel sized by the list's capacity, reading the count on the device: one host wait
+        // the resolve kernels sized by the list's capacity, reading the count on the device: one host wait
         if (c->cap_pending > 0) {
-            k_resolve<<<resolve_blocks(c->cap_pending), 128, 0, s>>>(a, -1);
+            k_resolve_prep<<<resolve_blocks(c->cap_pending, 1), 128, 0, s>>>(a, -1, scan);
+            AC_LAUNCHED();
+            k_resolve_scan<<<resolve_blocks(c->cap_pending, RESOLVE_LANES), 128, 0, s>>>(a, scan);
             AC_LAUNCHED();
         }
         AC_TRY(read_counters(c, &h, s));
