@@ -73,7 +73,11 @@ struct IdleBlock {
 static std::mutex g_idle_mu;
 static std::multimap<size_t, IdleBlock> g_idle;  // by size
 static size_t g_idle_bytes = 0;
-static constexpr size_t IDLE_KEEP_BYTES = 8ull << 30;
+// Only blocks up to IDLE_MAX_BLOCK are kept: the allocation calls saved are per
+// buffer, and a large block held here is memory the pool cannot hand to a
+// context of another size.
+static constexpr size_t IDLE_KEEP_BYTES = 2ull << 30;
+static constexpr size_t IDLE_MAX_BLOCK = 64ull << 20;
 static constexpr size_t IDLE_KEEP_BLOCKS = 1024;
 static thread_local bool g_release_idle = false;  // set by ac_destroy once the device is idle
 
@@ -83,6 +87,7 @@ static bool idle_give(void* p, size_t bytes) {
         cudaGetLastError();
         return false;
     }
+    if (bytes > IDLE_MAX_BLOCK) return false;
     std::lock_guard<std::mutex> g(g_idle_mu);
     if (g_idle_bytes + bytes > IDLE_KEEP_BYTES || g_idle.size() >= IDLE_KEEP_BLOCKS) return false;
     g_idle.emplace(bytes, IdleBlock{p, dev});
@@ -92,6 +97,7 @@ static bool idle_give(void* p, size_t bytes) {
 
 // The smallest idle block of this device with want..2 want + 1 MB bytes, or null.
 static void* idle_take(size_t want, size_t* got) {
+    if (want > IDLE_MAX_BLOCK) return nullptr;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) {
         cudaGetLastError();
