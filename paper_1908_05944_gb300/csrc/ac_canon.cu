@@ -798,12 +798,16 @@ __global__ void k_tri_mark(TriMarkArgs a) {
 constexpr int TW_WARPS = 4;
 constexpr int TW_CAP = 256;  // marked pairs ranked in shared memory; more take the slow path
 
-__device__ __forceinline__ void pair_of(int64_t bit, int& p, int& q) {
+// The pair (p, q), p < q, of pair-mask bit q (q - 1) / 2 + p. Rows hold at most
+// MAX_DEGREE entries, so bit < 2^19: 32-bit arithmetic throughout (a 64-bit
+// integer conversion would run on the narrow FP64 pipe).
+static_assert((int64_t)MAX_DEGREE * (MAX_DEGREE - 1) / 2 < (1 << 24), "pair bits exact in FP32");
+__device__ __forceinline__ void pair_of(int bit, int& p, int& q) {
     int x = (int)((1.0f + sqrtf(1.0f + 8.0f * (float)bit)) * 0.5f);
-    while ((int64_t)x * (x - 1) / 2 > bit) x--;
-    while ((int64_t)(x + 1) * x / 2 <= bit) x++;
+    while (x * (x - 1) / 2 > bit) x--;
+    while ((x + 1) * x / 2 <= bit) x++;
     q = x;
-    p = (int)(bit - (int64_t)q * (q - 1) / 2);
+    p = bit - q * (q - 1) / 2;
 }
 
 __global__ void __launch_bounds__(TW_WARPS * 32) k_tri_write(TriMarkArgs a, int64_t n, const int64_t* __restrict__ uoff,
@@ -827,7 +831,7 @@ __global__ void __launch_bounds__(TW_WARPS * 32) k_tri_write(TriMarkArgs a, int6
     const int base = (int)mol_off[mol_of[g]];
     auto key_of = [&](int64_t bit) {
         int p, q;
-        pair_of(bit, p, q);
+        pair_of((int)bit, p, q);
         const unsigned hb = (unsigned)a.order[a.nb[off + p]], hc = (unsigned)a.order[a.nb[off + q]];
         return hb < hc ? ((unsigned long long)hb << 32) | hc : ((unsigned long long)hc << 32) | hb;
     };
