@@ -113,7 +113,9 @@ typedef struct {
  * alpha (Section 2.4). Copies and quantises the input; the caller keeps its
  * buffers. centres: n x 3 row-major doubles (A); radii: n doubles (A), both
  * host or device. opt may be NULL.
- * Ranges checked here (else AC_ERR_RANGE): |coordinate| <= 2^20 A, and
+ * Ranges checked here (else AC_ERR_RANGE): |coordinate| < 2^20 A (below 2^30
+ * quanta of 1/1024 A after rounding to the nearest quantum, so that any two
+ * coordinates differ by less than 2^31 quanta), and
  * r_max^2 + alpha <= 16 A^2 (h = sqrt(r_max^2 + alpha) <= 4 A keeps every
  * predicate inside 128-bit integers). n must be below 2^31.
  * Errors: AC_ERR_INVALID_ARG (NULL out, n < 0, NaN/Inf, radius <= 0),

@@ -460,7 +460,7 @@ __global__ void k_quantise(const double* __restrict__ centres, const double* __r
     if (i < n) {
         double x = centres[3 * i], y = centres[3 * i + 1], z = centres[3 * i + 2], r = radii[i];
         bool finite = isfinite(x) && isfinite(y) && isfinite(z) && isfinite(r);
-        const double lim = 1048576.0;  // |x| <= 2^20 A keeps quantised coordinates within 2^30
+        const double lim = 1048576.0;  // |x| <= 2^20 A: the quantised coordinate fits 32 bits
         uint32_t bad = 0;
         if (!finite || !(r > 0.0)) {
             bad = DERR_INVALID;
@@ -471,8 +471,11 @@ __global__ void k_quantise(const double* __restrict__ centres, const double* __r
             Y = __double2int_rn(y * 1024.0);
             Z = __double2int_rn(z * 1024.0);
             const int R = __double2int_rn(r * 1024.0);
-            // radius quantised to 0, or above 4 A (W would leave the 2^24 range of the predicates)
-            if (R < 1 || R > 4096) bad = DERR_RANGE;
+            // |X| < 2^30 keeps every difference of two coordinates (a grid offset) within 32 bits;
+            // a radius quantised to 0, or above 4 A, would take W out of the 2^24 range of the predicates
+            const int cmax = (1 << 30) - 1;
+            if (X > cmax || X < -cmax || Y > cmax || Y < -cmax || Z > cmax || Z < -cmax || R < 1 || R > 4096)
+                bad = DERR_RANGE;
             else W = R * R;
         }
         if (bad) {
@@ -608,7 +611,7 @@ int quantise_and_plan(ac_ctx* c, cudaStream_t s) {
     }
     if (hc.err & DERR_RANGE) {
         char b[160];
-        snprintf(b, sizeof(b), "atom %d: |coordinate| > 2^20 A or radius outside (0, 4] A after quantisation",
+        snprintf(b, sizeof(b), "atom %d: |coordinate| >= 2^20 A or radius outside (0, 4] A after quantisation",
                  hc.bad_index);
         return fail(AC_ERR_RANGE, b);
     }

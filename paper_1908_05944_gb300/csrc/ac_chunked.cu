@@ -104,7 +104,9 @@ int quantise_z(const double* centres, const double* radii, int64_t n, double alp
                 continue;
             }
             const int64_t R = (int64_t)std::nearbyint(r * 1024.0);
-            if (R < 1 || R > 4096) {
+            const double cq = 1073741823.0;  // |quantised coordinate| < 2^30, as the device build requires
+            if (R < 1 || R > 4096 || std::fabs(std::nearbyint(x * 1024.0)) > cq || std::fabs(std::nearbyint(y * 1024.0)) > cq ||
+                std::fabs(std::nearbyint(z * 1024.0)) > cq) {
                 if (q.bad_range < 0) q.bad_range = i;
                 continue;
             }
@@ -130,7 +132,7 @@ int quantise_z(const double* centres, const double* radii, int64_t n, double alp
         return fail(AC_ERR_INVALID_ARG, b);
     }
     if (bad_range >= 0) {
-        snprintf(b, sizeof(b), "atom %lld: |coordinate| > 2^20 A or radius outside (0, 4] A after quantisation",
+        snprintf(b, sizeof(b), "atom %lld: |coordinate| >= 2^20 A or radius outside (0, 4] A after quantisation",
                  (long long)bad_range);
         return fail(AC_ERR_RANGE, b);
     }

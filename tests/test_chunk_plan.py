@@ -120,3 +120,20 @@ def test_plan_large_input_matches_greedy_cut():
     with pytest.raises(ac.AlphacError) as e:
         ac.chunk_plan(bad, r, 0.0, max_core)
     assert "atom 90001" in str(e.value)
+
+
+def test_plan_coordinate_range():
+    """Coordinates must quantise below 2^30 quanta (|x| < 2^20 A), so any two differ by less than 2^31."""
+    import paper_1908_05944_gb300 as ac
+
+    c, r = synth.globule(6, 50, probe=False)
+    for edge in (1048575.0, -1048575.0, 1048576.0 - 1.0 / 1024.0):
+        ok = c.copy()
+        ok[3, 0] = edge  # 2^30 - 1024 and 2^30 - 1 quanta: accepted
+        ac.chunk_plan(ok, r, 0.0, 10)
+    for edge in (1048576.0, -1048576.0, 1048576.0 - 1.0 / 4096.0):
+        bad = c.copy()
+        bad[3, 2] = edge  # 2^30 quanta after rounding: refused
+        with pytest.raises(ac.AlphacError) as e:
+            ac.chunk_plan(bad, r, 0.0, 10)
+        assert e.value.code == ac.AC_ERR_RANGE and "atom 3" in str(e.value)

@@ -179,6 +179,28 @@ def test_other_alphas(alpha):
     assert_same_complex(run_gpu(c, r, alpha), ref)
 
 
+def test_coordinate_range_limits():
+    """Two clusters centred at x = -(2^20 - 16) A and +(2^20 - 16) A (quantised coordinates just below
+    2^30 in magnitude, the extremes less than 2^31 apart) build and equal the oracle; a coordinate that
+    rounds to 2^30 quanta is refused."""
+    import paper_1908_05944_gb300 as ac
+
+    parts = []
+    for k, sx in enumerate((-1.0, 1.0)):
+        c, r = synth.globule(80 + k, 120, probe=True)
+        parts.append((c + np.array([sx * 1048560.0, 0.0, 0.0]), r))
+    c = np.concatenate([p[0] for p in parts])
+    r = np.concatenate([p[1] for p in parts])
+    assert np.abs(np.rint(c * 1024)).max() < 2**30
+    assert_same_complex(run_gpu(c, r, 0.0), oracle.alpha_complex(c, r, 0.0))
+    for edge in (1048576.0, -1048576.0, 1048576.0 - 1.0 / 4096.0):
+        bad = c.copy()
+        bad[5, 1] = edge
+        with pytest.raises(ac.AlphacError) as e:
+            run_gpu(bad, r, 0.0)
+        assert e.value.code == ac.AC_ERR_RANGE
+
+
 def test_error_codes():
     import paper_1908_05944_gb300 as ac
 
