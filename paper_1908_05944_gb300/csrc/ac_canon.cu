@@ -21,6 +21,7 @@
 #include <type_traits>
 
 #include "ac_internal.cuh"
+#include "ac_round.h"
 
 namespace ac {
 
@@ -1082,24 +1083,18 @@ void finish_mol_rows(ac_ctx* c) {
 // ---------------------------------------------------------------------------
 // OrthoSize (exact) and Size
 
-__device__ __forceinline__ double i128_to_double(i128 x) {
-    bool neg = x < 0;
-    unsigned __int128 u = neg ? (unsigned __int128)(-x) : (unsigned __int128)x;
-    unsigned long long hi = (unsigned long long)(u >> 64), lo = (unsigned long long)u;
-    double r = __ull2double_rn(hi) * 18446744073709551616.0 + __ull2double_rn(lo);
-    return neg ? -r : r;
-}
-
 // OrthoSize of a simplex of global input indices (ascending, K entries) as an
 // exact rational num / den in quanta^2 (den > 0).
 __device__ void orthosize_rational(const int4* __restrict__ P, const int4& t, int K, i128& num, i128& den);
 
-// OrthoSize in A^2 of a simplex of global input indices (ascending, K entries).
+// OrthoSize in A^2 of a simplex of global input indices (ascending, K entries):
+// the numerator (scaled by 2^-20, quanta^2 -> A^2) and the denominator each
+// rounded to the nearest double in integer arithmetic, then one FP64 division.
 __device__ double orthosize_exact(const int4* __restrict__ P, const int4& t, int K) {
     i128 num, den;
     orthosize_rational(P, t, K, num, den);
-    if (K == 1) return (double)(long long)num * 9.5367431640625e-07;  // 2^-20, exact
-    return i128_to_double(num) / i128_to_double(den) * 9.5367431640625e-07;
+    if (K == 1) return i128_to_double_rn(num, -20);  // exact
+    return i128_to_double_rn(num, -20) / i128_to_double_rn(den, 0);
 }
 
 __device__ void orthosize_rational(const int4* __restrict__ P, const int4& t, int K, i128& num, i128& den) {
