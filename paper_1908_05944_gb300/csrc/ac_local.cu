@@ -1512,9 +1512,9 @@ static void set_constants(const PredConst& pc, int64_t wmax, LocalArgs& a) {
 }
 
 // blocks of a resolve kernel for up to `items` escalated simplices: `lanes`
-// threads per simplex, at most four resident waves of the device (the kernels
-// stride over the rest, so the cap only bounds the blocks that start with
-// nothing to do)
+// threads per simplex, at most one wave of 16 blocks per SM (the kernels stride
+// over the rest, so the cap only bounds the blocks that start with nothing to
+// do when a first build sizes the launch by the list's capacity)
 static unsigned resolve_blocks(int64_t items, int lanes) {
     static int sms = 0;
     if (sms == 0) {
@@ -1523,7 +1523,7 @@ static unsigned resolve_blocks(int64_t items, int lanes) {
             sms = 152;
     }
     const int64_t want = (items * lanes + 127) / 128;
-    return (unsigned)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)sms * 16 * 4));
+    return (unsigned)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)sms * 16));
 }
 
 int run_local(ac_ctx* c, cudaStream_t s) {
