@@ -288,7 +288,18 @@ def time_builds(cx, steps, warmup, stream, flush):
     return ms
 
 
-def run_forms(args):
+def measured_fma_peaks():
+    """The device's FP32 and FP64 FMA throughput (TFLOP/s) from the library's probe (ac_fma_peak): independent
+    FMA chains in registers over every SM, about 50 ms per timed launch, median of three."""
+    import paper_1908_05944_gb300 as ac
+
+    out = {}
+    for name, fp64 in (("fp32_tflops", False), ("fp64_tflops", True)):
+        out[name] = float(np.median([ac.fma_peak(fp64) for _ in range(3)])) / 1e12
+    return out
+
+
+def run_forms(args, fma=None):
     """Side measurements: plain FP64 vs filtered, the 3M shell, batched vs per-molecule launches."""
     import torch
 
@@ -311,6 +322,9 @@ def run_forms(args):
         out[f"{wl}/{prec}"] = {"atoms_per_s": n * steps / (sum(ms) / 1e3), "ms_per_step": sum(ms) / steps,
                                "simplices": st["simplices"], "local_kernel_ms": loc, "local_tflops": tf,
                                "local_frac_fp32_peak_2070mhz": tf / (SMS * FP32_LANES_PER_SM * 2 * 2070e6 / 1e12)}
+        if fma:
+            out[f"{wl}/{prec}"]["local_frac_of_measured_fma"] = tf / fma["fp32_tflops" if prec == "filtered"
+                                                                         else "fp64_tflops"]
         if prec == "plain_fp64":  # its bounding roofline: the FP64 pipe
             out[f"{wl}/{prec}"]["local_frac_fp64_nominal_2070mhz"] = tf / FP64_NOMINAL_TFLOPS
         if prec == "plain_fp64":
@@ -720,6 +734,8 @@ def main():
         basis = (f"FP64: nominal {FP64_NOMINAL_TFLOPS} TFLOP/s at {MAX_SM_MHZ:.0f} MHz, scaled to the sampled "
                  f"{sm_mhz:.0f} MHz")
     achieved = res["local_flops"] / (res["local_ms"] * 1e-3) / 1e12 if res["local_ms"] > 0 else 0.0
+    fma = measured_fma_peaks()  # after the timed steps
+    measured = fma["fp32_tflops" if args.precision == "filtered" else "fp64_tflops"]
     line = {
         "metric": METRIC, "value": res["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": res["ms_per_step"], "higher_is_better": True, "scaling": "weak",
@@ -737,7 +753,10 @@ def main():
                      "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved / peak_tflops if peak_tflops else None,
                      "traffic": profiled_traffic(args.workload) if args.precision == "filtered" else None,
                      "traffic_unit": "bytes per pass (ncu dram read + write, both launches)",
-                     "peak_basis": basis},
+                     "peak_basis": basis,
+                     "peak_measured_fma": measured,
+                     "frac_of_measured_fma": achieved / measured if measured else None},
+        "fma_peaks_measured": fma,
         "stage_ms": res["stats"]["ms_stage"],
         "predicates": {"ac2_tet": res["stats"]["ac2_tests_tet"], "ac2_tri": res["stats"]["ac2_tests_tri"],
                        "ac2_edge": res["stats"]["ac2_tests_edge"], "ac3": res["stats"]["ac3_tests"]},
@@ -745,7 +764,7 @@ def main():
     if not args.no_e2e:
         line["e2e"] = run_e2e(args, rank, world, max(2, min(args.steps, 5)))
     if rank == 0 and world == 1 and not args.no_forms:
-        line["forms"] = run_forms(args)
+        line["forms"] = run_forms(args, fma)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args)
     if rank == 0:

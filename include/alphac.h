@@ -436,6 +436,18 @@ AC_API int ac_get_stats(ac_ctx* ctx, ac_stats* out);
  * output may be NULL. Errors: AC_ERR_INVALID_ARG (NULL ctx). */
 AC_API int ac_get_sizes(ac_ctx* ctx, int64_t* n_mol, int64_t* n_atoms);
 
+/* Measurement helper; the paper has no counterpart (it is not part of the
+ * method, Section 5 reports timings only): the device's FMA throughput in
+ * FP32 (fp64 = 0) or FP64 (fp64 = 1), in floating-point operations per second
+ * (an FMA counts two), from independent FMA chains in registers over a launch
+ * that fills every SM for `iters` steps per chain (one untimed launch of an
+ * eighth of them first), timed with CUDA events on `stream` (NULL: the default
+ * stream). The denominator that the per-atom kernel's arithmetic is compared
+ * with beside the peak derived from unit counts and clock. *ms (may be NULL)
+ * receives the timed launch's duration. Synchronises the stream.
+ * Errors: AC_ERR_INVALID_ARG (NULL output, iters < 1), AC_ERR_CUDA, AC_ERR_OOM. */
+AC_API int ac_fma_peak(int fp64, int iters, void* stream, double* flops_per_s, float* ms);
+
 /* Free the context and everything it owns. NULL is a no-op. */
 AC_API void ac_destroy(ac_ctx* ctx);
 

@@ -39,7 +39,8 @@ EXPORTS = ["ac_create", "ac_create_batch", "ac_build", "ac_get_simplices", "ac_f
            "ac_get_candidates", "ac_eval_filtration", "ac_eval_filtration_fp32", "ac_backward", "ac_backward_noalloc", "ac_autotune",
            "ac_subcomplex", "ac_get_simplices_host", "ac_chunk_plan", "ac_build_chunked", "ac_part_plan", "ac_build_part",
            "ac_merge_parts", "ac_chunked_simplices", "ac_chunked_info",
-           "ac_chunked_free", "ac_get_stats", "ac_get_sizes", "ac_destroy", "ac_error_string", "ac_last_error_detail"]
+           "ac_chunked_free", "ac_get_stats", "ac_get_sizes", "ac_destroy", "ac_error_string", "ac_last_error_detail",
+           "ac_fma_peak"]
 
 
 class ac_options(ctypes.Structure):
@@ -90,6 +91,7 @@ def _declare(lib):
     lib.ac_create.argtypes = [vp, vp, i64, dbl, P(ac_options), P(vp)]
     lib.ac_create_batch.argtypes = [vp, vp, vp, i64, dbl, P(ac_options), P(vp)]
     lib.ac_build.argtypes = [vp, vp]
+    lib.ac_fma_peak.argtypes = [i32, i32, vp, P(dbl), P(ctypes.c_float)]
     lib.ac_get_simplices.argtypes = [vp, i32, i64, P(vp), P(i64)]
     lib.ac_filtration_values.argtypes = [vp, i32, i64, P(vp), P(i64)]
     lib.ac_attached_flags.argtypes = [vp, i32, i64, P(vp), P(i64)]
@@ -542,6 +544,16 @@ def distributed_complex(centres, radii, alpha: float = 0.0, max_core_atoms: int 
         return None
     n = int(_host_f64(radii).shape[0])
     return merge_parts(n, got, alpha)
+
+
+def fma_peak(fp64: bool = False, iters: int = 0, stream=None) -> float:
+    """ac_fma_peak: the device's measured FMA throughput (FLOP/s, an FMA counts two) in FP32 or FP64."""
+    if iters <= 0:
+        iters = 12000 if fp64 else 800000  # about 50 ms per timed launch on one GB300
+    out = ctypes.c_double()
+    _check(lib().ac_fma_peak(1 if fp64 else 0, int(iters), _stream_ptr(stream), ctypes.byref(out), None),
+           "ac_fma_peak")
+    return out.value
 
 
 def alpha_complex(centres, radii, alpha: float = 0.0, stream=None, **opt) -> AlphaComplex:

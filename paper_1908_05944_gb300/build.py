@@ -18,7 +18,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libalphac.so")
 INCLUDE = os.path.join(ROOT, "include")
 
-SOURCES = ["ac_api.cu", "ac_grid.cu", "ac_local.cu", "ac_canon.cu", "ac_backward.cu", "ac_chunked.cu"]
+SOURCES = ["ac_api.cu", "ac_grid.cu", "ac_local.cu", "ac_canon.cu", "ac_backward.cu", "ac_chunked.cu", "ac_peak.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC",
          "-Xcompiler", "-fvisibility=hidden", "-I", INCLUDE, "-I", CSRC]
