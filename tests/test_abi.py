@@ -57,6 +57,9 @@ def test_null_arguments_are_rejected_without_touching_the_gpu(lib):
     n = ctypes.c_int64()
     assert lib.ac_get_simplices(None, 0, -1, ctypes.byref(p), ctypes.byref(n)) == ac.AC_ERR_INVALID_ARG
     assert lib.ac_get_stats(None, None) == ac.AC_ERR_INVALID_ARG
+    d = ctypes.c_double()
+    assert lib.ac_fma_peak(0, 100, None, None, None) == ac.AC_ERR_INVALID_ARG
+    assert lib.ac_fma_peak(1, 0, None, ctypes.byref(d), None) == ac.AC_ERR_INVALID_ARG
     lib.ac_destroy(None)
     assert b"NULL" in lib.ac_last_error_detail() or lib.ac_last_error_detail() != b""
 
