@@ -1004,6 +1004,8 @@ static int record_build(ac_ctx* c, const DevCounters& post, cudaStream_t s) {
     r.nb_stride = c->nb_stride;
     r.n_wide = c->n_wide;
     r.n_huge = c->n_huge;
+    r.n_w128 = c->n_w128;
+    r.n_w256 = c->n_w256;
     r.post = post;
     r.post.err = 0;
     r.n_pending = (int64_t)post.n_pending;

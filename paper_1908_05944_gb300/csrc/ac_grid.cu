@@ -266,8 +266,11 @@ __global__ void k_deg_starts(const unsigned* __restrict__ hist, unsigned* __rest
     unsigned run = 0;
     for (int q = DEG_BINS - 1; q > b; q--) run += h[q];
     cursor[b] = run;
+    // atoms over 64, 512, 128 and 256 neighbours: the tiers of the per-atom pass
     if (b == 65) n_wide[0] = run + h[65];
     if (b == DEG_BINS - 1) n_wide[1] = h[DEG_BINS - 1];
+    if (b == 129) n_wide[2] = run + h[129];
+    if (b == DEG_BINS - 2) n_wide[3] = run + h[DEG_BINS - 2];
 }
 
 __global__ void k_deg_scatter(const int64_t* __restrict__ cnt, int64_t n, unsigned* __restrict__ cursor,
@@ -295,7 +298,7 @@ int build_neighbours(ac_ctx* c, cudaStream_t s) {
     int64_t* cntp = c->nb_cnt.as<int64_t>();
     if (n == 0) {
         c->nb_total = 0;
-        c->n_wide = 0;
+        c->n_wide = c->n_huge = c->n_w128 = c->n_w256 = 0;
         c->nb_stride = 0;
         c->pair_words = 0;
         AC_CUDA(cudaMemsetAsync(cntp, 0, sizeof(int64_t), s));
@@ -328,7 +331,8 @@ int build_neighbours(ac_ctx* c, cudaStream_t s) {
     unsigned* hist = c->deg.as<unsigned>();
     unsigned* cursor = hist + DEG_BINS;
     static_assert((2 * DEG_BINS * sizeof(unsigned)) % 8 == 0, "head counts 8-aligned");
-    long long* n_wide = reinterpret_cast<long long*>(hist + 2 * DEG_BINS);  // n_wide[0], n_huge = n_wide[1]
+    // atoms over 64 neighbours, over 512 (n_huge), over 128, over 256
+    long long* n_wide = reinterpret_cast<long long*>(hist + 2 * DEG_BINS);
     AC_CUDA(cudaMemsetAsync(hist, 0, DEG_BINS * sizeof(unsigned), s));
     k_deg_hist<<<nb, 128, 0, s>>>(cntp, n, hist);
     AC_LAUNCHED();
@@ -343,13 +347,17 @@ int build_neighbours(ac_ctx* c, cudaStream_t s) {
         total = c->rec.nb_total;
         c->n_wide = c->rec.n_wide;
         c->n_huge = c->rec.n_huge;
+        c->n_w128 = c->rec.n_w128;
+        c->n_w256 = c->rec.n_w256;
         AC_TRY(expect_u64(c, &dc->nb_sum, (unsigned long long)total, s));
         AC_TRY(expect_i64(c, reinterpret_cast<const int64_t*>(n_wide), c->n_wide, s));
         AC_TRY(expect_i64(c, reinterpret_cast<const int64_t*>(n_wide + 1), c->n_huge, s));
+        AC_TRY(expect_i64(c, reinterpret_cast<const int64_t*>(n_wide + 2), c->n_w128, s));
+        AC_TRY(expect_i64(c, reinterpret_cast<const int64_t*>(n_wide + 3), c->n_w256, s));
         AC_TRY(expect_i64(c, c->pair_moff.as<int64_t>() + n, c->pair_words, s));
     } else {
         AC_CUDA(cudaMemcpyAsync(c->h_stage + 1, n_wide, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-        AC_CUDA(cudaMemcpyAsync(c->h_stage + 3, n_wide + 1, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        AC_CUDA(cudaMemcpyAsync(c->h_stage + 3, n_wide + 1, 3 * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
         AC_CUDA(cudaMemcpyAsync(c->h_stage + 2, c->pair_moff.as<int64_t>() + n, sizeof(int64_t),
                                 cudaMemcpyDeviceToHost, s));
         DevCounters h;
@@ -357,6 +365,8 @@ int build_neighbours(ac_ctx* c, cudaStream_t s) {
         total = (int64_t)h.nb_sum;
         c->n_wide = c->h_stage[1];
         c->n_huge = c->h_stage[3];
+        c->n_w128 = c->h_stage[4];
+        c->n_w256 = c->h_stage[5];
         c->pair_words = c->h_stage[2];
         if (h.err & DERR_COINCIDENT)
             return fail(AC_ERR_DEGENERATE, "two centres coincide after quantisation to 1/1024 A");

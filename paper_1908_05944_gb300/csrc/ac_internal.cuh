@@ -113,6 +113,8 @@ struct DevCounters {
     unsigned long long work_next;     // persistent-kernel work counter (narrow-row launch)
     unsigned long long work_next2;    // work counter of the wide-row launch
     unsigned long long work_next3;    // work counter of the launch for atoms beyond 512 neighbours
+    unsigned long long work_next4;    // work counters of the launches for 129..256 and 65..128 neighbours
+    unsigned long long work_next5;
     unsigned int err;
     int max_degree;
     int bad_index;
@@ -183,7 +185,7 @@ struct BuildRecord {
     bool valid = false;
     ac_options opt{};
     int wmax = 0;
-    int64_t nb_total = 0, n_wide = 0, n_huge = 0;
+    int64_t nb_total = 0, n_wide = 0, n_huge = 0, n_w128 = 0, n_w256 = 0;
     int nb_stride = 0;      // layout of the neighbour lists (0: compact)
     int64_t n_pending = 0;  // escalated simplices before the resolve kernel
     DevCounters post{};     // counters after the resolve kernel
@@ -240,6 +242,7 @@ struct ac_ctx {
     ac::DevBuf deg;       // degree histogram and cursors of the work order
     int64_t n_wide = 0;   // atoms with more than 64 neighbours (the head of work)
     int64_t n_huge = 0;   // atoms with more than 512 neighbours (the head of the head)
+    int64_t n_w128 = 0, n_w256 = 0;  // atoms with more than 128, more than 256 neighbours
     ac::DevBuf huge_ws;   // per-warp working sets of the launch for those atoms (global memory)
     int64_t cap_tet = 0, cap_tri = 0, cap_edge = 0, cap_cand[4] = {0, 0, 0, 0}, cap_pending = 0;
 

@@ -138,7 +138,7 @@ struct LocalArgs {
     int nb_stride;
     int64_t n;
     // Work of one launch: the atoms work[0..n-1], taken through work_next,
-    // work_next2 or work_next3 (counter 0, 1, 2: launches running beside one another).
+    // work_next2 .. work_next5 (counter 0 .. 4: launches running beside one another).
     const int32_t* work;
     int counter;
     // rows of more than 16 words: the per-warp working sets, in global memory
@@ -521,7 +521,11 @@ __global__ void __launch_bounds__(256, 4) k_local(LocalArgs A) {
     __syncwarp();
 
     const long long n_items = A.n;
-    unsigned long long* next = A.counter == 2 ? &cnt->work_next3 : A.counter == 1 ? &cnt->work_next2 : &cnt->work_next;
+    unsigned long long* next = A.counter == 4   ? &cnt->work_next5
+                               : A.counter == 3 ? &cnt->work_next4
+                               : A.counter == 2 ? &cnt->work_next3
+                               : A.counter == 1 ? &cnt->work_next2
+                                                : &cnt->work_next;
     for (;;) {
         long long i_ll = 0;
         if (lane == 0) i_ll = (long long)atomicAdd(next, 1ull);
@@ -1404,8 +1408,10 @@ static int launch_huge(ac_ctx* c, LocalArgs a, cudaStream_t s) {
     int dev = 0, sms = 0;
     AC_CUDA(cudaGetDevice(&dev));
     AC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    const int64_t cap = ((int64_t)2 << 30) / (int64_t)sizeof(WarpSmem<32>);
-    const int64_t warps = std::min<int64_t>(std::min<int64_t>(a.n, 16 * (int64_t)sms), cap);
+    // as many warps as can be resident (two-warp blocks, 64 registers: 32 warps per SM), their
+    // working sets within 4 GB
+    const int64_t cap = ((int64_t)4 << 30) / (int64_t)sizeof(WarpSmem<32>);
+    const int64_t warps = std::min<int64_t>(std::min<int64_t>(a.n, 32 * (int64_t)sms), cap);
     const int64_t blocks = (warps + 1) / 2;
     AC_TRY(c->huge_ws.reserve((size_t)blocks * 2 * sizeof(WarpSmem<32>), s));
     a.gws = c->huge_ws.p;
@@ -1427,17 +1433,19 @@ static int launch_words(ac_ctx* c, int words, const LocalArgs& a, int warps, cud
 
 // One per-atom pass over the work order (decreasing neighbour count). When
 // some atom has more than 64 neighbours, those atoms (the head of the order)
-// run in a kernel with wider rows on a side stream, concurrently with the
-// narrow kernel (64-bit rows: smaller shared-memory footprint, twice the
-// resident warps) over the rest; the wide launch is small and starts first.
-// Atoms with more than 512 neighbours (the head of the head) run before it on
-// the side stream, with their working sets in global memory.
+// run on a side stream, concurrently with the narrow kernel (64-bit rows:
+// smaller shared-memory footprint, twice the resident warps) over the rest,
+// in tiers of the row width they need, each with the shared memory (and so the
+// resident warps) of its own width: more than 512 neighbours (working sets in
+// global memory), 257..512 (16 words), 129..256 (8), 65..128 (4).
 template <class R>
 static int launch_pass(ac_ctx* c, int words, LocalArgs& a, cudaStream_t s) {
     AC_TRY(stage_mark(c, 8, s));
     const int32_t* work = c->work.as<int32_t>();
     const int64_t n_wide = words > 2 ? c->n_wide : 0;
     const int64_t n_huge = words > 16 ? std::min(c->n_huge, n_wide) : 0;
+    const int64_t n_w256 = words > 8 ? std::max(std::min(c->n_w256, n_wide), n_huge) : n_huge;
+    const int64_t n_w128 = words > 4 ? std::max(std::min(c->n_w128, n_wide), n_w256) : n_w256;
     if (n_wide > 0) {
         AC_CUDA(cudaEventRecord(c->ev_fork, s));
         AC_CUDA(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
@@ -1448,13 +1456,18 @@ static int launch_pass(ac_ctx* c, int words, LocalArgs& a, cudaStream_t s) {
             huge.counter = 2;
             AC_TRY(launch_huge<R>(c, huge, c->side));
         }
-        if (n_wide > n_huge) {
-            LocalArgs wide = a;
-            wide.work = work + n_huge;
-            wide.n = n_wide - n_huge;
-            wide.counter = 1;
-            AC_TRY(launch_words<R>(c, words > 16 ? 16 : words, wide, 4, c->side));
-        }
+        // [first, last) of the work order in a tier of the given row width
+        auto tier = [&](int64_t first, int64_t last, int w, int counter, int warps) -> int {
+            if (last <= first) return AC_OK;
+            LocalArgs t = a;
+            t.work = work + first;
+            t.n = last - first;
+            t.counter = counter;
+            return launch_words<R>(c, w, t, warps, c->side);
+        };
+        AC_TRY(tier(n_huge, n_w256, 16, 1, 4));
+        AC_TRY(tier(n_w256, n_w128, 8, 3, 4));
+        AC_TRY(tier(n_w128, n_wide, 4, 4, 0));
         AC_CUDA(cudaEventRecord(c->ev_join, c->side));
     }
     LocalArgs narrow = a;
