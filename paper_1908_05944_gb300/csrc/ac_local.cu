@@ -141,8 +141,9 @@ struct LocalArgs {
     // work_next2 .. work_next5 (counter 0 .. 4: launches running beside one another).
     const int32_t* work;
     int counter;
-    // rows of more than 16 words: the per-warp working sets, in global memory
-    // (one per warp of the launch), as they do not fit shared memory
+    // rows of 8 words or more: the per-warp working sets in global memory (one
+    // per warp of the launch), where shared memory would hold too few of them;
+    // rows of more than 16 words always (they do not fit shared memory)
     void* gws;
     PredConst pc;
     Bounds<float> b32;
@@ -506,8 +507,12 @@ __global__ void __launch_bounds__(256, 4) k_local(LocalArgs A) {
     constexpr bool is32 = sizeof(R) == 4;
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
-    SM& S = WORDS > 16 ? reinterpret_cast<SM*>(A.gws)[(size_t)blockIdx.x * (blockDim.x >> 5) + wib]
-                       : reinterpret_cast<SM*>(smem_raw)[wib];
+    // working set: shared memory, or (rows of 8 words or more when the launch
+    // provides them, always beyond 16 words) one per warp in global memory
+    constexpr bool may_global = WORDS >= 8;
+    SM& S = (WORDS > 16 || (may_global && A.gws))
+                ? reinterpret_cast<SM*>(A.gws)[(size_t)blockIdx.x * (blockDim.x >> 5) + wib]
+                : reinterpret_cast<SM*>(smem_raw)[wib];
     DevCounters* cnt = A.cnt;
     const long long Aq = A.pc.A;
     constexpr bool keep = KEEP;  // A.pc.keep_candidates
@@ -1403,19 +1408,23 @@ static int launch_local(ac_ctx* c, const LocalArgs& a, int64_t max_items, int wa
 // (about 300 KB) in global memory, one warp per atom up to 16 per SM (the
 // kernel waits on memory: warps hide it), 2 GB of working sets at most;
 // blocks of two warps.
-template <class R>
-static int launch_huge(ac_ctx* c, LocalArgs a, cudaStream_t s) {
+// A launch whose per-warp working sets live in global memory (rows of 8 words
+// or more): as many warps as can be resident (two-warp blocks, 64 registers:
+// 32 warps per SM) where shared memory would allow 2 to 8, their working sets
+// within 4 GB. The tiers that use it run one after another on one stream and
+// share the buffer.
+template <int WORDS, class R>
+static int launch_global(ac_ctx* c, LocalArgs a, cudaStream_t s) {
+    static_assert(WORDS >= 8, "narrow rows keep their working sets in shared memory");
     int dev = 0, sms = 0;
     AC_CUDA(cudaGetDevice(&dev));
     AC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    // as many warps as can be resident (two-warp blocks, 64 registers: 32 warps per SM), their
-    // working sets within 4 GB
-    const int64_t cap = ((int64_t)4 << 30) / (int64_t)sizeof(WarpSmem<32>);
+    const int64_t cap = ((int64_t)4 << 30) / (int64_t)sizeof(WarpSmem<WORDS>);
     const int64_t warps = std::min<int64_t>(std::min<int64_t>(a.n, 32 * (int64_t)sms), cap);
     const int64_t blocks = (warps + 1) / 2;
-    AC_TRY(c->huge_ws.reserve((size_t)blocks * 2 * sizeof(WarpSmem<32>), s));
+    AC_TRY(c->huge_ws.reserve((size_t)blocks * 2 * sizeof(WarpSmem<WORDS>), s));
     a.gws = c->huge_ws.p;
-    void (*kern)(LocalArgs) = a.pc.keep_candidates ? k_local<32, R, true> : k_local<32, R, false>;
+    void (*kern)(LocalArgs) = a.pc.keep_candidates ? k_local<WORDS, R, true> : k_local<WORDS, R, false>;
     kern<<<(unsigned)blocks, 64, 0, s>>>(a);
     AC_LAUNCHED();
     c->local_launches++;
@@ -1454,20 +1463,22 @@ static int launch_pass(ac_ctx* c, int words, LocalArgs& a, cudaStream_t s) {
             huge.work = work;
             huge.n = n_huge;
             huge.counter = 2;
-            AC_TRY(launch_huge<R>(c, huge, c->side));
+            AC_TRY((launch_global<32, R>(c, huge, c->side)));
         }
         // [first, last) of the work order in a tier of the given row width
-        auto tier = [&](int64_t first, int64_t last, int w, int counter, int warps) -> int {
+        auto tier = [&](int64_t first, int64_t last, int w, int counter) -> int {
             if (last <= first) return AC_OK;
             LocalArgs t = a;
             t.work = work + first;
             t.n = last - first;
             t.counter = counter;
-            return launch_words<R>(c, w, t, warps, c->side);
+            return w == 16 ? launch_global<16, R>(c, t, c->side)
+                   : w == 8 ? launch_global<8, R>(c, t, c->side)
+                            : launch_words<R>(c, w, t, 0, c->side);
         };
-        AC_TRY(tier(n_huge, n_w256, 16, 1, 4));
-        AC_TRY(tier(n_w256, n_w128, 8, 3, 4));
-        AC_TRY(tier(n_w128, n_wide, 4, 4, 0));
+        AC_TRY(tier(n_huge, n_w256, 16, 1));
+        AC_TRY(tier(n_w256, n_w128, 8, 3));
+        AC_TRY(tier(n_w128, n_wide, 4, 4));
         AC_CUDA(cudaEventRecord(c->ev_join, c->side));
     }
     LocalArgs narrow = a;
