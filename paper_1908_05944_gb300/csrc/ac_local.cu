@@ -1444,9 +1444,11 @@ static int launch_words(ac_ctx* c, int words, const LocalArgs& a, int warps, cud
 // some atom has more than 64 neighbours, those atoms (the head of the order)
 // run on a side stream, concurrently with the narrow kernel (64-bit rows:
 // smaller shared-memory footprint, twice the resident warps) over the rest,
-// in tiers of the row width they need, each with the shared memory (and so the
-// resident warps) of its own width: more than 512 neighbours (working sets in
-// global memory), 257..512 (16 words), 129..256 (8), 65..128 (4).
+// in tiers of the row width they need: more than 512 neighbours (32 words),
+// 257..512 (16), 129..256 (8), each with its working sets in global memory at
+// 32 warps per SM (shared memory would hold 2 to 8 of them), and 65..128 (4),
+// whose working sets stay in shared memory (in global memory that tier ran
+// slower on a 100k-atom globule).
 template <class R>
 static int launch_pass(ac_ctx* c, int words, LocalArgs& a, cudaStream_t s) {
     AC_TRY(stage_mark(c, 8, s));
