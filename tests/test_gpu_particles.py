@@ -55,6 +55,27 @@ def test_particles_beyond_512_neighbours():
         assert_same_complex(gpu, oracle.alpha_complex(c, r, 0.0))
 
 
+def test_particles_candidate_lists_all_tiers():
+    """The candidate lists (Sigma_ortho^1..3, the keep_candidates build) of a cloud whose particles
+    reach every row width of the per-atom pass: up to 64 neighbours (shared-memory working sets),
+    65..128, 129..256, 257..512 and 513..1,024 (working sets in global memory), against the oracle's."""
+    c, r = synth.particles(14, 3000, r_hi=4.0)
+    # grown-ball neighbour counts at alpha = 0 (balls meet: |c_i - c_x| <= r_i + r_x), in FP64: only
+    # to show that every width is reached
+    cc, rr = np.asarray(c, np.float64), np.asarray(r, np.float64)
+    d2 = ((cc[:, None, :] - cc[None, :, :]) ** 2).sum(-1)
+    deg = (d2 <= (rr[:, None] + rr[None, :]) ** 2).sum(1) - 1
+    for lo, hi in ((1, 64), (65, 128), (129, 256), (257, 512), (513, 1024)):
+        assert np.any((deg >= lo) & (deg <= hi)), (lo, hi)
+    ref = oracle.alpha_complex(c, r, 0.0)
+    gpu = run_gpu(c, r, 0.0, keep_candidates=True)
+    assert gpu.stats()["max_degree"] > 512
+    for d in (1, 2, 3):
+        got = gpu.candidates(d).cpu().numpy()
+        assert np.array_equal(got, ref.candidates[d]), f"Sigma_ortho^{d} differs"
+    assert_same_complex(gpu, ref)
+
+
 def test_particles_beyond_1024_neighbours_refused():
     import paper_1908_05944_gb300 as ac
 
