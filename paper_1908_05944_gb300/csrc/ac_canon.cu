@@ -21,6 +21,7 @@
 #include <type_traits>
 
 #include "ac_internal.cuh"
+#include "ac_bucket.h"
 #include "ac_round.h"
 
 namespace ac {
@@ -249,34 +250,10 @@ __device__ __forceinline__ void bitonic_place(SortSmem& S, const int4* __restric
     }
 }
 
-// Buckets above CSORT_MAX items (rare): one lane, insertion sort then de-duplication.
+// Buckets above CSORT_MAX items (rare): one lane, heap sort in place (O(k log k)) then de-duplication.
 template <int K>
 __device__ void sort_big_bucket(int4* __restrict__ T, int64_t a, int64_t b, int64_t* __restrict__ uniq_g) {
-    auto less = [](const int4& u, const int4& v) {
-        if (u.y != v.y) return u.y < v.y;
-        if (u.z != v.z) return u.z < v.z;
-        return K == 4 && u.w < v.w;
-    };
-    auto eq = [](const int4& u, const int4& v) { return u.y == v.y && u.z == v.z && (K != 4 || u.w == v.w); };
-    for (int64_t i = a + 1; i < b; i++) {
-        const int4 v = T[i];
-        int64_t j = i;
-        while (j > a && less(v, T[j - 1])) {
-            T[j] = T[j - 1];
-            j--;
-        }
-        T[j] = v;
-    }
-    int64_t w = a;
-    for (int64_t i = a; i < b; i++) {
-        const int4 v = T[i];
-        if (w > a && eq(T[w - 1], v)) {
-            if (K < 4) T[w - 1].w |= v.w;
-        } else {
-            T[w++] = v;
-        }
-    }
-    *uniq_g = w - a;
+    *uniq_g = sort_unique_bucket<K>(T, a, b);
 }
 
 template <int K>
