@@ -80,7 +80,7 @@ def test_shell3m_closure_and_monotone_size(shell):
     assert 5 < per_atom < 40
 
 
-def test_batch1024_every_molecule():
+def test_batch1024_every_molecule(tmp_path):
     from concurrent.futures import ThreadPoolExecutor
 
     import torch
@@ -138,8 +138,8 @@ def test_batch1024_every_molecule():
                                  "first": [(int(m), int(cr[m]), int(cs[m])) for m in np.nonzero(cr != cs)[0][:5]]}
         import json
 
-        with open(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "gpurun_out",
-                               "batch_fail.json"), "w") as fh:
-            json.dump(report, fh, indent=1)
-        errors.append(f"plan {tuned}; {len(bad)} molecules differ; a synchronised build matches the oracle: {sync_ok}")
+        path = tmp_path / "batch_fail.json"
+        path.write_text(json.dumps(report, indent=1))
+        errors.append(f"plan {tuned}; {len(bad)} molecules differ; a synchronised build matches the oracle: "
+                      f"{sync_ok}; per-dimension report in {path}")
     assert not errors, errors[:5] + errors[-1:]
