@@ -3,7 +3,9 @@ compiled for the host with g++ and checked against a plain Python sort: for
 K = 2, 3 (w a flag, OR-ed over equal tuples) and K = 4 (w part of the key),
 buckets of 0 to 5,000 tuples with many repeats, already sorted, reversed and
 all-equal inputs, and a bucket in the middle of a larger array (the items
-around it must stay untouched).
+around it must stay untouched). A third check counts the key comparisons on
+buckets of 10^5 tuples: at most 3 k log2 k, so the sort stays O(k log k) (an
+insertion sort, quadratic, took minutes on the GPU for such buckets).
 """
 import os
 import random
@@ -117,3 +119,62 @@ def test_bucket_inside_a_larger_array(harness):
         assert rows[:a] == T[:a] and rows[b:] == T[b:], "items outside the bucket changed"
         assert u == len(_want(K, T, a, b))
         assert rows[a:a + u] == _want(K, T, a, b)
+
+
+COUNTING = r"""
+#include <stdio.h>
+#include <vector>
+#include "ac_bucket.h"
+static long long g_cmp = 0;
+struct CInt {  // an int whose comparisons are counted
+    int v;
+    bool operator<(const CInt& o) const { ++g_cmp; return v < o.v; }
+    bool operator!=(const CInt& o) const { ++g_cmp; return v != o.v; }
+    bool operator==(const CInt& o) const { ++g_cmp; return v == o.v; }
+    CInt& operator|=(const CInt& o) { v |= o.v; return *this; }
+};
+struct Tup { CInt x, y, z, w; };
+int main() {
+    long long n;
+    int kind;
+    while (scanf("%lld %d", &n, &kind) == 2) {
+        std::vector<Tup> T(n);
+        unsigned s = 12345u;
+        for (long long i = 0; i < n; i++) {
+            s = s * 1664525u + 1013904223u;
+            int y = kind == 0 ? (int)(s >> 8) % 1000000 : kind == 1 ? (int)i : (int)(n - i);
+            T[i] = Tup{{17}, {y}, {(int)(s >> 20) & 7}, {(int)(s >> 3) & 1}};
+        }
+        g_cmp = 0;
+        long long u = ac::sort_unique_bucket<4>(T.data(), 0, n);
+        bool sorted = true;
+        for (long long i = 1; i < u; i++) {
+            const Tup &a = T[i - 1], &b = T[i];
+            if (a.y.v > b.y.v || (a.y.v == b.y.v && (a.z.v > b.z.v || (a.z.v == b.z.v && a.w.v >= b.w.v))))
+                sorted = false;
+        }
+        printf("%lld %lld %d\n", g_cmp, u, sorted ? 1 : 0);
+    }
+    return 0;
+}
+"""
+
+
+def test_comparisons_are_n_log_n(tmp_path):
+    import math
+
+    cxx = shutil.which("g++") or shutil.which("c++")
+    if not cxx:
+        pytest.skip("no host C++ compiler")
+    src = tmp_path / "c.cpp"
+    src.write_text(COUNTING)
+    exe = tmp_path / "c"
+    subprocess.check_call([cxx, "-O2", "-std=c++17", "-I", CSRC, str(src), "-o", str(exe)])
+    n = 100000
+    inp = "".join(f"{n} {kind}\n" for kind in (0, 1, 2))  # random, ascending, descending
+    out = subprocess.run([str(exe)], input=inp, capture_output=True, text=True, check=True).stdout.split("\n")
+    for line in out[:3]:
+        cmp, u, ok = (int(v) for v in line.split())
+        assert ok == 1 and 0 < u <= n
+        # each key comparison is up to 3 field comparisons (y, z, w); the de-duplication adds 3 per tuple
+        assert cmp <= 3 * (3 * n * math.log2(n)) + 3 * n, (cmp, n)
